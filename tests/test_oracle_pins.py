@@ -1,0 +1,264 @@
+"""Pins for the CPU FP64 oracle: checks against things other than the oracle itself.
+
+Contraction (the loop domain + sum instruction of Section 2.1, dG FEM volume of
+Table 1): hand-worked tables, numpy's einsum as an independent library routine,
+closed forms (identity, permutation, rank one, zero), exact integer arithmetic,
+linearity, and the layout change of Section 2.4.3 (node-major is the transpose).
+A set of planted mistakes (transposed operand, dropped term, wrong sign, wrong
+index) must each fail at least one of these checks.
+
+bf16 rounding and split: torch's nearest-even bfloat16 conversion, hand values
+at ties, and the exactness of the three-term split.
+
+Cost model: a hand-worked network, central finite differences of the loss, and
+Adam's closed form under a constant gradient.
+"""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------- contraction
+
+def _load_hand():
+    with open(os.path.join(GOLDEN, "contract_hand.json")) as fh:
+        return json.load(fh)["cases"]
+
+
+def _pin_failures(fn):
+    """Run every contraction pin against ``fn(D, u, layout)``; return failing pin names."""
+    fails = []
+    for case in _load_hand():
+        D = np.array(case["D"], dtype=np.float64)
+        u = np.array(case["u"], dtype=np.float64)
+        if not np.array_equal(fn(D, u, "elem"), np.array(case["out"], dtype=np.float64)):
+            fails.append("hand")
+    rng = np.random.default_rng(11)
+    E, N, F = 37, 9, 3
+    D = rng.uniform(-1, 1, size=(F, N, N))
+    u = rng.standard_normal((E, N))
+    ref = np.einsum("fij,ej->fei", D, u)
+    if not np.allclose(fn(D, u, "elem"), ref, rtol=1e-13, atol=1e-13):
+        fails.append("einsum")
+    I = np.broadcast_to(np.eye(N), (1, N, N))
+    if not np.array_equal(fn(I, u, "elem")[0], u):
+        fails.append("identity")
+    perm = rng.permutation(N)
+    P = np.zeros((1, N, N))
+    P[0, np.arange(N), perm] = 1.0          # (P u)_i = u_{perm[i]}
+    if not np.array_equal(fn(P, u, "elem")[0], u[:, perm]):
+        fails.append("permutation")
+    a = rng.standard_normal(N)
+    b = rng.standard_normal(N)
+    R1 = np.outer(a, b)[None]
+    if not np.allclose(fn(R1, u, "elem")[0], (u @ b)[:, None] * a[None, :], rtol=1e-12, atol=1e-12):
+        fails.append("rank_one")
+    if np.any(fn(np.zeros((2, N, N)), u, "elem") != 0.0):
+        fails.append("zero")
+    Di = rng.integers(-8, 9, size=(F, N, N))
+    ui = rng.integers(-8, 9, size=(E, N))
+    exact = np.einsum("fij,ej->fei", Di.astype(np.int64), ui.astype(np.int64))
+    if not np.array_equal(fn(Di.astype(np.float64), ui.astype(np.float64), "elem"), exact.astype(np.float64)):
+        fails.append("integer_exact")
+    v = rng.standard_normal((E, N))
+    lhs = fn(D, 2.0 * u - 3.0 * v, "elem")
+    rhs = 2.0 * fn(D, u, "elem") - 3.0 * fn(D, v, "elem")
+    if not np.allclose(lhs, rhs, rtol=1e-12, atol=1e-12):
+        fails.append("linear_u")
+    if not np.array_equal(fn(D, np.ascontiguousarray(u.T), "node"),
+                          np.ascontiguousarray(fn(D, u, "elem").transpose(0, 2, 1))):
+        fails.append("node_major")
+    return fails
+
+
+def test_oracle_passes_every_pin():
+    assert _pin_failures(oracle.contract) == []
+
+
+def _mutant(kind):
+    def fn(D, u, layout):
+        D = np.asarray(D, dtype=np.float64)
+        u = np.asarray(u, dtype=np.float64)
+        if layout == "node":
+            u = u.T
+        F, N, _ = D.shape
+        E = u.shape[0]
+        out = np.zeros((F, E, N))
+        for f in range(F):
+            for e in range(E):
+                for i in range(N):
+                    acc = 0.0
+                    jr = range(N - 1) if kind == "drop_last_term" else range(N)
+                    for j in jr:
+                        d = D[f, j, i] if kind == "transpose_D" else D[f, i, j]
+                        x = u[e, i] if kind == "u_index_i" else u[e, j]
+                        acc = acc - d * x if (kind == "sign" and j == N - 1) else acc + d * x
+                    out[f, e, i] = acc
+        if layout == "node":
+            out = out.transpose(0, 2, 1)
+        return out
+    return fn
+
+
+@pytest.mark.parametrize("kind", ["transpose_D", "drop_last_term", "sign", "u_index_i"])
+def test_pins_catch_planted_mistakes(kind):
+    assert _pin_failures(_mutant(kind)), f"no pin caught the planted mistake {kind}"
+
+
+def test_correct_python_loop_nest_passes_pins():
+    # The same loop nest without a planted mistake passes, so the mutants fail for their mistake.
+    assert _pin_failures(_mutant("none")) == []
+
+
+def test_empty_and_degenerate_shapes():
+    D = np.ones((2, 3, 3))
+    assert oracle.contract(D, np.zeros((0, 3))).shape == (2, 0, 3)
+    assert oracle.contract(D, np.zeros((3, 0)), "node").shape == (2, 3, 0)
+    out = oracle.contract(np.full((1, 1, 1), 3.0), np.array([[2.0], [-1.0]]))
+    assert np.array_equal(out, np.array([[[6.0], [-3.0]]]))
+
+
+def test_contract_rows_matches_full():
+    D, u = synth.operands(300, 7, 2, np.float32, seed=3)
+    rows = np.array([0, 5, 299, 17])
+    full = oracle.contract(D, u)
+    assert np.array_equal(oracle.contract_rows(D, u, rows), full[:, rows, :])
+    unm = synth.to_node_major(u)
+    assert np.array_equal(oracle.contract_rows(D, unm, rows, "node"), full[:, rows, :])
+
+
+def test_threads_do_not_change_result():
+    D, u = synth.operands(1000, 13, 3, np.float32, seed=4)
+    assert np.array_equal(oracle.contract(D, u, threads=1), oracle.contract(D, u, threads=4))
+
+
+def test_rel_fro_error_closed_form():
+    ref = np.array([3.0, 4.0])
+    assert oracle.rel_fro_error(ref, ref) == 0.0
+    assert abs(oracle.rel_fro_error(ref + np.array([0.3, 0.4]), ref) - 0.1) < 1e-15
+
+
+# ------------------------------------------------------------------ bf16 pins
+
+def test_bf16_round_matches_torch_nearest_even():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(5)
+    x = np.concatenate([
+        rng.standard_normal(20000).astype(np.float32),
+        (rng.standard_normal(2000) * 1e-30).astype(np.float32),
+        (rng.standard_normal(2000) * 1e30).astype(np.float32),
+        np.array([0.0, -0.0, 1.0, np.float32(3.4e38), 1e-45, -1e-40, np.inf, -np.inf], np.float32),
+    ])
+    # exact ties: upper half even and odd, lower half 0x8000
+    bits = rng.integers(0, 1 << 15, size=4000, dtype=np.uint32) << 16 | 0x8000
+    bits |= rng.integers(0x30, 0x4f, size=4000, dtype=np.uint32) << 24
+    x = np.concatenate([x, bits.view(np.float32)])
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy()
+    assert np.array_equal(oracle.bf16_round(x), ref, equal_nan=True)
+
+
+def test_bf16_round_hand_values():
+    one = np.float32(1.0)
+    x = np.array([one + np.float32(2.0 ** -8),        # tie between 1 and 1+2^-7 -> even (1)
+                  one + np.float32(3 * 2.0 ** -8),    # tie between 1+2^-7 and 1+2^-6 -> even (1+2^-6)
+                  one + np.float32(2.0 ** -8 + 2.0 ** -20),  # just above the tie -> up
+                  np.float32(-1.5)], dtype=np.float32)
+    y = oracle.bf16_round(x)
+    assert y.tolist() == [1.0, 1.0 + 2.0 ** -6, 1.0 + 2.0 ** -7, -1.5]
+
+
+def test_bf16_split3_exact_and_terms_are_bf16():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(6)
+    x = (rng.standard_normal(50000) * 10.0 ** rng.uniform(-6, 6, 50000)).astype(np.float32)
+    hi, mid, lo = oracle.bf16_split3(x)
+    assert np.array_equal(hi.astype(np.float64) + mid + lo, x.astype(np.float64))
+    for t in (hi, mid, lo):
+        assert np.array_equal(oracle.bf16_round(t), t)
+    # the same split through torch's conversion (differences are exact in float32)
+    tx = torch.from_numpy(x)
+    th = tx.to(torch.bfloat16).float()
+    tm = (tx - th).to(torch.bfloat16).float()
+    tl = (tx - th - tm).to(torch.bfloat16).float()
+    assert np.array_equal(th.numpy(), hi) and np.array_equal(tm.numpy(), mid) and np.array_equal(tl.numpy(), lo)
+    # magnitudes fall by at least 2^8 per term
+    nz = hi != 0
+    assert np.all(np.abs(mid[nz]) <= np.abs(hi[nz]) * 2.0 ** -8)
+
+
+def test_bf16x3_all_nine_products_equal_exact_contraction():
+    D, u = synth.operands(200, 11, 2, np.float32, seed=7, scale_exp=3.0)
+    allpairs = [(a, b) for a in range(3) for b in range(3)]
+    full = oracle.contract_bf16x3(D, u, pairs=allpairs)
+    ref = oracle.contract(D, u)
+    assert oracle.rel_fro_error(full, ref) < 1e-15
+    kept = oracle.contract_bf16x3(D, u)
+    assert oracle.rel_fro_error(kept, ref) < 2.0 ** -22
+    plain = oracle.contract_bf16(D, u)
+    err = oracle.rel_fro_error(plain, ref)
+    assert 1e-4 < err < 1e-2   # bf16 operand rounding shows up at about 2^-8
+
+
+def test_integer_inputs_are_bf16_exact():
+    D, u = synth.integer_operands(64, 33, 2, seed=8)
+    ref = oracle.contract(D, u)
+    assert np.array_equal(oracle.contract_bf16(D, u), ref)
+    assert np.array_equal(oracle.contract_bf16x3(D, u), ref)
+
+
+# --------------------------------------------------------------- MLP pins
+
+def test_mlp_hand_network():
+    with open(os.path.join(GOLDEN, "mlp_hand.json")) as fh:
+        g = json.load(fh)
+    pr = g["params"]
+    p = np.array([pr[k] for k in ("W1", "b1", "W2", "b2", "W3", "b3", "w4", "b4")])
+    assert oracle.mlp_param_count(1, 1) == 8
+    x = np.array([[c["x"]] for c in g["cases"]])
+    y = oracle.mlp_forward(p, x, H=1)
+    assert y.tolist() == [c["y"] for c in g["cases"]]
+    gc = g["grad_case"]
+    loss, grad = oracle.mlp_loss_grad(p, np.array([[gc["x"]]]), np.array([gc["t"]]), H=1)
+    assert loss == gc["loss"]
+    want = np.array([gc["grad"][k] for k in ("W1", "b1", "W2", "b2", "W3", "b3", "w4", "b4")])
+    assert np.array_equal(grad, want)
+
+
+def test_mlp_gradient_matches_central_differences():
+    rng = np.random.default_rng(9)
+    din, H, B = 6, 64, 16
+    n = oracle.mlp_param_count(din, H)
+    assert n == H * din + H + 2 * (H * H + H) + H + 1
+    p = rng.uniform(-1, 1, n) * np.sqrt(6.0 / 64)
+    x = rng.standard_normal((B, din))
+    t = rng.standard_normal(B)
+    loss, g = oracle.mlp_loss_grad(p, x, t)
+    assert abs(loss - np.mean((oracle.mlp_forward(p, x) - t) ** 2)) < 1e-12
+    idx = rng.choice(n, 200, replace=False)
+    h = 1e-6
+    fd = np.empty(idx.size)
+    for k, q in enumerate(idx):
+        pp = p.copy(); pp[q] += h
+        pm = p.copy(); pm[q] -= h
+        fd[k] = (oracle.mlp_loss_grad(pp, x, t)[0] - oracle.mlp_loss_grad(pm, x, t)[0]) / (2 * h)
+    assert np.linalg.norm(fd - g[idx]) / np.linalg.norm(g[idx]) < 1e-6
+
+
+def test_adam_constant_gradient_closed_form():
+    # With a constant gradient the bias-corrected moments are g and g^2 exactly,
+    # so every step moves p by lr * g / (|g| + eps).
+    g = np.array([0.5, -2.0, 1e-3, 0.0])
+    p = np.zeros(4); m = np.zeros(4); v = np.zeros(4)
+    lr, eps = 1e-3, 1e-8
+    for t in range(1, 6):
+        oracle.adam_step(p, g, m, v, t, lr=lr, eps=eps)
+    want = -5 * lr * g / (np.abs(g) + eps)
+    assert np.allclose(p, want, rtol=1e-9, atol=1e-15)
