@@ -1,0 +1,380 @@
+#!/usr/bin/env python
+"""Benchmark of the batched element-local contraction on GB300.
+
+    out[f,e,i] = sum_j D_f[i,j] * u[e,j]        (dG FEM volume, Table 1)
+
+Workload (default): E = 2^21 elements, N = 35 nodes, F = 3 operators, FP32,
+element-major, D ~ U[-1,1), u ~ N(0,1), seed 0. One step = one contraction of the
+whole batch (load u, stage D, contract, store out) through the C ABI.
+
+Prints one JSON line. `value` is device-timed GFLOP/s with inputs resident in
+HBM (flops = 2 E N^2 F); `e2e` is the same metric through lc_contract_host with
+pinned host buffers, host<->device copies inside the timed region. The input and
+output (1.17 GB per step) are larger than the 129 MB L2, so no flush is needed.
+
+--impl reference times the CPU FP64 oracle (the untransformed loop nest) on the
+host cores on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "fp32_three": dict(E=1 << 21, N=35, F=3, precision="fp32",
+                       desc="FP32 three-operator contraction E=2^21 N=35 F=3"),
+    "precision": dict(E=1 << 20, N=84, F=4, precision="fp32",
+                      desc="precision-sweep problem E=2^20 N=84 F=4 (u scaled 10^k)"),
+    "fp64_single": dict(E=4096, N=20, F=1, precision="fp64",
+                        desc="FP64 single-operator contraction E=4096 N=20 F=1"),
+}
+
+# DRAM bytes per launch from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum),
+# keyed by (workload, variant key); valid only while the kernel sources hash to `src`.
+NCU_TRAFFIC = {}
+
+
+def csrc_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1405_7470_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return dict(hbm_gbs=d["hbm_gbs"], bf16_tflops=d["bf16_tflops"],
+                    bf16_tflops_sustained=d.get("bf16_tflops_sustained", d["bf16_tflops"]),
+                    sm_max_mhz=d.get("sm_max_mhz", 2070.0), source="measured")
+    return dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0, sm_max_mhz=2070.0,
+                source="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        exe = shutil.which("nvidia-smi")
+        if not exe:
+            return
+        os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.fh = open(self.path, "w")
+        self.proc = subprocess.Popen([exe, f"--id={self.index}", f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits", "-lms", "100"],
+                                     stdout=self.fh, stderr=subprocess.DEVNULL)
+        time.sleep(0.3)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sms, maxs, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sms.append(float(parts[1]))
+                    maxs.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, p in zip(names, parts[5:9]):
+                    if p.lower() == "active":
+                        reasons.add(n)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxs), "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def choose_variant(lc, kernel, wl, layout, spec):
+    if spec and spec != "default":
+        d = json.loads(spec)
+        return lc.Variant(**d)
+    return lc.variant_default(kernel, wl["E"], wl["N"], wl["F"], layout, wl["precision"])
+
+
+def roofline_for(v, wl, peaks, sms, t_launch_s, workload_key):
+    E, N, F = wl["E"], wl["N"], wl["F"]
+    es = 8 if wl["precision"] == "fp64" else 4
+    flops = 2.0 * E * N * N * F
+    nbytes = es * E * N * (1 + F) + es * F * N * N
+    t_hbm = nbytes / (peaks["hbm_gbs"] * 1e9)
+    engine = v["engine"]
+    if engine == "tcgen05":
+        alu_peak = None
+    else:
+        # FP32: 128 FMA lanes per SM; FP64: 2 per SM (the part's nominal 1.25 TFLOP/s FP64)
+        lanes = 128 if es == 4 else 2
+        alu_peak = sms * lanes * 2 * peaks["sm_max_mhz"] * 1e6
+    t_alu = flops / alu_peak if alu_peak else 0.0
+    traffic = None
+    key = (workload_key, json.dumps(v, sort_keys=True))
+    rec = NCU_TRAFFIC.get(key)
+    if rec and rec.get("src") == csrc_hash():
+        traffic = rec["bytes"]
+    if t_alu > t_hbm:
+        ach = flops / t_launch_s / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": alu_peak / 1e12, "unit": "TFLOP/s",
+                "frac": ach / (alu_peak / 1e12), "traffic": traffic,
+                "peak_source": f"derived: {sms} SMs x {lanes} FMA lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz",
+                "hbm_frac": (nbytes / t_launch_s / 1e9) / peaks["hbm_gbs"]}
+    ach = nbytes / t_launch_s / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / peaks["hbm_gbs"], "traffic": traffic, "peak_source": peaks["source"]}
+
+
+def run_oracle_baseline(wl, D, u, layout, budget_s=12.0):
+    """Time the CPU FP64 oracle on the same workload (whole batch, repeated up to ~budget_s)."""
+    import oracle
+    D64 = D.astype(np.float64)
+    u64 = u.astype(np.float64)
+    flops = 2.0 * wl["E"] * wl["N"] ** 2 * wl["F"]
+    reps, t_total, ref = 0, 0.0, None
+    while True:
+        t0 = time.perf_counter()
+        ref = oracle.contract(D64, u64, layout)
+        t_total += time.perf_counter() - t0
+        reps += 1
+        if t_total > budget_s or reps >= 3:
+            break
+    cores = oracle.num_threads()
+    return ref, {"value": flops * reps / t_total / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                 "sample": f"whole batch (E={wl['E']}) x {reps} run(s), {t_total:.1f} s, OpenMP over elements"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fp32_three", choices=sorted(WORKLOADS))
+    ap.add_argument("--layout", default="elem", choices=["elem", "node"])
+    ap.add_argument("--variant", default="default", help="JSON descriptor fields or 'default'")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    wl = WORKLOADS[args.workload]
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        return run_reference(args, wl)
+
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_1405_7470_gb300 import lc
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    lc.load()
+    info = lc.device_info()
+    sms = info["sm_count"]
+    peaks = load_peaks()
+
+    E, N, F = wl["E"], wl["N"], wl["F"]
+    if args.workload == "precision":
+        D, u = synth.precision_sweep()
+    elif args.workload == "fp64_single":
+        D, u = synth.fp64_single()
+    else:
+        D, u = synth.fp32_three()
+    u_in = synth.to_node_major(u) if args.layout == "node" else u
+    kernel = lc.Kernel() if F > 1 else lc.Kernel("{ [e,i,j]: 0<=e<E and 0<=i,j<N }",
+                                                  "out[e,i] = sum(j, D[i,j]*u[e,j])")
+    v = choose_variant(lc, kernel, wl, args.layout, args.variant)
+    vd = lc.variant_dict(v)
+    stream = torch.cuda.Stream()
+    Dd = torch.from_numpy(D).cuda()
+    ud = torch.from_numpy(np.ascontiguousarray(u_in)).cuda()
+    shape = (F, N, E) if args.layout == "node" else (F, E, N)
+    out = torch.empty(shape, dtype=ud.dtype, device="cuda")
+    flops = 2.0 * E * N * N * F
+
+    def step():
+        lc.check(lc.lc_contract(kernel, v, Dd.data_ptr(), ud.data_ptr(), out.data_ptr(), E, N, F,
+                                stream.cuda_stream), "lc_contract")
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    if lc.device_error() != 0:
+        raise RuntimeError("device error word set during warm-up")
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = starts[0].elapsed_time(ends[-1])
+    per_launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = flops * world / (ms_per_step * 1e-3) / 1e9
+    launch_s = statistics.mean(per_launch_ms) * 1e-3
+
+    # error of this run against the FP64 oracle, reduced on the GPU (lc_error_norm)
+    rel_err = None
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        ref, cpu = run_oracle_baseline(wl, D, u_in, args.layout)
+        refd = torch.from_numpy(ref).cuda()
+        rel_err = lc.error_norm(out, refd)
+        del refd, ref
+
+    e2e = None
+    if not args.no_e2e:
+        Dh = torch.from_numpy(D).pin_memory()
+        uh = torch.from_numpy(np.ascontiguousarray(u_in)).pin_memory()
+        oh = torch.empty(shape, dtype=ud.dtype).pin_memory()
+
+        def estep():
+            lc.contract_host(kernel, v, Dh, uh, oh, Dd, ud, out, stream=stream)
+
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                estep()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ksteps = max(3, args.steps // 4)
+        e0.record(stream)
+        for _ in range(ksteps):
+            estep()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        es = e0.elapsed_time(e1) / ksteps
+        if world > 1:
+            t = torch.tensor([es], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            es = float(t.item())
+        esz = 8 if wl["precision"] == "fp64" else 4
+        e2e = {"value": flops * world / (es * 1e-3) / 1e9, "unit": "GFLOP/s",
+               "h2d_bytes_per_step": esz * (E * N + F * N * N), "d2h_bytes_per_step": esz * F * E * N,
+               "ms_per_step": es}
+    if lc.device_error() != 0:
+        raise RuntimeError("device error word set during the timed region")
+
+    if rank == 0:
+        roof = roofline_for(vd, wl, peaks, sms, launch_s, args.workload)
+        line = {
+            "metric": "contraction GFLOP/s", "value": value, "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if wl["precision"] == "fp64" else "f32", "data": "synthetic",
+            "config": {"workload": wl["desc"], "E": E, "N": N, "F": F, "layout": args.layout,
+                       "precision": wl["precision"], "variant": vd, "parallelism": f"replicas x{world}",
+                       "l2": "inputs+outputs larger than L2 (no flush needed)",
+                       "bytes_per_step": (8 if wl["precision"] == "fp64" else 4) * (E * N * (1 + F) + F * N * N)},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+            "clocks": clk, "rel_error_vs_oracle": rel_err,
+            "hbm_gbs_achieved": ((8 if wl["precision"] == "fp64" else 4) * (E * N * (1 + F) + F * N * N))
+            / (ms_per_step * 1e-3) / 1e9,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args, wl):
+    """CPU FP64 oracle on the host cores: each step a bounded sample of the workload."""
+    import oracle
+    import synth
+    E, N, F = wl["E"], wl["N"], wl["F"]
+    if args.workload == "precision":
+        D, u = synth.precision_sweep()
+    elif args.workload == "fp64_single":
+        D, u = synth.fp64_single()
+    else:
+        D, u = synth.fp32_three()
+    Es = min(E, 1 << 18)
+    sub = u[:Es]
+    u_in = synth.to_node_major(sub) if args.layout == "node" else sub
+    D64, u64 = D.astype(np.float64), np.ascontiguousarray(u_in, dtype=np.float64)
+    flops = 2.0 * Es * N * N * F
+    for _ in range(args.warmup):
+        oracle.contract(D64, u64, args.layout)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.contract(D64, u64, args.layout)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = flops / dt / 1e9
+    cores = oracle.num_threads()
+    line = {
+        "metric": "contraction GFLOP/s", "value": value, "unit": "GFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["desc"], "E": E, "N": N, "F": F, "layout": args.layout,
+                   "precision": wl["precision"], "sample_elements": Es},
+        "impl": "reference",
+        "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": "GFLOP/s",
+                         "sample": f"first {Es} of {E} elements per step, OpenMP over elements"},
+        "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * lc.h -- C ABI of the GB300 (sm_103a) batched element-local contraction library.
+ *
+ * The computation is the dG FEM volume workload of Table 1:
+ *
+ *     out[f, e, i] = sum_j D[f, i, j] * u[e, j]
+ *         over the loop domain { [f,e,i,j] : 0<=f<F and 0<=e<E and 0<=i,j<N }
+ *
+ * stated, as in Section 2.1, as a loop domain plus one instruction with a sum
+ * reduction, plus optional assumptions on the parameters.  The transformations
+ * of Section 2.4 (split_iname of Eq. 1 with tail guards, the unr / ilp / vec
+ * iname tags, array-axis layout tags, add_prefetch / precompute) are not applied
+ * by a code generator here: each is a field of an explicit variant descriptor
+ * (lc_variant) that selects a hand-written CUDA kernel instance.  Every variant
+ * computes the same result up to rounding (the unordered semantics of
+ * Section 2.3).
+ *
+ * Conventions for every call:
+ *   - Pointers named *_dev are device pointers; the caller allocates and owns
+ *     them.  The library never allocates device memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Work is enqueued asynchronously, like the event-returning invocation of
+ *     Section 2.2; argument errors are returned before anything is enqueued.
+ *   - Arrays are dense and row-major:
+ *       D    [F][N][N]               D[(f*N + i)*N + j]
+ *       u    element-major [E][N]    u[e*N + j]        node-major [N][E]  u[j*E + e]
+ *       out  element-major [F][E][N]                   node-major [F][N][E]
+ *     Element type: double for LC_PREC_FP64, float for every other precision.
+ *   - All entry points are thread-safe; a kernel handle is immutable after
+ *     creation (Section 2.4: transformations return new kernels).
+ */
+#ifndef LC_H
+#define LC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lc_status {
+    LC_OK = 0,
+    LC_ERR_INVALID_ARGUMENT = 1, /* null pointer, negative size, bad enum value */
+    LC_ERR_UNSUPPORTED = 2,      /* domain / instruction / assumption text not recognised */
+    LC_ERR_INVALID_VARIANT = 3,  /* descriptor fields out of range for this problem */
+    LC_ERR_ASSUMPTION = 4,       /* E, N, F violate the kernel's assumptions */
+    LC_ERR_MISALIGNED = 5,       /* a pointer is not aligned as the variant needs */
+    LC_ERR_BUFFER_TOO_SMALL = 6, /* caller buffer (text or workspace) too small */
+    LC_ERR_CUDA = 7,             /* a CUDA runtime call failed; see lc_last_cuda_error */
+    LC_ERR_TIMEOUT = 8,          /* a bounded device wait gave up (device error word) */
+    LC_ERR_NO_DEVICE = 9,        /* no sm_103 device current */
+    LC_ERR_NOT_FOUND = 10        /* lookup failed (e.g. no timing for a candidate) */
+} lc_status;
+
+/* Human-readable name of a status. Never NULL. */
+const char *lc_status_string(lc_status s);
+/* The last CUDA error code seen by this thread (0 if none). */
+int lc_last_cuda_error(void);
+
+/* ------------------------------------------------------------------------- */
+/* Kernel: loop domain + instruction + assumptions (Section 2.1).            */
+/* ------------------------------------------------------------------------- */
+typedef struct lc_kernel lc_kernel;
+typedef struct lc_variant lc_variant;
+
+/*
+ * Parse and validate a contraction kernel.
+ *   domain       isl-style set, e.g. "{ [f,e,i,j]: 0<=f<F and 0<=e<E and 0<=i,j<N }".
+ *                Every iname must have lower bound 0 and an upper bound "< P" or
+ *                "<= P - 1" with P a parameter name.  A three-iname domain
+ *                "{ [e,i,j]: ... }" is the single-operator form (F = 1).
+ *   instructions one assignment "out[f,e,i] = sum(j, D[f,i,j]*u[e,j])" (names are
+ *                free; the index structure must be this one, factors in either
+ *                order; single-operator form "out[e,i] = sum(j, D[i,j]*u[e,j])").
+ *   assumptions  NULL or a conjunction of "P mod k = 0", "P >= k", "P > k",
+ *                "P <= k", "P < k", "P = k" over the domain's parameters.
+ *   out          receives a new handle (free with lc_kernel_destroy).
+ * Errors: LC_ERR_INVALID_ARGUMENT (null text/out), LC_ERR_UNSUPPORTED (text
+ * outside the forms above; *out is left untouched).
+ */
+lc_status lc_kernel_create(const char *domain, const char *instructions,
+                           const char *assumptions, lc_kernel **out);
+void lc_kernel_destroy(lc_kernel *k);
+
+/*
+ * Text dump of a kernel in the spirit of Section 2.1's listing: arguments with
+ * shapes and dimension tags, domain, assumptions, instruction; with a variant,
+ * also the transformations it applies (split of e with its guard, iname tags,
+ * layout tags, prefetch).  Writes at most `cap` bytes including the NUL; sets
+ * *needed to the full length + 1.  `v` may be NULL.
+ * Errors: LC_ERR_BUFFER_TOO_SMALL (text truncated, still NUL-terminated).
+ */
+lc_status lc_kernel_print(const lc_kernel *k, const lc_variant *v, char *buf,
+                          size_t cap, size_t *needed);
+
+/* ------------------------------------------------------------------------- */
+/* Variant descriptor (the transformations of Section 2.4 as values).        */
+/* ------------------------------------------------------------------------- */
+enum { LC_ENGINE_SIMT = 0, LC_ENGINE_TCGEN05 = 1, LC_ENGINE_WARP = 2 };
+enum { LC_LAYOUT_ELEM_MAJOR = 0, LC_LAYOUT_NODE_MAJOR = 1 };
+enum { LC_PREC_FP64 = 0, LC_PREC_FP32 = 1, LC_PREC_BF16 = 2, LC_PREC_BF16X3 = 3 };
+
+struct lc_variant {
+    uint32_t struct_size;     /* sizeof(lc_variant) */
+    int32_t engine;           /* LC_ENGINE_*: SIMT FMA tiles, tcgen05 tensor cores, or one warp
+                                 per element group with shuffles (small N) */
+    int32_t layout;           /* LC_LAYOUT_*: array-axis layout tag of u and out (Sec. 2.4.3) */
+    int32_t precision;        /* LC_PREC_*: FP64/FP32 on the FMA pipes; BF16 or three-term
+                                 split BF16 on the tensor cores with FP32 accumulation */
+    int32_t tile_e;           /* split_iname(e, tile_e): e = e_in + tile_e * e_out (Eq. 1),
+                                 one tile per CTA step */
+    int32_t elems_per_thread; /* ilp tag on e_in: elements per thread (SIMT register block) */
+    int32_t split_i;          /* ilp tag on i: output columns per thread (SIMT register block) */
+    int32_t unroll;           /* unr tag on the j reduction: 1, 2, 4 or 8 */
+    int32_t prefetch_smem;    /* add_prefetch of the u tile into shared memory by TMA (1) or
+                                 direct global loads into registers (0) */
+    int32_t tail_free;        /* 1: no guard on the last e tile; only accepted when an
+                                 assumption "E mod m = 0" with m a multiple of tile_e holds */
+    int32_t stages;           /* u tiles in flight in shared memory (TMA ring depth), >= 1 */
+    int32_t ctas_per_sm;      /* persistent grid size in CTAs per SM; 0 = one CTA per tile */
+};
+
+/*
+ * A reasonable descriptor for (E, N, F, layout, precision): fills *v.
+ * Errors: LC_ERR_INVALID_ARGUMENT, LC_ERR_UNSUPPORTED (no engine supports it).
+ */
+lc_status lc_variant_default(const lc_kernel *k, int64_t E, int32_t N, int32_t F,
+                             int32_t layout, int32_t precision, lc_variant *v);
+
+/*
+ * Check a descriptor against a problem size without launching anything:
+ * field ranges, shared-memory capacity, assumption-gated fast paths.
+ * Errors: LC_ERR_INVALID_VARIANT, LC_ERR_ASSUMPTION, LC_ERR_INVALID_ARGUMENT.
+ */
+lc_status lc_variant_validate(const lc_kernel *k, int64_t E, int32_t N, int32_t F,
+                              const lc_variant *v);
+
+/*
+ * The contraction itself: enqueue out = contraction(D, u) on `stream`.
+ *   D_dev    [F][N][N] operators (double for FP64, else float)
+ *   u_dev    input, layout per v->layout
+ *   out_dev  output, layout per v->layout; must not overlap u_dev or D_dev
+ * Sizes: E >= 0, 1 <= N <= 256, 1 <= F <= 8.  E == 0 enqueues nothing.
+ * Alignment: every pointer 16-byte aligned.
+ * Errors (returned before any launch): LC_ERR_INVALID_ARGUMENT, LC_ERR_INVALID_VARIANT,
+ * LC_ERR_ASSUMPTION, LC_ERR_MISALIGNED, LC_ERR_NO_DEVICE; launch failures: LC_ERR_CUDA.
+ * Bounded device waits that give up set the device error word (lc_device_error).
+ */
+lc_status lc_contract(const lc_kernel *k, const lc_variant *v, const void *D_dev,
+                      const void *u_dev, void *out_dev, int64_t E, int32_t N, int32_t F,
+                      void *stream);
+
+/*
+ * The contraction on host arrays: copies D and u from host to the caller's
+ * device buffers, enqueues lc_contract, and copies out back to the host, all in
+ * order on `stream` (asynchronous with respect to the host when the host
+ * buffers are page-locked; synchronise the stream before reading out_host).
+ *   D_host, u_host, out_host   host arrays with the layouts of lc_contract
+ *   D_dev, u_dev, out_dev      device buffers of the same sizes (caller-owned)
+ * Errors: as lc_contract, plus LC_ERR_CUDA for a failed copy.
+ */
+lc_status lc_contract_host(const lc_kernel *k, const lc_variant *v, const void *D_host,
+                           const void *u_host, void *out_host, int64_t E, int32_t N, int32_t F,
+                           void *D_dev, void *u_dev, void *out_dev, void *stream);
+
+/*
+ * Device error word: returns LC_ERR_TIMEOUT if any kernel recorded a bounded
+ * wait that gave up since the last clear, else LC_OK.  Synchronises the device.
+ * clear != 0 resets the word.
+ */
+lc_status lc_device_error(int clear);
+
+/* ------------------------------------------------------------------------- */
+/* FP64 error norm on the GPU.                                               */
+/* ------------------------------------------------------------------------- */
+enum { LC_DTYPE_F32 = 0, LC_DTYPE_F64 = 1 };
+
+/* Workspace bytes needed by lc_error_norm for n elements. */
+lc_status lc_error_norm_workspace_size(int64_t n, size_t *bytes);
+
+/*
+ * sums_dev[0] = sum_k (out[k] - ref[k])^2,  sums_dev[1] = sum_k ref[k]^2, in FP64,
+ * so that ||out - ref||_F / ||ref||_F = sqrt(sums[0] / sums[1]).  Deterministic:
+ * fixed grid, per-block partial sums in `workspace_dev`, one final block.
+ *   out_dev        n values of type out_dtype (LC_DTYPE_F32 or LC_DTYPE_F64)
+ *   ref_dev        n doubles
+ *   sums_dev       2 doubles (device)
+ *   workspace_dev  lc_error_norm_workspace_size bytes, 16-byte aligned
+ * Errors: LC_ERR_INVALID_ARGUMENT, LC_ERR_BUFFER_TOO_SMALL, LC_ERR_MISALIGNED, LC_ERR_CUDA.
+ */
+lc_status lc_error_norm(const void *out_dev, int32_t out_dtype, const double *ref_dev,
+                        int64_t n, double *sums_dev, void *workspace_dev,
+                        size_t workspace_bytes, void *stream);
+
+/* Number of SMs and compute capability of the current device. */
+lc_status lc_device_info(int32_t *sm_count, int32_t *cc_major, int32_t *cc_minor);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LC_H */

@@ -1,0 +1,1070 @@
+// Host side of the C ABI: kernel text parsing (loop domain, instruction,
+// assumptions; Section 2.1), kernel printing, descriptor validation and
+// dispatch to the CUDA kernels.  No device memory is allocated here.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cctype>
+#include <map>
+#include <mutex>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "lc_internal.h"
+
+struct lc_kernel {
+    lc::Kernel k;
+};
+
+namespace lc {
+
+// ------------------------------------------------------------------ errors
+
+static thread_local int g_last_cuda_error = 0;
+
+lc_status cuda_fail(cudaError_t e)
+{
+    g_last_cuda_error = (int)e;
+    return LC_ERR_CUDA;
+}
+
+// Device error word: set by bounded waits that give up.  Its device address is
+// looked up once per device and passed to kernels as a parameter.
+__device__ unsigned int g_device_error_word;
+
+static std::mutex g_dev_mu;
+static std::map<int, unsigned int *> g_err_ptr;
+static std::map<int, int> g_sm_count;
+static std::map<int, size_t> g_smem_optin;
+
+unsigned int *error_word()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return nullptr;
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    auto it = g_err_ptr.find(dev);
+    if (it != g_err_ptr.end())
+        return it->second;
+    unsigned int *p = nullptr;
+    if (cudaGetSymbolAddress((void **)&p, g_device_error_word) != cudaSuccess)
+        return nullptr;
+    g_err_ptr[dev] = p;
+    return p;
+}
+
+int sm_count()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return 0;
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    auto it = g_sm_count.find(dev);
+    if (it != g_sm_count.end())
+        return it->second;
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    g_sm_count[dev] = n;
+    return n;
+}
+
+size_t smem_optin_limit()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return 0;
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    auto it = g_smem_optin.find(dev);
+    if (it != g_smem_optin.end())
+        return it->second;
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return 0;
+    g_smem_optin[dev] = (size_t)n;
+    return (size_t)n;
+}
+
+int current_cc(int *major, int *minor)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return -1;
+    if (cudaDeviceGetAttribute(major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess)
+        return -1;
+    if (cudaDeviceGetAttribute(minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess)
+        return -1;
+    return 0;
+}
+
+// ------------------------------------------------------------------ tokenizer
+
+struct Tok {
+    enum Kind { ID, INT, OP, END } kind;
+    std::string s;
+    long long v = 0;
+};
+
+static bool tokenize(const char *text, std::vector<Tok> &out)
+{
+    out.clear();
+    const char *p = text;
+    while (*p) {
+        unsigned char c = (unsigned char)*p;
+        if (isspace(c)) {
+            ++p;
+            continue;
+        }
+        if (isalpha(c) || c == '_') {
+            const char *b = p;
+            while (isalnum((unsigned char)*p) || *p == '_')
+                ++p;
+            out.push_back({Tok::ID, std::string(b, p)});
+            continue;
+        }
+        if (isdigit(c)) {
+            long long v = 0;
+            while (isdigit((unsigned char)*p)) {
+                if (v > (1LL << 50))
+                    return false;
+                v = v * 10 + (*p - '0');
+                ++p;
+            }
+            Tok t{Tok::INT, ""};
+            t.v = v;
+            out.push_back(t);
+            continue;
+        }
+        if ((p[0] == '<' || p[0] == '>' || p[0] == '=') && p[1] == '=') {
+            out.push_back({Tok::OP, std::string(p, p + 2)});
+            p += 2;
+            continue;
+        }
+        if (strchr("{}[]():,<>=*-+", c)) {
+            out.push_back({Tok::OP, std::string(1, (char)c)});
+            ++p;
+            continue;
+        }
+        return false;
+    }
+    out.push_back({Tok::END, ""});
+    return true;
+}
+
+struct Cursor {
+    const std::vector<Tok> &t;
+    size_t i = 0;
+    explicit Cursor(const std::vector<Tok> &tt) : t(tt) {}
+    const Tok &peek(size_t k = 0) const { return t[std::min(i + k, t.size() - 1)]; }
+    bool op(const char *s)
+    {
+        if (peek().kind == Tok::OP && peek().s == s) {
+            ++i;
+            return true;
+        }
+        return false;
+    }
+    bool id(std::string &s)
+    {
+        if (peek().kind == Tok::ID) {
+            s = peek().s;
+            ++i;
+            return true;
+        }
+        return false;
+    }
+    bool integer(long long &v)
+    {
+        bool neg = false;
+        size_t save = i;
+        if (op("-"))
+            neg = true;
+        if (peek().kind == Tok::INT) {
+            v = neg ? -peek().v : peek().v;
+            ++i;
+            return true;
+        }
+        i = save;
+        return false;
+    }
+    bool end() const { return peek().kind == Tok::END; }
+};
+
+// One side of a comparison chain: an integer, "P" or "P - 1", or a list of inames.
+struct Operand {
+    enum Kind { INT, PARAM, NAMES } kind;
+    long long v = 0;
+    std::string param;
+    long long param_offset = 0;  // P + offset
+    std::vector<std::string> names;
+};
+
+static bool parse_operand(Cursor &c, Operand &o)
+{
+    long long v;
+    if (c.integer(v)) {
+        o.kind = Operand::INT;
+        o.v = v;
+        return true;
+    }
+    std::string s;
+    if (!c.id(s))
+        return false;
+    o.names = {s};
+    if (c.op("-") || (c.peek().kind == Tok::OP && c.peek().s == "+")) {
+        bool minus = c.t[c.i - 1].s == "-";
+        if (!minus)
+            c.op("+");
+        long long k;
+        if (c.peek().kind != Tok::INT)
+            return false;
+        k = c.peek().v;
+        ++c.i;
+        o.kind = Operand::PARAM;
+        o.param = s;
+        o.param_offset = minus ? -k : k;
+        return true;
+    }
+    while (c.op(",")) {
+        if (!c.id(s))
+            return false;
+        o.names.push_back(s);
+    }
+    o.kind = Operand::NAMES;
+    return true;
+}
+
+static bool is_cmp(const Cursor &c)
+{
+    const Tok &t = c.peek();
+    return t.kind == Tok::OP && (t.s == "<" || t.s == "<=" || t.s == ">" || t.s == ">=");
+}
+
+// Parse "{ [a,b,...] : chain and chain ... }" with an optional "[P,...] ->" prefix.
+static bool parse_domain(const char *text, Kernel &K, std::string &why)
+{
+    std::vector<Tok> toks;
+    if (!tokenize(text, toks)) {
+        why = "domain: bad character";
+        return false;
+    }
+    Cursor c(toks);
+    if (c.peek().kind == Tok::OP && c.peek().s == "[") {
+        // parameter list "[F, E, N] ->"
+        c.op("[");
+        std::string s;
+        while (c.id(s))
+            if (!c.op(","))
+                break;
+        if (!c.op("]") || !c.op("-") || !c.op(">")) {
+            why = "domain: bad parameter list";
+            return false;
+        }
+    }
+    if (!c.op("{") || !c.op("[")) {
+        why = "domain: expected '{ ['";
+        return false;
+    }
+    std::string s;
+    while (c.id(s)) {
+        K.inames.push_back(s);
+        if (!c.op(","))
+            break;
+    }
+    if (!c.op("]") || !c.op(":")) {
+        why = "domain: expected '] :'";
+        return false;
+    }
+    std::map<std::string, int> lower;          // iname -> 1 if lower bound 0 seen
+    std::map<std::string, std::string> upper;  // iname -> bounding parameter
+    for (;;) {
+        std::vector<Operand> ops;
+        std::vector<std::string> cmps;
+        Operand o;
+        if (!parse_operand(c, o)) {
+            why = "domain: expected a constraint";
+            return false;
+        }
+        ops.push_back(o);
+        while (is_cmp(c)) {
+            cmps.push_back(c.peek().s);
+            ++c.i;
+            Operand o2;
+            if (!parse_operand(c, o2)) {
+                why = "domain: bad constraint operand";
+                return false;
+            }
+            ops.push_back(o2);
+        }
+        if (cmps.empty()) {
+            why = "domain: constraint without comparison";
+            return false;
+        }
+        for (size_t k = 0; k < cmps.size(); ++k) {
+            Operand L = ops[k], R = ops[k + 1];
+            std::string op = cmps[k];
+            // normalise to L (< | <=) R
+            if (op == ">" || op == ">=") {
+                std::swap(L, R);
+                op = op == ">" ? "<" : "<=";
+            }
+            auto param_of = [&](const Operand &x, long long &off, std::string &p) {
+                if (x.kind == Operand::PARAM) {
+                    p = x.param;
+                    off = x.param_offset;
+                    return true;
+                }
+                if (x.kind == Operand::NAMES && x.names.size() == 1 &&
+                    std::find(K.inames.begin(), K.inames.end(), x.names[0]) == K.inames.end()) {
+                    p = x.names[0];
+                    off = 0;
+                    return true;
+                }
+                return false;
+            };
+            if (L.kind == Operand::INT && R.kind == Operand::NAMES) {
+                // lower bound: 0 <= x  or  -1 < x
+                bool ok = (op == "<=" && L.v == 0) || (op == "<" && L.v == -1);
+                if (!ok) {
+                    why = "domain: every lower bound must be 0";
+                    return false;
+                }
+                for (auto &n : R.names)
+                    lower[n] = 1;
+                continue;
+            }
+            std::string p;
+            long long off = 0;
+            if (L.kind == Operand::NAMES && param_of(R, off, p) &&
+                std::find(K.inames.begin(), K.inames.end(), L.names[0]) != K.inames.end()) {
+                bool ok = (op == "<" && off == 0) || (op == "<=" && off == -1);
+                if (!ok) {
+                    why = "domain: upper bounds must read x < P or x <= P - 1";
+                    return false;
+                }
+                for (auto &n : L.names) {
+                    if (upper.count(n)) {
+                        why = "domain: iname bounded twice";
+                        return false;
+                    }
+                    upper[n] = p;
+                }
+                continue;
+            }
+            why = "domain: unsupported constraint";
+            return false;
+        }
+        std::string kw;
+        if (c.peek().kind == Tok::ID && c.peek().s == "and") {
+            ++c.i;
+            continue;
+        }
+        break;
+    }
+    if (!c.op("}") || !c.end()) {
+        why = "domain: expected '}'";
+        return false;
+    }
+    std::set<std::string> uniq(K.inames.begin(), K.inames.end());
+    if (uniq.size() != K.inames.size()) {
+        why = "domain: repeated iname";
+        return false;
+    }
+    for (auto &n : K.inames) {
+        if (!lower.count(n) || !upper.count(n)) {
+            why = "domain: iname " + n + " lacks a bound";
+            return false;
+        }
+        if (uniq.count(upper[n])) {
+            why = "domain: bound must be a parameter";
+            return false;
+        }
+        K.bounds.push_back(upper[n]);
+    }
+    for (auto &kv : lower)
+        if (!uniq.count(kv.first)) {
+            why = "domain: bound on unknown iname";
+            return false;
+        }
+    return true;
+}
+
+struct Access {
+    std::string name;
+    std::vector<std::string> idx;
+};
+
+static bool parse_access(Cursor &c, Access &a)
+{
+    if (!c.id(a.name) || !c.op("["))
+        return false;
+    std::string s;
+    while (c.id(s)) {
+        a.idx.push_back(s);
+        if (!c.op(","))
+            break;
+    }
+    return c.op("]");
+}
+
+// Parse "out[f,e,i] = sum(j, D[f,i,j]*u[e,j])" (or the F = 1 form) and assign roles.
+static bool parse_instruction(const char *text, Kernel &K, std::string &why)
+{
+    std::vector<Tok> toks;
+    if (!tokenize(text, toks)) {
+        why = "instruction: bad character";
+        return false;
+    }
+    Cursor c(toks);
+    Access lhs, x, y;
+    std::string red, sum;
+    if (!parse_access(c, lhs) || !c.op("=")) {
+        why = "instruction: expected 'out[...] ='";
+        return false;
+    }
+    if (!c.id(sum) || sum != "sum" || !c.op("(") || !c.id(red) || !c.op(",")) {
+        why = "instruction: expected 'sum(j, ...)'";
+        return false;
+    }
+    if (!parse_access(c, x) || !c.op("*") || !parse_access(c, y) || !c.op(")") || !c.end()) {
+        why = "instruction: expected a product of two array accesses";
+        return false;
+    }
+    const bool multi = lhs.idx.size() == 3;
+    if (!(lhs.idx.size() == 3 || lhs.idx.size() == 2)) {
+        why = "instruction: output must have 2 or 3 indices";
+        return false;
+    }
+    const size_t dn = multi ? 3 : 2;
+    Access *Dp = nullptr, *Up = nullptr;
+    if (x.idx.size() == dn && y.idx.size() == 2 && dn == 3) {
+        Dp = &x;
+        Up = &y;
+    } else if (y.idx.size() == dn && x.idx.size() == 2 && dn == 3) {
+        Dp = &y;
+        Up = &x;
+    } else if (dn == 2 && x.idx.size() == 2 && y.idx.size() == 2) {
+        // D[i,j] * u[e,j]: D's first index is the output's last.
+        const std::string &i = lhs.idx[1];
+        if (x.idx[0] == i) {
+            Dp = &x;
+            Up = &y;
+        } else {
+            Dp = &y;
+            Up = &x;
+        }
+    } else {
+        why = "instruction: operand ranks do not match a contraction";
+        return false;
+    }
+    std::string f = multi ? lhs.idx[0] : "", e = lhs.idx[multi ? 1 : 0], i = lhs.idx[multi ? 2 : 1];
+    std::vector<std::string> dwant = multi ? std::vector<std::string>{f, i, red}
+                                           : std::vector<std::string>{i, red};
+    if (Dp->idx != dwant || Up->idx != std::vector<std::string>{e, red}) {
+        why = "instruction: index structure is not out[f,e,i] = sum(j, D[f,i,j]*u[e,j])";
+        return false;
+    }
+    std::vector<std::string> used = {e, i, red};
+    if (multi)
+        used.push_back(f);
+    std::set<std::string> su(used.begin(), used.end());
+    if (su.size() != used.size()) {
+        why = "instruction: repeated iname";
+        return false;
+    }
+    std::set<std::string> dom(K.inames.begin(), K.inames.end());
+    if (su != dom) {
+        why = "instruction: inames differ from the domain's";
+        return false;
+    }
+    if (lhs.name == Dp->name || lhs.name == Up->name || Dp->name == Up->name) {
+        why = "instruction: arrays must be distinct";
+        return false;
+    }
+    auto bound = [&](const std::string &n) {
+        size_t k = std::find(K.inames.begin(), K.inames.end(), n) - K.inames.begin();
+        return K.bounds[k];
+    };
+    if (bound(i) != bound(red)) {
+        why = "instruction: i and j must share one bound (square operators)";
+        return false;
+    }
+    std::set<std::string> params = {bound(e), bound(i)};
+    if (multi)
+        params.insert(bound(f));
+    if (params.size() != (multi ? 3u : 2u)) {
+        why = "instruction: F, E and N must be distinct parameters";
+        return false;
+    }
+    K.out_name = lhs.name;
+    K.d_name = Dp->name;
+    K.u_name = Up->name;
+    K.f_iname = f;
+    K.e_iname = e;
+    K.i_iname = i;
+    K.j_iname = red;
+    K.F_param = multi ? bound(f) : "";
+    K.E_param = bound(e);
+    K.N_param = bound(i);
+    return true;
+}
+
+static bool parse_assumptions(const char *text, Kernel &K, std::string &why)
+{
+    if (!text)
+        return true;
+    std::vector<Tok> toks;
+    if (!tokenize(text, toks)) {
+        why = "assumptions: bad character";
+        return false;
+    }
+    Cursor c(toks);
+    if (c.end())
+        return true;
+    std::set<std::string> params = {K.E_param, K.N_param};
+    if (!K.F_param.empty())
+        params.insert(K.F_param);
+    for (;;) {
+        Assumption a;
+        if (!c.id(a.param) || !params.count(a.param)) {
+            why = "assumptions: expected a parameter of the domain";
+            return false;
+        }
+        if (c.peek().kind == Tok::ID && c.peek().s == "mod") {
+            ++c.i;
+            long long k, z;
+            if (!c.integer(k) || k <= 0 || !c.op("=") || !c.integer(z) || z != 0) {
+                why = "assumptions: expected 'P mod k = 0'";
+                return false;
+            }
+            a.op = 0;
+            a.k = k;
+        } else {
+            const std::string s = c.peek().s;
+            if (c.peek().kind != Tok::OP) {
+                why = "assumptions: expected a comparison";
+                return false;
+            }
+            if (s == ">=") a.op = 1;
+            else if (s == ">") a.op = 2;
+            else if (s == "<=") a.op = 3;
+            else if (s == "<") a.op = 4;
+            else if (s == "=" || s == "==") a.op = 5;
+            else {
+                why = "assumptions: unknown comparison";
+                return false;
+            }
+            ++c.i;
+            if (!c.integer(a.k)) {
+                why = "assumptions: expected an integer";
+                return false;
+            }
+        }
+        K.assumptions.push_back(a);
+        if (c.peek().kind == Tok::ID && c.peek().s == "and") {
+            ++c.i;
+            continue;
+        }
+        break;
+    }
+    if (!c.end()) {
+        why = "assumptions: trailing text";
+        return false;
+    }
+    return true;
+}
+
+static bool assumptions_hold(const Kernel &K, long long E, long long N, long long F)
+{
+    for (const auto &a : K.assumptions) {
+        long long v = a.param == K.E_param ? E : a.param == K.N_param ? N : F;
+        bool ok = true;
+        switch (a.op) {
+        case 0: ok = (v % a.k) == 0; break;
+        case 1: ok = v >= a.k; break;
+        case 2: ok = v > a.k; break;
+        case 3: ok = v <= a.k; break;
+        case 4: ok = v < a.k; break;
+        case 5: ok = v == a.k; break;
+        }
+        if (!ok)
+            return false;
+    }
+    return true;
+}
+
+// True when the assumptions imply E mod m == 0.
+static bool implies_E_multiple_of(const Kernel &K, long long m)
+{
+    for (const auto &a : K.assumptions)
+        if (a.param == K.E_param && a.op == 0 && a.k % m == 0)
+            return true;
+    return false;
+}
+
+// ------------------------------------------------------------------ validation
+
+struct Resolved {
+    int engine, layout, precision;
+    SimtGeom g;
+    int unroll, prefetch, tail_free;
+    int warp_per;  // WARP engine: elements per warp step
+};
+
+static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_variant *v, Resolved &r,
+                         bool need_device)
+{
+    if (!v || v->struct_size != sizeof(lc_variant))
+        return LC_ERR_INVALID_ARGUMENT;
+    if (E < 0 || N < 1 || N > 256 || F < 1 || F > 8)
+        return LC_ERR_INVALID_ARGUMENT;
+    if (K.F_param.empty() && F != 1)
+        return LC_ERR_INVALID_ARGUMENT;
+    if (!assumptions_hold(K, E, N, F))
+        return LC_ERR_ASSUMPTION;
+    if (v->layout != LC_LAYOUT_ELEM_MAJOR && v->layout != LC_LAYOUT_NODE_MAJOR)
+        return LC_ERR_INVALID_VARIANT;
+    if (v->precision < LC_PREC_FP64 || v->precision > LC_PREC_BF16X3)
+        return LC_ERR_INVALID_VARIANT;
+    if (v->tail_free != 0 && v->tail_free != 1)
+        return LC_ERR_INVALID_VARIANT;
+    if (v->ctas_per_sm < 0 || v->ctas_per_sm > 32)
+        return LC_ERR_INVALID_VARIANT;
+    r.engine = v->engine;
+    r.layout = v->layout;
+    r.precision = v->precision;
+    r.unroll = v->unroll;
+    r.prefetch = v->prefetch_smem;
+    r.tail_free = v->tail_free;
+    if (v->tail_free && !implies_E_multiple_of(K, v->tile_e > 0 ? v->tile_e : 1))
+        return LC_ERR_INVALID_VARIANT;  // the guard-free last tile needs "E mod tile_e = 0"
+    const int sms = need_device ? sm_count() : 148;
+    const size_t smem_cap = need_device ? smem_optin_limit() : 232448;
+    if (need_device && (sms <= 0 || smem_cap == 0))
+        return LC_ERR_NO_DEVICE;
+
+    if (v->engine == LC_ENGINE_SIMT) {
+        if (v->precision != LC_PREC_FP32 && v->precision != LC_PREC_FP64)
+            return LC_ERR_INVALID_VARIANT;
+        const int VEC = v->precision == LC_PREC_FP64 ? 2 : 4;
+        const int es = v->precision == LC_PREC_FP64 ? 8 : 4;
+        SimtGeom &g = r.g;
+        g.VEC = VEC;
+        g.RE = v->elems_per_thread;
+        g.RC = v->split_i;
+        if (!(g.RE == VEC || g.RE == 2 * VEC) || !(g.RC == VEC || g.RC == 2 * VEC))
+            return LC_ERR_INVALID_VARIANT;
+        if (!(v->unroll == 1 || v->unroll == 2 || v->unroll == 4 || v->unroll == 8))
+            return LC_ERR_INVALID_VARIANT;
+        if (v->prefetch_smem != 0 && v->prefetch_smem != 1)
+            return LC_ERR_INVALID_VARIANT;
+        if (v->stages != 1)
+            return LC_ERR_INVALID_VARIANT;
+        if (v->tile_e <= 0 || v->tile_e % g.RE != 0)
+            return LC_ERR_INVALID_VARIANT;
+        g.TE = v->tile_e;
+        g.EG = g.TE / g.RE;
+        if (g.EG > 512)
+            return LC_ERR_INVALID_VARIANT;
+        const int C = F * N;
+        const int TEp = v->layout == LC_LAYOUT_NODE_MAJOR ? g.TE : g.TE + VEC;
+        size_t fixed = 0;  // u tile + output staging
+        if (v->prefetch_smem)
+            fixed += (size_t)N * TEp * es;
+        if (v->layout == LC_LAYOUT_ELEM_MAJOR)
+            fixed += (size_t)F * g.TE * N * es;
+        if (fixed + (size_t)N * g.RC * es > smem_cap)
+            return LC_ERR_INVALID_VARIANT;
+        // column groups: enough to cover C, within 512 threads and the shared memory left for D^T
+        const long long cg_smem = (long long)((smem_cap - fixed) / ((size_t)N * g.RC * es));
+        g.CG = (int)std::max<long long>(
+            1, std::min<long long>({(long long)(C + g.RC - 1) / g.RC, (long long)(512 / g.EG), cg_smem}));
+        g.threads = g.EG * g.CG;
+        g.CW = g.CG * g.RC;
+        g.nchunks = (C + g.CW - 1) / g.CW;
+        g.smem = fixed + (size_t)N * g.CW * es;
+        if (g.smem > smem_cap)
+            return LC_ERR_INVALID_VARIANT;
+        g.ntiles = (E + g.TE - 1) / g.TE;
+        long long grid = g.ntiles;
+        if (v->ctas_per_sm > 0)
+            grid = std::min<long long>(grid, (long long)v->ctas_per_sm * sms);
+        if (grid > 0x7fffffffLL)
+            return LC_ERR_INVALID_VARIANT;
+        g.grid = (int)std::max<long long>(grid, 1);
+        return LC_OK;
+    }
+    if (v->engine == LC_ENGINE_WARP) {
+        if (v->precision != LC_PREC_FP32 && v->precision != LC_PREC_FP64)
+            return LC_ERR_INVALID_VARIANT;
+        if (N > (v->precision == LC_PREC_FP64 ? 16 : 32) || F > 4)
+            return LC_ERR_INVALID_VARIANT;
+        const int per = 32 / N;
+        if (v->tile_e <= 0 || v->tile_e % per != 0 || v->tile_e / per > 16)
+            return LC_ERR_INVALID_VARIANT;
+        if (v->unroll != 1 || v->prefetch_smem != 0 || v->stages != 1 || v->elems_per_thread != 1 ||
+            v->split_i != 1)
+            return LC_ERR_INVALID_VARIANT;
+        r.warp_per = per;
+        SimtGeom &g = r.g;
+        g.threads = (v->tile_e / per) * 32;
+        g.TE = v->tile_e;
+        g.ntiles = (E + g.TE - 1) / g.TE;
+        long long grid = g.ntiles;
+        if (v->ctas_per_sm > 0)
+            grid = std::min<long long>(grid, (long long)v->ctas_per_sm * sms);
+        if (grid > 0x7fffffffLL)
+            return LC_ERR_INVALID_VARIANT;
+        g.grid = (int)std::max<long long>(grid, 1);
+        g.smem = 0;
+        return LC_OK;
+    }
+    return LC_ERR_INVALID_VARIANT;
+}
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace lc
+
+using namespace lc;
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+const char *lc_status_string(lc_status s)
+{
+    switch (s) {
+    case LC_OK: return "LC_OK";
+    case LC_ERR_INVALID_ARGUMENT: return "LC_ERR_INVALID_ARGUMENT";
+    case LC_ERR_UNSUPPORTED: return "LC_ERR_UNSUPPORTED";
+    case LC_ERR_INVALID_VARIANT: return "LC_ERR_INVALID_VARIANT";
+    case LC_ERR_ASSUMPTION: return "LC_ERR_ASSUMPTION";
+    case LC_ERR_MISALIGNED: return "LC_ERR_MISALIGNED";
+    case LC_ERR_BUFFER_TOO_SMALL: return "LC_ERR_BUFFER_TOO_SMALL";
+    case LC_ERR_CUDA: return "LC_ERR_CUDA";
+    case LC_ERR_TIMEOUT: return "LC_ERR_TIMEOUT";
+    case LC_ERR_NO_DEVICE: return "LC_ERR_NO_DEVICE";
+    case LC_ERR_NOT_FOUND: return "LC_ERR_NOT_FOUND";
+    }
+    return "LC_ERR_UNKNOWN";
+}
+
+int lc_last_cuda_error(void) { return g_last_cuda_error; }
+
+lc_status lc_kernel_create(const char *domain, const char *instructions, const char *assumptions,
+                           lc_kernel **out)
+{
+    if (!domain || !instructions || !out)
+        return LC_ERR_INVALID_ARGUMENT;
+    Kernel K;
+    std::string why;
+    if (!parse_domain(domain, K, why) || !parse_instruction(instructions, K, why) ||
+        !parse_assumptions(assumptions, K, why))
+        return LC_ERR_UNSUPPORTED;
+    K.domain_text = domain;
+    K.insn_text = instructions;
+    K.assumptions_text = assumptions ? assumptions : "";
+    lc_kernel *h = new (std::nothrow) lc_kernel;
+    if (!h)
+        return LC_ERR_INVALID_ARGUMENT;
+    h->k = std::move(K);
+    *out = h;
+    return LC_OK;
+}
+
+void lc_kernel_destroy(lc_kernel *k) { delete k; }
+
+static void appendf(std::string &s, const char *fmt, ...)
+{
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    s += buf;
+}
+
+lc_status lc_kernel_print(const lc_kernel *kh, const lc_variant *v, char *buf, size_t cap,
+                          size_t *needed)
+{
+    if (!kh)
+        return LC_ERR_INVALID_ARGUMENT;
+    const Kernel &K = kh->k;
+    const bool multi = !K.F_param.empty();
+    const bool node = v && v->struct_size == sizeof(lc_variant) && v->layout == LC_LAYOUT_NODE_MAJOR;
+    const char *ty = !v ? "<runtime>" : v->precision == LC_PREC_FP64 ? "float64" : "float32";
+    const char *F = multi ? K.F_param.c_str() : "1";
+    const char *E = K.E_param.c_str(), *N = K.N_param.c_str();
+    std::string s;
+    const char *rule = "------------------------------------------------------\n";
+    s += rule;
+    s += "KERNEL: element_local_contraction\n";
+    s += rule;
+    s += "ARGUMENTS:\n";
+    appendf(s, "%s: GlobalArg, type: %s, shape: (%s, %s, %s), dim_tags: (stride:%s*%s, stride:%s, stride:1)\n",
+            K.d_name.c_str(), ty, F, N, N, N, N, N);
+    if (multi)
+        appendf(s, "%s: ValueArg, type: int32\n", F);
+    appendf(s, "%s: ValueArg, type: int64\n%s: ValueArg, type: int32\n", E, N);
+    if (node) {
+        appendf(s, "%s: GlobalArg, type: %s, shape: (%s, %s, %s), dim_tags: (stride:%s*%s, stride:1, stride:%s)\n",
+                K.out_name.c_str(), ty, F, E, N, N, E, E);
+        appendf(s, "%s: GlobalArg, type: %s, shape: (%s, %s), dim_tags: (stride:1, stride:%s)\n",
+                K.u_name.c_str(), ty, E, N, E);
+    } else {
+        appendf(s, "%s: GlobalArg, type: %s, shape: (%s, %s, %s), dim_tags: (stride:%s*%s, stride:%s, stride:1)\n",
+                K.out_name.c_str(), ty, F, E, N, E, N, N);
+        appendf(s, "%s: GlobalArg, type: %s, shape: (%s, %s), dim_tags: (stride:%s, stride:1)\n",
+                K.u_name.c_str(), ty, E, N, N);
+    }
+    s += rule;
+    s += "DOMAINS:\n";
+    {
+        std::string params, cons;
+        std::set<std::string> seen;
+        for (size_t k = 0; k < K.inames.size(); ++k) {
+            if (!seen.count(K.bounds[k])) {
+                if (!params.empty())
+                    params += ", ";
+                params += K.bounds[k];
+                seen.insert(K.bounds[k]);
+            }
+            if (!cons.empty())
+                cons += " and ";
+            cons += "0 <= " + K.inames[k] + " < " + K.bounds[k];
+        }
+        std::string names;
+        for (size_t k = 0; k < K.inames.size(); ++k)
+            names += (k ? ", " : "") + K.inames[k];
+        appendf(s, "[%s] -> { [%s] : %s }\n", params.c_str(), names.c_str(), cons.c_str());
+    }
+    if (!K.assumptions.empty()) {
+        s += rule;
+        appendf(s, "ASSUMPTIONS: %s\n", K.assumptions_text.c_str());
+    }
+    s += rule;
+    s += "INSTRUCTIONS:\n";
+    if (multi)
+        appendf(s, "[%s, %s, %s] %s[%s, %s, %s] <- sum(%s, %s[%s, %s, %s]*%s[%s, %s])\n",
+                K.f_iname.c_str(), K.e_iname.c_str(), K.i_iname.c_str(), K.out_name.c_str(),
+                K.f_iname.c_str(), K.e_iname.c_str(), K.i_iname.c_str(), K.j_iname.c_str(),
+                K.d_name.c_str(), K.f_iname.c_str(), K.i_iname.c_str(), K.j_iname.c_str(),
+                K.u_name.c_str(), K.e_iname.c_str(), K.j_iname.c_str());
+    else
+        appendf(s, "[%s, %s] %s[%s, %s] <- sum(%s, %s[%s, %s]*%s[%s, %s])\n", K.e_iname.c_str(),
+                K.i_iname.c_str(), K.out_name.c_str(), K.e_iname.c_str(), K.i_iname.c_str(),
+                K.j_iname.c_str(), K.d_name.c_str(), K.i_iname.c_str(), K.j_iname.c_str(),
+                K.u_name.c_str(), K.e_iname.c_str(), K.j_iname.c_str());
+    if (v && v->struct_size == sizeof(lc_variant)) {
+        const char *eng = v->engine == LC_ENGINE_SIMT ? "simt" : v->engine == LC_ENGINE_TCGEN05 ? "tcgen05" : "warp";
+        const char *prec[] = {"fp64", "fp32", "bf16", "bf16x3"};
+        s += rule;
+        s += "TRANSFORMATIONS:\n";
+        appendf(s, "engine: %s, precision: %s, layout: %s-major\n", eng,
+                (v->precision >= 0 && v->precision <= 3) ? prec[v->precision] : "?",
+                node ? "node" : "element");
+        const char *e = K.e_iname.c_str();
+        appendf(s, "split_iname(%s, %d): %s = %s_inner + %d*%s_outer, %s_outer <= (%s + %d)/%d - 1\n", e,
+                v->tile_e, e, e, v->tile_e, e, e, E, v->tile_e - 1, v->tile_e);
+        if (v->tail_free)
+            appendf(s, "  no guard: assumption %s mod %d = 0\n", E, v->tile_e);
+        else
+            appendf(s, "  guard: %s_inner + %d*%s_outer < %s on the last tile only\n", e, v->tile_e, e, E);
+        appendf(s, "tags: %s_outer -> g.0 (persistent, %d CTAs/SM), ilp(%s_inner) = %d, ilp(%s) = %d, unr(%s) = %d\n",
+                e, v->ctas_per_sm, e, v->elems_per_thread, K.i_iname.c_str(), v->split_i,
+                K.j_iname.c_str(), v->unroll);
+        appendf(s, "add_prefetch(%s): %s, stages: %d\n", K.u_name.c_str(),
+                v->prefetch_smem ? "shared memory" : "none (global loads)", v->stages);
+    }
+    s += rule;
+    if (needed)
+        *needed = s.size() + 1;
+    if (!buf || cap == 0)
+        return LC_ERR_BUFFER_TOO_SMALL;
+    size_t n = std::min(cap - 1, s.size());
+    memcpy(buf, s.data(), n);
+    buf[n] = 0;
+    return n < s.size() ? LC_ERR_BUFFER_TOO_SMALL : LC_OK;
+}
+
+lc_status lc_variant_validate(const lc_kernel *kh, int64_t E, int32_t N, int32_t F, const lc_variant *v)
+{
+    if (!kh)
+        return LC_ERR_INVALID_ARGUMENT;
+    Resolved r;
+    return resolve(kh->k, E, N, F, v, r, false);
+}
+
+lc_status lc_variant_default(const lc_kernel *kh, int64_t E, int32_t N, int32_t F, int32_t layout,
+                             int32_t precision, lc_variant *v)
+{
+    if (!kh || !v)
+        return LC_ERR_INVALID_ARGUMENT;
+    lc_variant d;
+    memset(&d, 0, sizeof d);
+    d.struct_size = sizeof(lc_variant);
+    d.layout = layout;
+    d.precision = precision;
+    d.unroll = 4;
+    d.stages = 1;
+    d.prefetch_smem = 1;
+    d.ctas_per_sm = 0;
+    if (precision == LC_PREC_FP64) {
+        d.engine = LC_ENGINE_SIMT;
+        d.elems_per_thread = 2;
+        d.split_i = 4;
+        d.tile_e = 32;
+    } else if (precision == LC_PREC_FP32) {
+        d.engine = LC_ENGINE_SIMT;
+        d.elems_per_thread = 4;
+        d.split_i = 8;
+        d.tile_e = 64;
+    } else {
+        return LC_ERR_UNSUPPORTED;
+    }
+    // shrink the tile until the shared-memory plan fits
+    while (d.tile_e > d.elems_per_thread && lc_variant_validate(kh, E, N, F, &d) == LC_ERR_INVALID_VARIANT)
+        d.tile_e /= 2;
+    lc_status st = lc_variant_validate(kh, E, N, F, &d);
+    if (st != LC_OK)
+        return st;
+    *v = d;
+    return LC_OK;
+}
+
+lc_status lc_contract(const lc_kernel *kh, const lc_variant *v, const void *D, const void *u, void *out,
+                      int64_t E, int32_t N, int32_t F, void *stream)
+{
+    if (!kh || !v)
+        return LC_ERR_INVALID_ARGUMENT;
+    if (!D || !u || !out)
+        return LC_ERR_INVALID_ARGUMENT;
+    if (!aligned16(D) || !aligned16(u) || !aligned16(out))
+        return LC_ERR_MISALIGNED;
+    Resolved r;
+    lc_status st = resolve(kh->k, E, N, F, v, r, true);
+    if (st != LC_OK)
+        return st;
+    const size_t es = v->precision == LC_PREC_FP64 ? 8 : 4;
+    {
+        // out must not overlap its inputs
+        uintptr_t o0 = (uintptr_t)out, o1 = o0 + (size_t)F * E * N * es;
+        uintptr_t u0 = (uintptr_t)u, u1 = u0 + (size_t)E * N * es;
+        uintptr_t d0 = (uintptr_t)D, d1 = d0 + (size_t)F * N * N * es;
+        if ((o0 < u1 && u0 < o1) || (o0 < d1 && d0 < o1))
+            return LC_ERR_INVALID_ARGUMENT;
+    }
+    int major = 0, minor = 0;
+    if (current_cc(&major, &minor) != 0 || major != 10 || minor != 3)
+        return LC_ERR_NO_DEVICE;
+    if (E == 0)
+        return LC_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (r.engine == LC_ENGINE_SIMT) {
+        SimtArgs a;
+        a.D = D;
+        a.u = u;
+        a.out = out;
+        a.E = E;
+        a.N = N;
+        a.F = F;
+        a.C = F * N;
+        a.TE = r.g.TE;
+        a.EG = r.g.EG;
+        a.CG = r.g.CG;
+        a.CW = r.g.CW;
+        a.nchunks = r.g.nchunks;
+        a.ntiles = r.g.ntiles;
+        a.tail_free = r.tail_free;
+        a.err = error_word();
+        const bool node = r.layout == LC_LAYOUT_NODE_MAJOR;
+        if (r.precision == LC_PREC_FP32)
+            return node ? simt_launch_f32_node(a, r.g, r.unroll, r.prefetch, s)
+                        : simt_launch_f32_elem(a, r.g, r.unroll, r.prefetch, s);
+        return node ? simt_launch_f64_node(a, r.g, r.unroll, r.prefetch, s)
+                    : simt_launch_f64_elem(a, r.g, r.unroll, r.prefetch, s);
+    }
+    if (r.engine == LC_ENGINE_WARP) {
+        WarpArgs a;
+        a.D = D;
+        a.u = u;
+        a.out = out;
+        a.E = E;
+        a.N = N;
+        a.F = F;
+        a.per_warp = r.warp_per;
+        a.ngroups = (E + r.warp_per - 1) / r.warp_per;
+        a.tail_free = r.tail_free;
+        return warp_launch(a, r.layout, r.precision == LC_PREC_FP64, r.g.grid, r.g.threads, s);
+    }
+    return LC_ERR_INVALID_VARIANT;
+}
+
+lc_status lc_contract_host(const lc_kernel *kh, const lc_variant *v, const void *D_host, const void *u_host,
+                           void *out_host, int64_t E, int32_t N, int32_t F, void *D_dev, void *u_dev,
+                           void *out_dev, void *stream)
+{
+    if (!kh || !v || !D_host || !u_host || !out_host || !D_dev || !u_dev || !out_dev)
+        return LC_ERR_INVALID_ARGUMENT;
+    if (v->struct_size != sizeof(lc_variant) || E < 0 || N < 1 || F < 1)
+        return LC_ERR_INVALID_ARGUMENT;
+    Resolved r;
+    lc_status st = resolve(kh->k, E, N, F, v, r, true);
+    if (st != LC_OK)
+        return st;
+    const size_t es = v->precision == LC_PREC_FP64 ? 8 : 4;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(D_dev, D_host, (size_t)F * N * N * es, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(u_dev, u_host, (size_t)E * N * es, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    st = lc_contract(kh, v, D_dev, u_dev, out_dev, E, N, F, stream);
+    if (st != LC_OK)
+        return st;
+    e = cudaMemcpyAsync(out_host, out_dev, (size_t)F * E * N * es, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    return LC_OK;
+}
+
+lc_status lc_device_error(int clear)
+{
+    unsigned int *p = error_word();
+    if (!p)
+        return LC_ERR_NO_DEVICE;
+    unsigned int h = 0;
+    cudaError_t e = cudaMemcpy(&h, p, sizeof h, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    if (clear && h) {
+        unsigned int z = 0;
+        e = cudaMemcpy(p, &z, sizeof z, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess)
+            return cuda_fail(e);
+    }
+    return h ? LC_ERR_TIMEOUT : LC_OK;
+}
+
+lc_status lc_device_info(int32_t *sm, int32_t *major, int32_t *minor)
+{
+    if (!sm || !major || !minor)
+        return LC_ERR_INVALID_ARGUMENT;
+    int n = sm_count();
+    if (n <= 0)
+        return LC_ERR_NO_DEVICE;
+    int a = 0, b = 0;
+    if (current_cc(&a, &b) != 0)
+        return LC_ERR_NO_DEVICE;
+    *sm = n;
+    *major = a;
+    *minor = b;
+    return LC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,86 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "lc.h"
+
+namespace lc {
+
+// Parsed kernel: loop domain + one contraction instruction + assumptions (Section 2.1).
+struct Assumption {
+    std::string param;  // parameter name
+    int op;             // 0: mod k = 0, 1: >=, 2: >, 3: <=, 4: <, 5: =
+    long long k;
+};
+
+struct Kernel {
+    std::vector<std::string> inames;  // as written in the domain
+    std::vector<std::string> bounds;  // parameter bounding each iname
+    std::string out_name, d_name, u_name;
+    std::string f_iname, e_iname, i_iname, j_iname;  // roles ("" for f in the F = 1 form)
+    std::string F_param, E_param, N_param;           // "" for F in the F = 1 form
+    std::vector<Assumption> assumptions;
+    std::string domain_text, insn_text, assumptions_text;
+};
+
+// Launch geometry resolved from a descriptor and a problem size.
+struct SimtGeom {
+    int VEC;       // elements per 16-byte vector
+    int RE, RC;    // register block: elements x columns per thread
+    int EG, CG;    // thread grid: element groups x column groups
+    int TE;        // elements per tile (= EG * RE)
+    int CW;        // columns per chunk (= CG * RC)
+    int nchunks;   // column chunks covering C = F * N
+    int threads;   // EG * CG
+    size_t smem;   // dynamic shared memory bytes
+    long long ntiles;
+    int grid;
+};
+
+struct SimtArgs {
+    const void *D;
+    const void *u;
+    void *out;
+    long long E;
+    int N, F, C;
+    int TE, EG, CG, CW, nchunks;
+    long long ntiles;
+    int tail_free;
+    unsigned int *err;
+};
+
+// Warp-per-element-group kernel for small N.
+struct WarpArgs {
+    const void *D;
+    const void *u;
+    void *out;
+    long long E;
+    int N, F;
+    int per_warp;     // elements handled by one warp per step (32 / N rounded down)
+    long long ngroups;
+    int tail_free;
+};
+
+int sm_count();
+int current_cc(int *major, int *minor);
+unsigned int *error_word();
+lc_status cuda_fail(cudaError_t e);
+size_t smem_optin_limit();
+
+// SIMT launchers (one per element type / layout translation unit).
+lc_status simt_launch_f32_elem(const SimtArgs &a, const SimtGeom &g, int unroll, int prefetch,
+                               cudaStream_t s);
+lc_status simt_launch_f32_node(const SimtArgs &a, const SimtGeom &g, int unroll, int prefetch,
+                               cudaStream_t s);
+lc_status simt_launch_f64_elem(const SimtArgs &a, const SimtGeom &g, int unroll, int prefetch,
+                               cudaStream_t s);
+lc_status simt_launch_f64_node(const SimtArgs &a, const SimtGeom &g, int unroll, int prefetch,
+                               cudaStream_t s);
+lc_status warp_launch(const WarpArgs &a, int layout, int fp64, int grid, int threads, cudaStream_t s);
+
+}  // namespace lc

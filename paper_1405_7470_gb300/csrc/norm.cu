@@ -1,0 +1,124 @@
+// FP64 error norm on the GPU: sums[0] = sum (out - ref)^2, sums[1] = sum ref^2.
+// Two launches with a fixed grid, so the summation order (and the result) is the
+// same on every call: per-block partial sums, then one block adds them in order.
+#include <cuda_runtime.h>
+
+#include "lc_internal.h"
+
+namespace lc {
+
+static constexpr int kNormBlocks = 1024;
+static constexpr int kNormThreads = 256;
+
+__device__ __forceinline__ void block_sum2(double &a, double &b, double *sh)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        sh[2 * w] = a;
+        sh[2 * w + 1] = b;
+    }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        a = l < nw ? sh[2 * l] : 0.0;
+        b = l < nw ? sh[2 * l + 1] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kNormThreads) norm_partial_kernel(const T *__restrict__ out,
+                                                                    const double *__restrict__ ref,
+                                                                    long long n, double *partial)
+{
+    __shared__ double sh[2 * (kNormThreads / 32)];
+    double s0 = 0.0, s1 = 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        const double r = ref[k];
+        const double d = (double)out[k] - r;
+        s0 = fma(d, d, s0);
+        s1 = fma(r, r, s1);
+    }
+    block_sum2(s0, s1, sh);
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = s0;
+        partial[2 * blockIdx.x + 1] = s1;
+    }
+}
+
+__global__ void __launch_bounds__(kNormThreads) norm_final_kernel(const double *__restrict__ partial,
+                                                                  int nblocks, double *sums)
+{
+    __shared__ double sh[2 * (kNormThreads / 32)];
+    double s0 = 0.0, s1 = 0.0;
+    for (int k = threadIdx.x; k < nblocks; k += blockDim.x) {
+        s0 += partial[2 * k];
+        s1 += partial[2 * k + 1];
+    }
+    block_sum2(s0, s1, sh);
+    if (threadIdx.x == 0) {
+        sums[0] = s0;
+        sums[1] = s1;
+    }
+}
+
+size_t norm_workspace_bytes() { return sizeof(double) * 2 * kNormBlocks; }
+
+lc_status norm_launch(const void *out, int dtype, const double *ref, long long n, double *sums,
+                      double *partial, cudaStream_t s)
+{
+    if (dtype == LC_DTYPE_F32)
+        norm_partial_kernel<float><<<kNormBlocks, kNormThreads, 0, s>>>(static_cast<const float *>(out), ref,
+                                                                        n, partial);
+    else
+        norm_partial_kernel<double><<<kNormBlocks, kNormThreads, 0, s>>>(static_cast<const double *>(out),
+                                                                         ref, n, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    norm_final_kernel<<<1, kNormThreads, 0, s>>>(partial, kNormBlocks, sums);
+    e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    return LC_OK;
+}
+
+}  // namespace lc
+
+extern "C" {
+
+lc_status lc_error_norm_workspace_size(int64_t n, size_t *bytes)
+{
+    if (n < 0 || !bytes)
+        return LC_ERR_INVALID_ARGUMENT;
+    *bytes = lc::norm_workspace_bytes();
+    return LC_OK;
+}
+
+lc_status lc_error_norm(const void *out, int32_t out_dtype, const double *ref, int64_t n, double *sums,
+                        void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (!out || !ref || !sums || !workspace || n < 0)
+        return LC_ERR_INVALID_ARGUMENT;
+    if (out_dtype != LC_DTYPE_F32 && out_dtype != LC_DTYPE_F64)
+        return LC_ERR_INVALID_ARGUMENT;
+    if (workspace_bytes < lc::norm_workspace_bytes())
+        return LC_ERR_BUFFER_TOO_SMALL;
+    if (((uintptr_t)workspace & 15u) || ((uintptr_t)ref & 7u) || ((uintptr_t)sums & 7u) ||
+        ((uintptr_t)out & (out_dtype == LC_DTYPE_F64 ? 7u : 3u)))
+        return LC_ERR_MISALIGNED;
+    return lc::norm_launch(out, out_dtype, ref, n, sums, static_cast<double *>(workspace),
+                           (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,225 @@
+"""Thin ctypes binding of the C ABI declared in include/lc.h.
+
+Argument marshalling only: every step of the contraction runs in the CUDA
+library. Torch is used for device memory (``data_ptr``) and streams
+(``cuda_stream``). There is no CPU fallback: if ``liblc.so`` is missing or fails
+to load, every call raises.
+
+The raw entry points keep the C names (``lc_kernel_create``, ``lc_contract``,
+...); ``Kernel``, ``Variant`` and ``contract`` wrap them for torch tensors.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "liblc.so")
+
+LC_OK = 0
+STATUS = {
+    0: "LC_OK", 1: "LC_ERR_INVALID_ARGUMENT", 2: "LC_ERR_UNSUPPORTED", 3: "LC_ERR_INVALID_VARIANT",
+    4: "LC_ERR_ASSUMPTION", 5: "LC_ERR_MISALIGNED", 6: "LC_ERR_BUFFER_TOO_SMALL", 7: "LC_ERR_CUDA",
+    8: "LC_ERR_TIMEOUT", 9: "LC_ERR_NO_DEVICE", 10: "LC_ERR_NOT_FOUND",
+}
+ENGINE = {"simt": 0, "tcgen05": 1, "warp": 2}
+LAYOUT = {"elem": 0, "node": 1}
+PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16x3": 3}
+DTYPE_F32, DTYPE_F64 = 0, 1
+
+DOMAIN = "{ [f,e,i,j]: 0<=f<F and 0<=e<E and 0<=i,j<N }"
+INSTRUCTION = "out[f,e,i] = sum(j, D[f,i,j]*u[e,j])"
+
+
+class LcError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)}")
+
+
+class lc_variant(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32)] + [
+        (n, ctypes.c_int32) for n in (
+            "engine", "layout", "precision", "tile_e", "elems_per_thread", "split_i", "unroll",
+            "prefetch_smem", "tail_free", "stages", "ctas_per_sm")
+    ]
+
+
+# Exported symbols and their signatures (argtypes, restype).
+_P, _I32, _I64, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+_VP = ctypes.POINTER(lc_variant)
+SIGNATURES = {
+    "lc_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "lc_last_cuda_error": ([], ctypes.c_int),
+    "lc_kernel_create": ([ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(_P)], ctypes.c_int),
+    "lc_kernel_destroy": ([_P], None),
+    "lc_kernel_print": ([_P, _VP, ctypes.c_char_p, _SZ, ctypes.POINTER(_SZ)], ctypes.c_int),
+    "lc_variant_default": ([_P, _I64, _I32, _I32, _I32, _I32, _VP], ctypes.c_int),
+    "lc_variant_validate": ([_P, _I64, _I32, _I32, _VP], ctypes.c_int),
+    "lc_contract": ([_P, _VP, _P, _P, _P, _I64, _I32, _I32, _P], ctypes.c_int),
+    "lc_contract_host": ([_P, _VP, _P, _P, _P, _I64, _I32, _I32, _P, _P, _P, _P], ctypes.c_int),
+    "lc_device_error": ([ctypes.c_int], ctypes.c_int),
+    "lc_error_norm_workspace_size": ([_I64, ctypes.POINTER(_SZ)], ctypes.c_int),
+    "lc_error_norm": ([_P, _I32, _P, _I64, _P, _P, _SZ, _P], ctypes.c_int),
+    "lc_device_info": ([ctypes.POINTER(_I32)] * 3, ctypes.c_int),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str | None = None):
+    """Load liblc.so (raises if it is missing: there is no fallback path)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(f"CUDA library not built: {p} (run __graft_entry__.build())")
+            lib = ctypes.CDLL(p)
+            for name, (args, res) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def check(st: int, what: str = "lc"):
+    if st != LC_OK:
+        raise LcError(st, what)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Kernel:
+    """Immutable kernel handle: loop domain + instruction + assumptions (Section 2.1)."""
+
+    def __init__(self, domain: str = DOMAIN, instruction: str = INSTRUCTION, assumptions: str | None = None):
+        lib = load()
+        h = ctypes.c_void_p()
+        st = lib.lc_kernel_create(domain.encode(), instruction.encode(),
+                                  assumptions.encode() if assumptions else None, ctypes.byref(h))
+        check(st, "lc_kernel_create")
+        self._h = h
+        self._lib = lib
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.lc_kernel_destroy(self._h)
+            self._h = None
+
+    def print(self, variant: "lc_variant | None" = None) -> str:
+        need = ctypes.c_size_t(0)
+        vp = ctypes.byref(variant) if variant is not None else None
+        self._lib.lc_kernel_print(self._h, vp, None, 0, ctypes.byref(need))
+        buf = ctypes.create_string_buffer(need.value)
+        check(self._lib.lc_kernel_print(self._h, vp, buf, need.value, ctypes.byref(need)), "lc_kernel_print")
+        return buf.value.decode()
+
+
+def Variant(engine="simt", layout="elem", precision="fp32", tile_e=64, elems_per_thread=4, split_i=8,
+            unroll=4, prefetch_smem=1, tail_free=0, stages=1, ctas_per_sm=0) -> lc_variant:
+    v = lc_variant()
+    v.struct_size = ctypes.sizeof(lc_variant)
+    v.engine = ENGINE[engine] if isinstance(engine, str) else engine
+    v.layout = LAYOUT[layout] if isinstance(layout, str) else layout
+    v.precision = PRECISION[precision] if isinstance(precision, str) else precision
+    v.tile_e, v.elems_per_thread, v.split_i, v.unroll = tile_e, elems_per_thread, split_i, unroll
+    v.prefetch_smem, v.tail_free, v.stages, v.ctas_per_sm = prefetch_smem, tail_free, stages, ctas_per_sm
+    return v
+
+
+def variant_dict(v: lc_variant) -> dict:
+    inv = lambda m, x: next((k for k, val in m.items() if val == x), x)
+    return dict(engine=inv(ENGINE, v.engine), layout=inv(LAYOUT, v.layout), precision=inv(PRECISION, v.precision),
+                tile_e=v.tile_e, elems_per_thread=v.elems_per_thread, split_i=v.split_i, unroll=v.unroll,
+                prefetch_smem=v.prefetch_smem, tail_free=v.tail_free, stages=v.stages, ctas_per_sm=v.ctas_per_sm)
+
+
+def variant_default(kernel: Kernel, E: int, N: int, F: int, layout="elem", precision="fp32") -> lc_variant:
+    v = lc_variant()
+    check(load().lc_variant_default(kernel.handle, E, N, F, LAYOUT[layout], PRECISION[precision],
+                                    ctypes.byref(v)), "lc_variant_default")
+    return v
+
+
+def variant_validate(kernel: Kernel, E: int, N: int, F: int, v: lc_variant) -> int:
+    return load().lc_variant_validate(kernel.handle, E, N, F, ctypes.byref(v))
+
+
+def lc_contract(kernel: Kernel, v: lc_variant, D_ptr: int, u_ptr: int, out_ptr: int, E: int, N: int, F: int,
+                stream_ptr: int) -> int:
+    return load().lc_contract(kernel.handle, ctypes.byref(v), D_ptr, u_ptr, out_ptr, E, N, F, stream_ptr)
+
+
+def contract(kernel: Kernel, v: lc_variant, D, u, out=None, stream=None):
+    """Enqueue the contraction on torch CUDA tensors. Returns ``out``.
+
+    D: (F, N, N). u: (E, N) element-major or (N, E) node-major (per v.layout).
+    out: (F, E, N) or (F, N, E); allocated with torch if not given.
+    """
+    import torch
+    F, N, _ = D.shape
+    node = v.layout == LAYOUT["node"]
+    E = u.shape[1] if node else u.shape[0]
+    if out is None:
+        out = torch.empty((F, N, E) if node else (F, E, N), dtype=u.dtype, device=u.device)
+    for t in (D, u, out):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("D, u and out must be contiguous CUDA tensors")
+    st = lc_contract(kernel, v, D.data_ptr(), u.data_ptr(), out.data_ptr(), E, N, F, _stream_ptr(stream))
+    check(st, "lc_contract")
+    return out
+
+
+def contract_host(kernel: Kernel, v: lc_variant, D_host, u_host, out_host, D_dev, u_dev, out_dev, stream=None):
+    """Host arrays in, host array out, through the caller's device buffers (lc_contract_host)."""
+    F, N, _ = D_host.shape
+    node = v.layout == LAYOUT["node"]
+    E = u_host.shape[1] if node else u_host.shape[0]
+    st = load().lc_contract_host(kernel.handle, ctypes.byref(v), D_host.data_ptr(), u_host.data_ptr(),
+                                 out_host.data_ptr(), E, N, F, D_dev.data_ptr(), u_dev.data_ptr(),
+                                 out_dev.data_ptr(), _stream_ptr(stream))
+    check(st, "lc_contract_host")
+    return out_host
+
+
+def device_error(clear: bool = True) -> int:
+    return load().lc_device_error(1 if clear else 0)
+
+
+def error_norm(out, ref, stream=None):
+    """Relative Frobenius error ||out - ref|| / ||ref|| computed in FP64 on the GPU."""
+    import torch
+    lib = load()
+    n = out.numel()
+    assert ref.numel() == n and ref.dtype == torch.float64
+    ws = ctypes.c_size_t(0)
+    check(lib.lc_error_norm_workspace_size(n, ctypes.byref(ws)), "lc_error_norm_workspace_size")
+    work = torch.empty(ws.value // 8 + 2, dtype=torch.float64, device=out.device)
+    sums = torch.empty(2, dtype=torch.float64, device=out.device)
+    dt = DTYPE_F64 if out.dtype == torch.float64 else DTYPE_F32
+    check(lib.lc_error_norm(out.data_ptr(), dt, ref.data_ptr(), n, sums.data_ptr(), work.data_ptr(), ws.value,
+                            _stream_ptr(stream)), "lc_error_norm")
+    s = sums.cpu().tolist()
+    return (s[0] / s[1]) ** 0.5 if s[1] > 0 else s[0] ** 0.5
+
+
+def device_info():
+    a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    check(load().lc_device_info(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "lc_device_info")
+    return dict(sm_count=a.value, cc=(b.value, c.value))

@@ -1,0 +1,151 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports every
+symbol include/lc.h declares, parses the loop-domain / instruction / assumption
+texts of Section 2.1, prints kernels, and validates descriptors before any launch.
+"""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1405_7470_gb300 import lc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1405_7470_gb300 import build
+    build()
+    return lc.load()
+
+
+def header_functions():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"^\s*(?:const\s+)?[\w]+\s*\*?\s*(lc_\w+)\s*\(", text, flags=re.M))
+    return names
+
+
+def test_exports_every_declared_symbol(lib):
+    names = header_functions()
+    assert "lc_contract" in names and "lc_kernel_create" in names
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+    # and the binding knows every one of them
+    assert names <= set(lc.SIGNATURES), names - set(lc.SIGNATURES)
+
+
+def _create(lib, dom, insn, asm=None):
+    h = ctypes.c_void_p()
+    st = lib.lc_kernel_create(dom.encode(), insn.encode(), asm.encode() if asm else None, ctypes.byref(h))
+    if st == 0:
+        lib.lc_kernel_destroy(h)
+    return st
+
+
+@pytest.mark.parametrize("dom,insn,asm", [
+    ("{ [f,e,i,j]: 0<=f<F and 0<=e<E and 0<=i,j<N }", "out[f,e,i] = sum(j, D[f,i,j]*u[e,j])", None),
+    ("[F,E,N] -> {[f,e,i,j]: 0<=f<F and 0<=e<E and 0<=i<N and 0<=j<N}", "out[f,e,i]=sum(j,u[e,j]*D[f,i,j])", None),
+    ("{ [e,i,j,f]: e>=0 and E>e and 0<=i,j<=N-1 and 0<=f<F }", "res[f,e,i] = sum(j, A[f,i,j]*x[e,j])",
+     "E mod 128 = 0 and N >= 4"),
+    ("{ [e,i,j]: 0<=e<E and 0<=i,j<N }", "out[e,i] = sum(j, D[i,j]*u[e,j])", "N > 0"),
+    ("{ [k,a,b]: 0<=k<nel and 0<=a,b<nn }", "y[k,a] = sum(b, u[k,b]*M[a,b])", None),
+])
+def test_parse_accepts(lib, dom, insn, asm):
+    assert _create(lib, dom, insn, asm) == 0
+
+
+@pytest.mark.parametrize("dom,insn,asm", [
+    ("{ [f,e,i,j]: 1<=f<F and 0<=e<E and 0<=i,j<N }", "out[f,e,i] = sum(j, D[f,i,j]*u[e,j])", None),  # lower bound 1
+    ("{ [f,e,i,j]: 0<=f<F and 0<=e<E and 0<=i<N and 0<=j<M }", "out[f,e,i] = sum(j, D[f,i,j]*u[e,j])", None),  # non-square
+    ("{ [f,e,i,j]: 0<=f<F and 0<=e<E and 0<=i,j<N }", "out[f,e,i] = sum(j, D[f,j,i]*u[e,j])", None),  # transposed D
+    ("{ [f,e,i,j]: 0<=f<F and 0<=e<E and 0<=i,j<N }", "out[f,e,i] = sum(i, D[f,i,j]*u[e,j])", None),
+    ("{ [f,e,i,j]: 0<=f<F and 0<=e<E and 0<=i,j<N }", "out[f,e,i] = D[f,i,j]*u[e,j]", None),  # no reduction
+    ("{ [f,e,i,j]: 0<=f<F and 0<=e<E and 0<=i,j<N }", "out[f,e,i] = sum(j, D[f,i,j]*u[e,j])", "Q mod 4 = 0"),
+    ("{ [f,e,i,j]: 0<=f<F and 0<=e<E and 0<=i,j<N }", "out[f,e,i] = sum(j, D[f,i,j]*u[e,j])", "E mod 0 = 0"),
+    ("{ [f,e,i,j]: 0<=f<F and 0<=e<E }", "out[f,e,i] = sum(j, D[f,i,j]*u[e,j])", None),  # unbounded inames
+    ("{ [f,e,i,j]: 0<=f<F and 0<=e<E and 0<=i,j<N", "out[f,e,i] = sum(j, D[f,i,j]*u[e,j])", None),  # no brace
+    ("{ [f,e,i,j]: 0<=f<F and 0<=e<E and 0<=i,j<N }", "out[f,e,i] = sum(j, D[f,i,j]*D[e,j])", None),  # same array
+])
+def test_parse_rejects(lib, dom, insn, asm):
+    assert _create(lib, dom, insn, asm) == 2
+
+
+def test_null_arguments(lib):
+    h = ctypes.c_void_p()
+    assert lib.lc_kernel_create(None, b"x", None, ctypes.byref(h)) == 1
+    assert lib.lc_status_string(8) == b"LC_ERR_TIMEOUT"
+    assert lib.lc_status_string(99) == b"LC_ERR_UNKNOWN"
+
+
+def test_print_sections(lib):
+    k = lc.Kernel(assumptions="E mod 64 = 0")
+    text = k.print()
+    for sec in ("ARGUMENTS:", "DOMAINS:", "ASSUMPTIONS: E mod 64 = 0", "INSTRUCTIONS:",
+                "out[f, e, i] <- sum(j, D[f, i, j]*u[e, j])"):
+        assert sec in text
+    v = lc.Variant(tile_e=64, tail_free=1, layout="node")
+    t2 = k.print(v)
+    assert "split_iname(e, 64)" in t2 and "no guard: assumption E mod 64 = 0" in t2
+    assert "u: GlobalArg, type: float32, shape: (E, N), dim_tags: (stride:1, stride:E)" in t2
+    # a too-small buffer reports the needed size and truncates safely
+    need = ctypes.c_size_t(0)
+    buf = ctypes.create_string_buffer(10)
+    assert lib.lc_kernel_print(k.handle, None, buf, 10, ctypes.byref(need)) == 6
+    assert need.value == len(text) + 1 and len(buf.value) == 9
+
+
+def test_variant_validation_rules(lib):
+    k = lc.Kernel()
+    ok = lc.Variant()
+    assert lc.variant_validate(k, 1 << 21, 35, 3, ok) == 0
+    bad = [
+        dict(elems_per_thread=3), dict(split_i=16), dict(unroll=3), dict(prefetch_smem=2), dict(tile_e=66),
+        dict(tail_free=1), dict(stages=0), dict(engine="tcgen05", precision="fp32"), dict(precision="bf16"),
+        dict(ctas_per_sm=-1), dict(tile_e=4096 * 8, elems_per_thread=8),
+    ]
+    for b in bad:
+        assert lc.variant_validate(k, 1 << 21, 35, 3, lc.Variant(**b)) == 3, b
+    assert lc.variant_validate(k, 1 << 21, 300, 3, ok) == 1      # N out of range
+    assert lc.variant_validate(k, -1, 35, 3, ok) == 1
+    # shared-memory plan too large for one CTA
+    assert lc.variant_validate(k, 1 << 21, 256, 8, lc.Variant(tile_e=1024, elems_per_thread=8)) == 3
+    # warp engine only for N <= 32 and one warp-multiple tile
+    w = lc.Variant(engine="warp", tile_e=8 * 4, elems_per_thread=1, split_i=1, unroll=1, prefetch_smem=0)
+    assert lc.variant_validate(k, 1000, 4, 3, w) == 0
+    assert lc.variant_validate(k, 1000, 40, 3, w) == 3
+    # single-operator kernels take F = 1 only
+    k1 = lc.Kernel("{ [e,i,j]: 0<=e<E and 0<=i,j<N }", "out[e,i] = sum(j, D[i,j]*u[e,j])")
+    assert lc.variant_validate(k1, 100, 20, 1, ok) == 0
+    assert lc.variant_validate(k1, 100, 20, 2, ok) == 1
+
+
+def test_assumptions_checked_against_sizes(lib):
+    k = lc.Kernel(assumptions="E mod 128 = 0 and N >= 8 and F <= 4")
+    v = lc.Variant()
+    assert lc.variant_validate(k, 1024, 35, 3, v) == 0
+    assert lc.variant_validate(k, 1000, 35, 3, v) == 4
+    assert lc.variant_validate(k, 1024, 4, 3, v) == 4
+    assert lc.variant_validate(k, 1024, 35, 5, v) == 4
+
+
+def test_contract_rejects_before_launch(lib):
+    k = lc.Kernel()
+    v = lc.Variant()
+    assert lc.lc_contract(k, v, 0, 0, 0, 10, 35, 3, 0) == 1           # null pointers
+    assert lc.lc_contract(k, v, 0x1000, 0x2008, 0x30000, 10, 35, 3, 0) == 5  # misaligned u
+    bad = lc.Variant(unroll=5)
+    assert lc.lc_contract(k, bad, 0x1000, 0x2000, 0x30000, 10, 35, 3, 0) in (3, 9)
+
+
+def test_default_variant_fits(lib):
+    k = lc.Kernel()
+    for E, N, F in [(1 << 21, 35, 3), (1 << 20, 84, 4), (4096, 165, 4), (100, 4, 1), (1 << 23, 256, 8)]:
+        for layout in ("elem", "node"):
+            v = lc.variant_default(k, E, N, F, layout, "fp32")
+            assert lc.variant_validate(k, E, N, F, v) == 0
