@@ -190,6 +190,7 @@ def main():
     ap.add_argument("--variant", default="default", help="JSON descriptor fields or 'default'")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--E", type=int, default=0, help="override the workload's element count (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -197,7 +198,10 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.E:
+        wl["E"] = args.E
+        wl["desc"] += f" (E overridden to {args.E})"
 
     if args.impl == "reference":
         if rank != 0:
@@ -220,11 +224,11 @@ def main():
 
     E, N, F = wl["E"], wl["N"], wl["F"]
     if args.workload == "precision":
-        D, u = synth.precision_sweep()
+        D, u = synth.precision_sweep(E=E)
     elif args.workload == "fp64_single":
-        D, u = synth.fp64_single()
+        D, u = synth.fp64_single(E=E)
     else:
-        D, u = synth.fp32_three()
+        D, u = synth.fp32_three(E=E)
     u_in = synth.to_node_major(u) if args.layout == "node" else u
     kernel = lc.Kernel() if F > 1 else lc.Kernel("{ [e,i,j]: 0<=e<E and 0<=i,j<N }",
                                                   "out[e,i] = sum(j, D[i,j]*u[e,j])")

@@ -662,7 +662,7 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
             return LC_ERR_INVALID_VARIANT;
         if (v->prefetch_smem != 0 && v->prefetch_smem != 1)
             return LC_ERR_INVALID_VARIANT;
-        if (v->stages != 1)
+        if (v->stages < 1 || v->stages > 2 || (!v->prefetch_smem && v->stages != 1))
             return LC_ERR_INVALID_VARIANT;
         if (v->tile_e <= 0 || v->tile_e % g.RE != 0)
             return LC_ERR_INVALID_VARIANT;
@@ -670,25 +670,51 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         g.EG = g.TE / g.RE;
         if (g.EG > 512)
             return LC_ERR_INVALID_VARIANT;
+        g.stages = v->stages;
+        const bool node = v->layout == LC_LAYOUT_NODE_MAJOR;
         const int C = F * N;
-        const int TEp = v->layout == LC_LAYOUT_NODE_MAJOR ? g.TE : g.TE + VEC;
-        size_t fixed = 0;  // u tile + output staging
+        size_t fixed = 16;  // mbarriers + u tiles + output staging
         if (v->prefetch_smem)
-            fixed += (size_t)N * TEp * es;
-        if (v->layout == LC_LAYOUT_ELEM_MAJOR)
+            fixed += node ? (size_t)g.stages * N * g.TE * es
+                          : (size_t)N * (g.TE + VEC) * es + (size_t)g.stages * g.TE * N * es;
+        if (!node)
             fixed += (size_t)F * g.TE * N * es;
-        if (fixed + (size_t)N * g.RC * es > smem_cap)
+        // Warp shape WE x WC and column groups CG (a multiple of WC): the fewest padded
+        // columns within 512 threads and the shared memory left for D^T.
+        const int ncg = (C + g.RC - 1) / g.RC;
+        const int wcs[6] = {4, 2, 8, 1, 16, 32};
+        long long best_waste = -1;
+        for (int wc : wcs) {
+            const int we = 32 / wc;
+            if (g.EG % we != 0)
+                continue;
+            if (fixed + (size_t)N * g.RC * wc * es > smem_cap)
+                continue;
+            const long long cg_smem = (long long)((smem_cap - fixed) / ((size_t)N * g.RC * es));
+            long long cg = ((ncg + wc - 1) / wc) * (long long)wc;
+            cg = std::min<long long>(cg, (512 / g.EG) / wc * (long long)wc);
+            cg = std::min<long long>(cg, cg_smem / wc * (long long)wc);
+            if (cg < wc)
+                continue;
+            const long long cw = cg * g.RC;
+            const long long nch = (C + cw - 1) / cw;
+            const long long waste = nch * cw - C + (nch - 1) * 4;  // extra chunks reload D
+            if (best_waste < 0 || waste < best_waste) {
+                best_waste = waste;
+                g.WC = wc;
+                g.CG = (int)cg;
+            }
+        }
+        if (best_waste < 0)
             return LC_ERR_INVALID_VARIANT;
-        // column groups: enough to cover C, within 512 threads and the shared memory left for D^T
-        const long long cg_smem = (long long)((smem_cap - fixed) / ((size_t)N * g.RC * es));
-        g.CG = (int)std::max<long long>(
-            1, std::min<long long>({(long long)(C + g.RC - 1) / g.RC, (long long)(512 / g.EG), cg_smem}));
         g.threads = g.EG * g.CG;
         g.CW = g.CG * g.RC;
         g.nchunks = (C + g.CW - 1) / g.CW;
         g.smem = fixed + (size_t)N * g.CW * es;
-        if (g.smem > smem_cap)
+        if (g.smem > smem_cap || g.threads > 512 || g.threads % 32 != 0)
             return LC_ERR_INVALID_VARIANT;
+        g.bulk = v->prefetch_smem && (!node || E % VEC == 0);
+        g.bulk_store = !node && ((E * (long long)N) % VEC == 0);
         g.ntiles = (E + g.TE - 1) / g.TE;
         long long grid = g.ntiles;
         if (v->ctas_per_sm > 0)
@@ -916,14 +942,16 @@ lc_status lc_variant_default(const lc_kernel *kh, int64_t E, int32_t N, int32_t 
     d.ctas_per_sm = 0;
     if (precision == LC_PREC_FP64) {
         d.engine = LC_ENGINE_SIMT;
-        d.elems_per_thread = 2;
+        d.elems_per_thread = 4;
         d.split_i = 4;
-        d.tile_e = 32;
+        d.tile_e = 64;
+        d.stages = 2;
     } else if (precision == LC_PREC_FP32) {
         d.engine = LC_ENGINE_SIMT;
-        d.elems_per_thread = 4;
-        d.split_i = 8;
+        d.elems_per_thread = 8;
+        d.split_i = 4;
         d.tile_e = 64;
+        d.stages = 2;
     } else {
         return LC_ERR_UNSUPPORTED;
     }
@@ -942,7 +970,8 @@ lc_status lc_contract(const lc_kernel *kh, const lc_variant *v, const void *D, c
 {
     if (!kh || !v)
         return LC_ERR_INVALID_ARGUMENT;
-    if (!D || !u || !out)
+    // an empty batch may come with null u / out (zero-size allocations)
+    if (!D || (E > 0 && (!u || !out)))
         return LC_ERR_INVALID_ARGUMENT;
     if (!aligned16(D) || !aligned16(u) || !aligned16(out))
         return LC_ERR_MISALIGNED;
@@ -979,6 +1008,10 @@ lc_status lc_contract(const lc_kernel *kh, const lc_variant *v, const void *D, c
         a.CG = r.g.CG;
         a.CW = r.g.CW;
         a.nchunks = r.g.nchunks;
+        a.WC = r.g.WC;
+        a.stages = r.g.stages;
+        a.bulk = r.g.bulk;
+        a.bulk_store = r.g.bulk_store;
         a.ntiles = r.g.ntiles;
         a.tail_free = r.tail_free;
         a.err = error_word();

@@ -33,6 +33,10 @@ struct SimtGeom {
     int VEC;       // elements per 16-byte vector
     int RE, RC;    // register block: elements x columns per thread
     int EG, CG;    // thread grid: element groups x column groups
+    int WC;        // lanes of a warp along columns (the warp is (32 / WC) x WC)
+    int stages;    // u tiles in flight (prefetch ring depth)
+    int bulk;      // u tiles fetched by the bulk-copy engine
+    int bulk_store;  // element-major output tiles written by bulk stores
     int TE;        // elements per tile (= EG * RE)
     int CW;        // columns per chunk (= CG * RC)
     int nchunks;   // column chunks covering C = F * N
@@ -49,6 +53,7 @@ struct SimtArgs {
     long long E;
     int N, F, C;
     int TE, EG, CG, CW, nchunks;
+    int WC, stages, bulk, bulk_store;
     long long ntiles;
     int tail_free;
     unsigned int *err;

@@ -6,22 +6,28 @@
 //                            (Eq. 1); the last tile is guarded unless tail_free.
 //   ilp on e_in / on i       register block of RE elements x RC output columns per
 //                            thread (columns c = f*N + i, all F operators fused).
+//                            A warp is a WE x WC grid of lanes (WE*WC = 32) so that
+//                            shared-memory operand loads are broadcasts.
 //   unr on j                 UNR-fold unrolled reduction loop.
 //   vec                      16-byte vector loads and stores along the contiguous axis.
-//   add_prefetch(u)          PREFETCH: the u tile is staged in shared memory,
-//                            transposed to [j][e]; otherwise loaded from global
-//                            memory inside the j loop.
+//   add_prefetch(u)          PREFETCH: u tiles are fetched by the bulk-copy engine
+//                            (cp.async.bulk, mbarrier completion) into a ring of
+//                            `stages` shared-memory buffers, ahead of the compute;
+//                            otherwise u is read from global memory inside the j loop.
 //   precompute(D)            D^T staged once per CTA in shared memory, columns
 //                            permuted so each thread's RC columns are contiguous.
-//   layout tags              element-major u[E][N], out[F][E][N]: outputs are staged
-//                            in shared memory and written as contiguous [TE][N] runs;
-//                            node-major u[N][E], out[F][N][E]: coalesced vector stores
-//                            straight from registers.
+//   layout tags              element-major u[E][N], out[F][E][N]: the u tile is
+//                            transposed to [j][e] in shared memory and each operator's
+//                            output tile [TE][N] is written by one bulk store;
+//                            node-major u[N][E], out[F][N][E]: the fetched tile is
+//                            already [j][e] and outputs leave registers as coalesced
+//                            16-byte stores.
 #pragma once
 
 #include <cuda_runtime.h>
 
 #include "lc_internal.h"
+#include "tma.cuh"
 
 namespace lc {
 
@@ -47,30 +53,47 @@ __global__ void __launch_bounds__(512) simt_contract_kernel(SimtArgs a)
     constexpr int QC = RC / VEC;  // column vectors per thread
     static_assert(RE % VEC == 0 && RC % VEC == 0, "register block must be whole vectors");
     constexpr bool NODE = LAYOUT == LC_LAYOUT_NODE_MAJOR;
+    constexpr int ES = (int)sizeof(T);
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const int N = a.N, F = a.F, C = a.C, TE = a.TE, EG = a.EG, CG = a.CG, CW = a.CW;
     const long long E = a.E;
+    const int S = a.stages;
     const T *__restrict__ D = static_cast<const T *>(a.D);
     const T *__restrict__ u = static_cast<const T *>(a.u);
     T *__restrict__ out = static_cast<T *>(a.out);
     const int tid = threadIdx.x;
     const int nthr = blockDim.x;
-    // Lane order: element groups fastest for node-major (coalesced stores along e),
-    // column groups fastest for element-major (conflict-free staging along i).
-    const int eg = NODE ? tid % EG : tid / CG;
-    const int cg = NODE ? tid / EG : tid % CG;
-    const int TEp = NODE ? TE : TE + VEC;  // padded row of the transposed u tile
+    const int lane = tid & 31, warp = tid >> 5;
+    const int WC = a.WC, WE = 32 / WC;
+    const int nwe = EG / WE;
+    const int eg = (warp % nwe) * WE + lane % WE;
+    const int cg = (warp / nwe) * WC + lane / WE;
+    const int TEp = TE + VEC;  // padded row of the transposed element-major tile
 
-    T *Ds = reinterpret_cast<T *>(smem_raw);                 // [N][CW]
-    T *uT = Ds + (size_t)N * CW;                             // [N][TEp]   (PREFETCH)
-    T *ost = uT + (PREFETCH ? (size_t)N * TEp : 0);          // [F][TE][N] (element-major)
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);  // two mbarriers
+    T *Ds = reinterpret_cast<T *>(smem_raw + 16);              // [N][CW]
+    T *p = Ds + (size_t)N * CW;
+    T *uT = nullptr, *stage = nullptr, *ost = nullptr;
+    if (PREFETCH) {
+        if (NODE) {
+            stage = p;  // S x [N][TE]
+            p += (size_t)S * N * TE;
+        } else {
+            uT = p;  // [N][TEp]
+            p += (size_t)N * TEp;
+            stage = p;  // S x [TE*N]
+            p += (size_t)S * TE * N;
+        }
+    }
+    if (!NODE)
+        ost = p;  // [F][TE][N]
 
     // precompute(D): Ds[j][cg*RC + m] = D[f][i][j] with c = ch*CW + cg + m*CG = f*N + i.
     auto load_D = [&](int ch) {
         for (int idx = tid; idx < N * CW; idx += nthr) {
-            int j = idx / CW, p = idx - j * CW;
-            int g = p / RC, m = p - g * RC;
+            int j = idx / CW, q = idx - j * CW;
+            int g = q / RC, m = q - g * RC;
             int c = ch * CW + g + m * CG;
             T val = T(0);
             if (c < C) {
@@ -80,59 +103,112 @@ __global__ void __launch_bounds__(512) simt_contract_kernel(SimtArgs a)
             Ds[idx] = val;
         }
     };
-    if (a.nchunks == 1) {
+
+    const bool bulk = PREFETCH && a.bulk;
+    if (bulk && tid == 0) {
+        for (int s = 0; s < S; ++s)
+            mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    if (a.nchunks == 1)
         load_D(0);
+    __syncthreads();
+
+    // Warp 0 fetches tile `t` into ring slot `buf`.
+    auto issue = [&](long long t, int buf) {
+        const long long e0 = t * (long long)TE;
+        const int TEv = (int)min((long long)TE, E - e0);
+        if (NODE) {
+            const uint32_t bytes = (uint32_t)TEv * ES;  // a multiple of 16 when bulk is set
+            if (lane == 0)
+                mbar_arrive_expect_tx(&bars[buf], bytes * (uint32_t)N);
+            __syncwarp();
+            T *dst = stage + (size_t)buf * N * TE;
+            for (int j = lane; j < N; j += 32)
+                bulk_g2s(dst + (size_t)j * TE, u + (size_t)j * E + e0, bytes, &bars[buf]);
+        } else if (lane == 0) {
+            const uint32_t bytes = ((uint32_t)TEv * N * ES) & ~15u;
+            mbar_arrive_expect_tx(&bars[buf], bytes);
+            if (bytes)
+                bulk_g2s(stage + (size_t)buf * TE * N, u + e0 * N, bytes, &bars[buf]);
+        }
+    };
+    if (bulk && warp == 0) {
+        for (int s = 0; s < S; ++s) {
+            const long long t = blockIdx.x + (long long)s * gridDim.x;
+            if (t < a.ntiles)
+                issue(t, s);
+        }
     }
 
-    for (long long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    int k = 0;
+    for (long long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++k) {
         const long long e0 = tile * (long long)TE;
         const bool full = a.tail_free || (e0 + TE <= E);
         const int TEv = full ? TE : (int)(E - e0);
-        __syncthreads();  // previous tile finished with uT / ost
+        const int buf = bulk ? k % S : 0;
+        const T *ut = nullptr;  // [N][ldu] tile the compute reads
+        int ldu = 0;
 
         if (PREFETCH) {
-            if (NODE) {
-                // rows u[j][e0 : e0+TE] -> uT[j][0:TE]
-                const int QT = TE / VEC;
-                const bool vec_ok = full && (E % VEC == 0);
-                for (int idx = tid; idx < N * QT; idx += nthr) {
-                    int j = idx / QT, q = idx - j * QT;
-                    const T *src = u + (size_t)j * E + e0 + q * VEC;
-                    V val;
-                    if (vec_ok) {
-                        val = *reinterpret_cast<const V *>(src);
-                    } else {
-                        T *pv = reinterpret_cast<T *>(&val);
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v)
-                            pv[v] = (q * VEC + v < TEv) ? src[v] : T(0);
-                    }
-                    *reinterpret_cast<V *>(uT + (size_t)j * TEp + q * VEC) = val;
+            if (bulk) {
+                const bool ok = mbar_wait(&bars[buf], (uint32_t)((k / S) & 1));
+                if (!__syncthreads_and(ok)) {
+                    if (tid == 0)
+                        atomicOr(a.err, 1u);
+                    break;
                 }
             } else {
-                // contiguous block u[e0 : e0+TEv][0:N] -> uT[j][e], zero-filled tail
-                const T *src = u + e0 * N;
-                const int total = TEv * N;
-                int e = tid / N, j = tid - (tid / N) * N;
-                const int de = nthr / N, dj = nthr - (nthr / N) * N;
-                for (int k = tid; k < total; k += nthr) {
-                    uT[(size_t)j * TEp + e] = src[k];
-                    e += de;
-                    j += dj;
-                    if (j >= N) {
-                        j -= N;
-                        ++e;
-                    }
-                }
-                if (!full) {
-                    for (int idx = tid; idx < N * (TE - TEv); idx += nthr) {
-                        int j2 = idx / (TE - TEv), e2 = TEv + idx % (TE - TEv);
-                        uT[(size_t)j2 * TEp + e2] = T(0);
+                // no bulk path (node-major with E % VEC != 0): cooperative synchronous loads
+                __syncthreads();
+                if (NODE) {
+                    for (int idx = tid; idx < N * TE; idx += nthr) {
+                        int j = idx / TE, e = idx - j * TE;
+                        stage[idx] = e < TEv ? u[(size_t)j * E + e0 + e] : T(0);
                     }
                 }
             }
+            if (NODE) {
+                ut = stage + (size_t)buf * N * TE;
+                ldu = TE;
+            } else {
+                // transpose the [TE][N] tile into uT[j][e]; lanes walk e so the writes are
+                // conflict-free; the part the bulk copy did not cover comes from global memory
+                const T *st = stage + (size_t)buf * TE * N;
+                const int total = TEv * N;
+                const int kb = bulk ? (int)((((uint32_t)total * ES) & ~15u) / ES) : 0;
+                int j = tid / TE, e = tid - (tid / TE) * TE;
+                const int dj = nthr / TE, de = nthr - (nthr / TE) * TE;
+                for (int idx = tid; idx < N * TE; idx += nthr) {
+                    const int kk = e * N + j;
+                    uT[(size_t)j * TEp + e] = kk < kb ? st[kk] : (kk < total ? u[e0 * N + kk] : T(0));
+                    e += de;
+                    j += dj;
+                    if (e >= TE) {
+                        e -= TE;
+                        ++j;
+                    }
+                }
+                ut = uT;
+                ldu = TEp;
+            }
+            if (!NODE) {
+                if (tid == 0)
+                    bulk_wait_read0();  // previous tile's output stores have read ost
+                fence_async_smem();
+            }
+            __syncthreads();
+            if (!NODE && bulk && warp == 0) {
+                // stage[buf] is consumed: fetch the tile S steps ahead into it
+                const long long nt = tile + (long long)S * gridDim.x;
+                if (nt < a.ntiles)
+                    issue(nt, buf);
+            }
+        } else if (!NODE) {
+            if (tid == 0)
+                bulk_wait_read0();
+            __syncthreads();
         }
-        __syncthreads();
 
         for (int ch = 0; ch < a.nchunks; ++ch) {
             if (a.nchunks > 1) {
@@ -147,14 +223,15 @@ __global__ void __launch_bounds__(512) simt_contract_kernel(SimtArgs a)
                 for (int y = 0; y < RC; ++y)
                     acc[x][y] = T(0);
 
+            const T *dcol = Ds + cg * RC;
 #pragma unroll UNR
             for (int j = 0; j < N; ++j) {
                 T av[RE], bv[RC];
                 if (PREFETCH) {
+                    const T *urow = ut + (size_t)j * ldu + eg * VEC;
 #pragma unroll
                     for (int q = 0; q < QE; ++q)
-                        *reinterpret_cast<V *>(&av[q * VEC]) =
-                            *reinterpret_cast<const V *>(uT + (size_t)j * TEp + (eg + q * EG) * VEC);
+                        *reinterpret_cast<V *>(&av[q * VEC]) = *reinterpret_cast<const V *>(urow + q * EG * VEC);
                 } else if (NODE) {
 #pragma unroll
                     for (int q = 0; q < QE; ++q) {
@@ -179,8 +256,7 @@ __global__ void __launch_bounds__(512) simt_contract_kernel(SimtArgs a)
                 }
 #pragma unroll
                 for (int r = 0; r < QC; ++r)
-                    *reinterpret_cast<V *>(&bv[r * VEC]) =
-                        *reinterpret_cast<const V *>(Ds + (size_t)j * CW + cg * RC + r * VEC);
+                    *reinterpret_cast<V *>(&bv[r * VEC]) = *reinterpret_cast<const V *>(dcol + (size_t)j * CW + r * VEC);
 #pragma unroll
                 for (int x = 0; x < RE; ++x)
 #pragma unroll
@@ -188,7 +264,6 @@ __global__ void __launch_bounds__(512) simt_contract_kernel(SimtArgs a)
                         acc[x][y] = fma(av[x], bv[y], acc[x][y]);
             }
 
-            // Stores.
 #pragma unroll
             for (int y = 0; y < RC; ++y) {
                 const int c = ch * CW + cg + y * CG;
@@ -225,26 +300,45 @@ __global__ void __launch_bounds__(512) simt_contract_kernel(SimtArgs a)
             }
         }
 
-        if (!NODE) {
-            // out[f][e0 : e0+TEv][0:N] is one contiguous run per operator.
+        if (NODE) {
+            if (bulk) {
+                __syncthreads();  // every warp is done reading stage[buf]
+                if (warp == 0) {
+                    const long long nt = tile + (long long)S * gridDim.x;
+                    if (nt < a.ntiles)
+                        issue(nt, buf);
+                }
+            }
+        } else {
+            // out[f][e0 : e0+TEv][0:N] is one contiguous run per operator
+            fence_async_smem();
             __syncthreads();
             const int total = TEv * N;
-            for (int f = 0; f < F; ++f) {
-                const T *src = ost + (size_t)f * TE * N;
-                T *dst = out + ((size_t)f * E + e0) * N;
-                const bool vec_ok = ((((size_t)f * E + e0) * N) % VEC) == 0;
-                int done = 0;
-                if (vec_ok) {
-                    const int nv = total / VEC;
-                    for (int k = tid; k < nv; k += nthr)
-                        reinterpret_cast<V *>(dst)[k] = reinterpret_cast<const V *>(src)[k];
-                    done = nv * VEC;
+            if (a.bulk_store && ((total * ES) & 15) == 0) {
+                if (tid == 0) {
+                    for (int f = 0; f < F; ++f)
+                        bulk_s2g(out + ((size_t)f * E + e0) * N, ost + (size_t)f * TE * N, (uint32_t)total * ES);
+                    bulk_commit();
                 }
-                for (int k = done + tid; k < total; k += nthr)
-                    dst[k] = src[k];
+            } else {
+                for (int f = 0; f < F; ++f) {
+                    const T *src = ost + (size_t)f * TE * N;
+                    T *dst = out + ((size_t)f * E + e0) * N;
+                    int done = 0;
+                    if (((((size_t)f * E + e0) * N) % VEC) == 0) {
+                        const int nv = total / VEC;
+                        for (int q = tid; q < nv; q += nthr)
+                            reinterpret_cast<V *>(dst)[q] = reinterpret_cast<const V *>(src)[q];
+                        done = nv * VEC;
+                    }
+                    for (int q = done + tid; q < total; q += nthr)
+                        dst[q] = src[q];
+                }
             }
         }
     }
+    if (!NODE && tid == 0)
+        bulk_wait0();
 }
 
 // Host-side dispatch over the compiled instances of one element type and layout.

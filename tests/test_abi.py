@@ -106,7 +106,7 @@ def test_variant_validation_rules(lib):
     assert lc.variant_validate(k, 1 << 21, 35, 3, ok) == 0
     bad = [
         dict(elems_per_thread=3), dict(split_i=16), dict(unroll=3), dict(prefetch_smem=2), dict(tile_e=66),
-        dict(tail_free=1), dict(stages=0), dict(engine="tcgen05", precision="fp32"), dict(precision="bf16"),
+        dict(tail_free=1), dict(stages=0), dict(stages=3), dict(stages=2, prefetch_smem=0), dict(engine="tcgen05", precision="fp32"), dict(precision="bf16"),
         dict(ctas_per_sm=-1), dict(tile_e=4096 * 8, elems_per_thread=8),
     ]
     for b in bad:

@@ -59,9 +59,15 @@ SHAPES = [(1000, 35, 3), (517, 20, 1), (333, 7, 2), (64, 84, 4), (1, 5, 1), (129
 
 def simt_variants(fp64):
     V = 2 if fp64 else 4
-    for re_, rc, unr, pf, ctas in itertools.product((V, 2 * V), (V, 2 * V), (1, 4), (0, 1), (0, 2)):
-        yield dict(engine="simt", elems_per_thread=re_, split_i=rc, unroll=unr, prefetch_smem=pf,
+    for re_, rc, unr, (pf, st), ctas in itertools.product((V, 2 * V), (V, 2 * V), (1, 4),
+                                                         ((0, 1), (1, 1), (1, 2)), (0, 2)):
+        yield dict(engine="simt", elems_per_thread=re_, split_i=rc, unroll=unr, prefetch_smem=pf, stages=st,
                    tile_e=re_ * 16, ctas_per_sm=ctas)
+    # other tile shapes: narrow tiles (wide warps along columns) and wide tiles
+    for te, re_ in ((4 * V, V), (8 * V, 2 * V), (64 * V, V)):
+        for pf, st in ((0, 1), (1, 2)):
+            yield dict(engine="simt", elems_per_thread=re_, split_i=2 * V, unroll=2, prefetch_smem=pf, stages=st,
+                       tile_e=te, ctas_per_sm=1)
 
 
 @pytest.mark.parametrize("layout", ["elem", "node"])
