@@ -611,6 +611,8 @@ static bool implies_E_multiple_of(const Kernel &K, long long m)
 struct Resolved {
     int engine, layout, precision;
     SimtGeom g;
+    TcArgs tc;
+    int tc_grid;
     int unroll, prefetch, tail_free;
     int warp_per;  // WARP engine: elements per warp step
 };
@@ -668,7 +670,8 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
             return LC_ERR_INVALID_VARIANT;
         g.TE = v->tile_e;
         g.EG = g.TE / g.RE;
-        if (g.EG > 512)
+        const int max_threads = g.RE * g.RC >= 64 ? 256 : 512;  // register budget per thread
+        if (g.EG > max_threads)
             return LC_ERR_INVALID_VARIANT;
         g.stages = v->stages;
         const bool node = v->layout == LC_LAYOUT_NODE_MAJOR;
@@ -692,7 +695,7 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
                 continue;
             const long long cg_smem = (long long)((smem_cap - fixed) / ((size_t)N * g.RC * es));
             long long cg = ((ncg + wc - 1) / wc) * (long long)wc;
-            cg = std::min<long long>(cg, (512 / g.EG) / wc * (long long)wc);
+            cg = std::min<long long>(cg, (max_threads / g.EG) / wc * (long long)wc);
             cg = std::min<long long>(cg, cg_smem / wc * (long long)wc);
             if (cg < wc)
                 continue;
@@ -711,7 +714,7 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         g.CW = g.CG * g.RC;
         g.nchunks = (C + g.CW - 1) / g.CW;
         g.smem = fixed + (size_t)N * g.CW * es;
-        if (g.smem > smem_cap || g.threads > 512 || g.threads % 32 != 0)
+        if (g.smem > smem_cap || g.threads > max_threads || g.threads % 32 != 0)
             return LC_ERR_INVALID_VARIANT;
         g.bulk = v->prefetch_smem && (!node || E % VEC == 0);
         g.bulk_store = !node && ((E * (long long)N) % VEC == 0);
@@ -722,6 +725,75 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         if (grid > 0x7fffffffLL)
             return LC_ERR_INVALID_VARIANT;
         g.grid = (int)std::max<long long>(grid, 1);
+        return LC_OK;
+    }
+    if (v->engine == LC_ENGINE_TCGEN05) {
+        if (v->precision != LC_PREC_BF16 && v->precision != LC_PREC_BF16X3)
+            return LC_ERR_INVALID_VARIANT;
+        if (v->tile_e != 128 || v->elems_per_thread != 1 || v->unroll != 1 || v->prefetch_smem != 1)
+            return LC_ERR_INVALID_VARIANT;
+        if (v->stages < 1 || v->stages > 2 || v->split_i < 0 || v->split_i > F || v->ctas_per_sm > 1)
+            return LC_ERR_INVALID_VARIANT;
+        const bool node = v->layout == LC_LAYOUT_NODE_MAJOR;
+        const int NT = v->precision == LC_PREC_BF16X3 ? 3 : 1;
+        TcArgs &t = r.tc;
+        memset(&t, 0, sizeof t);
+        t.N = N;
+        t.F = F;
+        t.E = E;
+        t.Kp = (N + 15) / 16 * 16;
+        t.KB = t.Kp % 64 == 0 ? 64 : (t.Kp % 32 == 0 ? 32 : 16);
+        t.nkb = t.Kp / t.KB;
+        t.stages = v->stages;
+        const size_t W = 2 * (size_t)t.KB;
+        auto plan = [&](int G, TcArgs &q) -> bool {
+            q.G = G;
+            q.CB = G * N;
+            q.CBp = (q.CB + 15) / 16 * 16;
+            if (q.CBp > 256)
+                return false;
+            q.tmem_cols = 32;
+            while (q.tmem_cols < q.CBp)
+                q.tmem_cols *= 2;
+            size_t off = 0;
+            off += (size_t)NT * q.nkb * q.CBp * W;  // B terms
+            off += (size_t)NT * q.nkb * 128 * W;    // A terms
+            q.off_stage = (unsigned)off;
+            off += (size_t)q.stages * 128 * N * 4;
+            q.off_out = (unsigned)off;
+            if (!node)
+                off += (size_t)G * 128 * N * 4;
+            off = (off + 15) / 16 * 16;
+            q.off_bar = (unsigned)off;
+            off += 64;
+            // alignment slack; at least 120 KB so one CTA holds an SM (and its tensor memory)
+            q.smem_bytes = (unsigned)std::max<size_t>(off + 1024, 120 * 1024);
+            return q.smem_bytes <= smem_cap;
+        };
+        int G = v->split_i;
+        if (G == 0) {
+            for (int g = F; g >= 1; --g) {
+                TcArgs q = t;
+                if (plan(g, q)) {
+                    G = g;
+                    break;
+                }
+            }
+            if (G == 0)
+                return LC_ERR_INVALID_VARIANT;
+        }
+        if (!plan(G, t))
+            return LC_ERR_INVALID_VARIANT;
+        t.nblocks = (F + G - 1) / G;
+        t.ntiles = (E + 127) / 128;
+        t.bulk_u = node ? (E % 4 == 0) : 1;
+        t.bulk_store = !node && ((E * (long long)N) % 4 == 0);
+        long long work = t.ntiles * t.nblocks;
+        long long grid = std::min<long long>(work, (long long)sms);
+        grid = std::max<long long>(grid / t.nblocks * t.nblocks, t.nblocks);
+        if (grid > 0x7fffffffLL)
+            return LC_ERR_INVALID_VARIANT;
+        r.tc_grid = (int)grid;
         return LC_OK;
     }
     if (v->engine == LC_ENGINE_WARP) {
@@ -953,7 +1025,19 @@ lc_status lc_variant_default(const lc_kernel *kh, int64_t E, int32_t N, int32_t 
         d.tile_e = 64;
         d.stages = 2;
     } else {
-        return LC_ERR_UNSUPPORTED;
+        d.engine = LC_ENGINE_TCGEN05;
+        d.tile_e = 128;
+        d.elems_per_thread = 1;
+        d.split_i = 0;
+        d.unroll = 1;
+        d.stages = 2;
+        if (lc_variant_validate(kh, E, N, F, &d) != LC_OK)
+            d.stages = 1;
+        lc_status st = lc_variant_validate(kh, E, N, F, &d);
+        if (st != LC_OK)
+            return st;
+        *v = d;
+        return LC_OK;
     }
     // shrink the tile until the shared-memory plan fits
     while (d.tile_e > d.elems_per_thread && lc_variant_validate(kh, E, N, F, &d) == LC_ERR_INVALID_VARIANT)
@@ -1021,6 +1105,14 @@ lc_status lc_contract(const lc_kernel *kh, const lc_variant *v, const void *D, c
                         : simt_launch_f32_elem(a, r.g, r.unroll, r.prefetch, s);
         return node ? simt_launch_f64_node(a, r.g, r.unroll, r.prefetch, s)
                     : simt_launch_f64_elem(a, r.g, r.unroll, r.prefetch, s);
+    }
+    if (r.engine == LC_ENGINE_TCGEN05) {
+        TcArgs a = r.tc;
+        a.D = static_cast<const float *>(D);
+        a.u = static_cast<const float *>(u);
+        a.out = static_cast<float *>(out);
+        a.err = error_word();
+        return tc_launch(a, r.layout, r.precision == LC_PREC_BF16X3 ? 3 : 1, r.tc_grid, s);
     }
     if (r.engine == LC_ENGINE_WARP) {
         WarpArgs a;

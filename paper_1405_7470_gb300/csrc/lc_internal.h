@@ -71,6 +71,27 @@ struct WarpArgs {
     int tail_free;
 };
 
+// Tensor-core kernel (tcgen05): one column block of G operators per CTA.
+struct TcArgs {
+    const float *D;
+    const float *u;
+    float *out;
+    long long E;
+    int N, F;
+    int G;          // operators per column block
+    int nblocks;    // column blocks (ceil(F / G))
+    int CB, CBp;    // columns per block (G * N) and the MMA N (CB rounded up to 16)
+    int Kp, KB, nkb;  // K padded to 16, K-block width (16/32/64 -> 32/64/128-byte swizzle), blocks
+    int tmem_cols;  // columns per accumulator (power of two >= CBp)
+    int stages;     // u stage buffers (1 or 2)
+    long long ntiles;
+    int bulk_u, bulk_store;
+    unsigned int *err;
+    unsigned int off_stage, off_out, off_bar, smem_bytes;
+};
+
+lc_status tc_launch(const TcArgs &a, int layout, int nterms, int grid, cudaStream_t s);
+
 int sm_count();
 int current_cc(int *major, int *minor);
 unsigned int *error_word();

@@ -4,10 +4,11 @@
 // The descriptor's transformations (Section 2.4) map onto this template:
 //   split_iname(e, TE)       one tile of TE elements per CTA step, e = e_in + TE*e_out
 //                            (Eq. 1); the last tile is guarded unless tail_free.
-//   ilp on e_in / on i       register block of RE elements x RC output columns per
-//                            thread (columns c = f*N + i, all F operators fused).
-//                            A warp is a WE x WC grid of lanes (WE*WC = 32) so that
-//                            shared-memory operand loads are broadcasts.
+//   ilp on e_in / on i       register block of RE consecutive elements x RC output
+//                            columns per thread (columns c = f*N + i, all F operators
+//                            fused). A warp is a WE x WC grid of lanes (WE*WC = 32) so
+//                            that shared-memory operand loads are broadcasts; operand
+//                            addresses advance by one pointer increment per j.
 //   unr on j                 UNR-fold unrolled reduction loop.
 //   vec                      16-byte vector loads and stores along the contiguous axis.
 //   add_prefetch(u)          PREFETCH: u tiles are fetched by the bulk-copy engine
@@ -25,6 +26,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "lc_internal.h"
 #include "tma.cuh"
@@ -44,8 +47,11 @@ struct VecT<double> {
     static constexpr int n = 2;
 };
 
+// Threads per CTA allowed for a register block (the 8 x 8 FP32 block needs > 128 registers).
+__host__ __device__ constexpr int simt_max_threads(int re, int rc) { return re * rc >= 64 ? 256 : 512; }
+
 template <typename T, int RE, int RC, int UNR, int LAYOUT, bool PREFETCH>
-__global__ void __launch_bounds__(512) simt_contract_kernel(SimtArgs a)
+__global__ void __launch_bounds__(simt_max_threads(RE, RC)) simt_contract_kernel(SimtArgs a)
 {
     constexpr int VEC = VecT<T>::n;
     using V = typename VecT<T>::type;
@@ -141,6 +147,20 @@ __global__ void __launch_bounds__(512) simt_contract_kernel(SimtArgs a)
         }
     }
 
+    // Output offsets of this thread's RC columns c = f*N + i (chunk 0; recomputed per
+    // chunk only when the columns do not fit one chunk).
+    using Off = typename std::conditional<NODE, long long, int>::type;
+    Off coff[RC];
+    auto col_offsets = [&](int ch) {
+#pragma unroll
+        for (int y = 0; y < RC; ++y) {
+            const int c = ch * CW + cg + y * CG;
+            const int f = c / N, i = c - f * N;
+            coff[y] = c >= C ? Off(-1) : (NODE ? Off(((long long)f * N + i) * E) : Off(f * TE * N + i));
+        }
+    };
+    col_offsets(0);
+
     int k = 0;
     for (long long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++k) {
         const long long e0 = tile * (long long)TE;
@@ -179,14 +199,26 @@ __global__ void __launch_bounds__(512) simt_contract_kernel(SimtArgs a)
                 const int kb = bulk ? (int)((((uint32_t)total * ES) & ~15u) / ES) : 0;
                 int j = tid / TE, e = tid - (tid / TE) * TE;
                 const int dj = nthr / TE, de = nthr - (nthr / TE) * TE;
-                for (int idx = tid; idx < N * TE; idx += nthr) {
-                    const int kk = e * N + j;
-                    uT[(size_t)j * TEp + e] = kk < kb ? st[kk] : (kk < total ? u[e0 * N + kk] : T(0));
-                    e += de;
-                    j += dj;
-                    if (e >= TE) {
-                        e -= TE;
-                        ++j;
+                if (kb == N * TE) {
+                    for (int idx = tid; idx < N * TE; idx += nthr) {
+                        uT[j * TEp + e] = st[e * N + j];
+                        e += de;
+                        j += dj;
+                        if (e >= TE) {
+                            e -= TE;
+                            ++j;
+                        }
+                    }
+                } else {
+                    for (int idx = tid; idx < N * TE; idx += nthr) {
+                        const int kk = e * N + j;
+                        uT[j * TEp + e] = kk < kb ? st[kk] : (kk < total ? u[e0 * N + kk] : T(0));
+                        e += de;
+                        j += dj;
+                        if (e >= TE) {
+                            e -= TE;
+                            ++j;
+                        }
                     }
                 }
                 ut = uT;
@@ -214,6 +246,7 @@ __global__ void __launch_bounds__(512) simt_contract_kernel(SimtArgs a)
             if (a.nchunks > 1) {
                 __syncthreads();
                 load_D(ch);
+                col_offsets(ch);
                 __syncthreads();
             }
             T acc[RE][RC];
@@ -223,40 +256,40 @@ __global__ void __launch_bounds__(512) simt_contract_kernel(SimtArgs a)
                 for (int y = 0; y < RC; ++y)
                     acc[x][y] = T(0);
 
-            const T *dcol = Ds + cg * RC;
+            const T *dp = Ds + cg * RC;
+            const T *up = PREFETCH ? ut + eg * RE : nullptr;
+            const long long eb0 = e0 + (long long)eg * RE;  // this thread's first element
 #pragma unroll UNR
             for (int j = 0; j < N; ++j) {
                 T av[RE], bv[RC];
                 if (PREFETCH) {
-                    const T *urow = ut + (size_t)j * ldu + eg * VEC;
 #pragma unroll
                     for (int q = 0; q < QE; ++q)
-                        *reinterpret_cast<V *>(&av[q * VEC]) = *reinterpret_cast<const V *>(urow + q * EG * VEC);
+                        *reinterpret_cast<V *>(&av[q * VEC]) = *reinterpret_cast<const V *>(up + q * VEC);
+                    up += ldu;
                 } else if (NODE) {
+                    const T *src = u + (size_t)j * E + eb0;
 #pragma unroll
                     for (int q = 0; q < QE; ++q) {
-                        const long long eb = e0 + (long long)(eg + q * EG) * VEC;
-                        const T *src = u + (size_t)j * E + eb;
                         if (full && (E % VEC == 0)) {
-                            *reinterpret_cast<V *>(&av[q * VEC]) = __ldg(reinterpret_cast<const V *>(src));
+                            *reinterpret_cast<V *>(&av[q * VEC]) = __ldg(reinterpret_cast<const V *>(src + q * VEC));
                         } else {
 #pragma unroll
                             for (int v = 0; v < VEC; ++v)
-                                av[q * VEC + v] = (eb + v < E) ? __ldg(src + v) : T(0);
+                                av[q * VEC + v] = (eb0 + q * VEC + v < E) ? __ldg(src + q * VEC + v) : T(0);
                         }
                     }
                 } else {
 #pragma unroll
-                    for (int q = 0; q < QE; ++q)
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) {
-                            const long long e = e0 + (long long)(eg + q * EG) * VEC + v;
-                            av[q * VEC + v] = (full || e < E) ? __ldg(u + e * N + j) : T(0);
-                        }
+                    for (int x = 0; x < RE; ++x) {
+                        const long long e = eb0 + x;
+                        av[x] = (full || e < E) ? __ldg(u + e * N + j) : T(0);
+                    }
                 }
 #pragma unroll
                 for (int r = 0; r < QC; ++r)
-                    *reinterpret_cast<V *>(&bv[r * VEC]) = *reinterpret_cast<const V *>(dcol + (size_t)j * CW + r * VEC);
+                    *reinterpret_cast<V *>(&bv[r * VEC]) = *reinterpret_cast<const V *>(dp + r * VEC);
+                dp += CW;
 #pragma unroll
                 for (int x = 0; x < RE; ++x)
 #pragma unroll
@@ -264,38 +297,39 @@ __global__ void __launch_bounds__(512) simt_contract_kernel(SimtArgs a)
                         acc[x][y] = fma(av[x], bv[y], acc[x][y]);
             }
 
+            if (NODE) {
+                const bool vec_ok = full && (E % VEC == 0);
 #pragma unroll
-            for (int y = 0; y < RC; ++y) {
-                const int c = ch * CW + cg + y * CG;
-                if (c >= C)
-                    continue;
-                const int f = c / N, i = c - f * N;
-                if (NODE) {
-                    T *orow = out + ((size_t)f * N + i) * E;
+                for (int y = 0; y < RC; ++y) {
+                    if (coff[y] < 0)
+                        continue;
+                    T *orow = out + coff[y] + eb0;
 #pragma unroll
                     for (int q = 0; q < QE; ++q) {
-                        const long long eb = e0 + (long long)(eg + q * EG) * VEC;
-                        if (full && (E % VEC == 0)) {
+                        if (vec_ok) {
                             V val;
                             T *pv = reinterpret_cast<T *>(&val);
 #pragma unroll
                             for (int v = 0; v < VEC; ++v)
                                 pv[v] = acc[q * VEC + v][y];
-                            *reinterpret_cast<V *>(orow + eb) = val;
+                            *reinterpret_cast<V *>(orow + q * VEC) = val;
                         } else {
 #pragma unroll
                             for (int v = 0; v < VEC; ++v)
-                                if (eb + v < E)
-                                    orow[eb + v] = acc[q * VEC + v][y];
+                                if (eb0 + q * VEC + v < E)
+                                    orow[q * VEC + v] = acc[q * VEC + v][y];
                         }
                     }
-                } else {
-                    T *o = ost + (size_t)f * TE * N + i;
+                }
+            } else {
+                T *o = ost + eg * RE * N;
 #pragma unroll
-                    for (int q = 0; q < QE; ++q)
+                for (int x = 0; x < RE; ++x) {
 #pragma unroll
-                        for (int v = 0; v < VEC; ++v)
-                            o[(size_t)((eg + q * EG) * VEC + v) * N] = acc[q * VEC + v][y];
+                    for (int y = 0; y < RC; ++y)
+                        if (coff[y] >= 0)
+                            o[coff[y]] = acc[x][y];
+                    o += N;
                 }
             }
         }

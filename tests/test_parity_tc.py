@@ -1,0 +1,127 @@
+"""GPU parity of the tcgen05 tensor-core paths (BF16, three-term split BF16X3) against
+the CPU FP64 oracle.
+
+Bars:
+  * integer-valued inputs (exact in bf16, all partial sums exact in FP32): bit-exact;
+  * random inputs: each output within an FP32-accumulation bound of the oracle's exact
+    result for the same reduced-precision operands (contract_bf16 / contract_bf16x3),
+    and the relative Frobenius error against the exact FP64 result at most 1e-2 (BF16)
+    or 1e-6 (BF16X3);
+  * sentinel elements around every output stay untouched.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_util import CanaryOut, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1405_7470_gb300 import lc as lcmod
+    lcmod.load()
+    return lcmod
+
+
+def run(lc, kernel, v, D, u, layout):
+    import torch
+    F, N, _ = D.shape
+    E = u.shape[1] if layout == "node" else u.shape[0]
+    co = CanaryOut((F, N, E) if layout == "node" else (F, E, N), np.float32)
+    lc.contract(kernel, v, to_dev(D), to_dev(u), co.out)
+    torch.cuda.synchronize()
+    assert lc.device_error() == 0
+    assert co.intact(), "write outside the output"
+    return co.out.cpu().numpy().astype(np.float64)
+
+
+def accum_bound(D, u, layout, prec):
+    """|err| <= 2 * (products + 2) * 2^-24 * sum |terms| (FP32 accumulation of the kept products)."""
+    N = D.shape[-1]
+    npairs = 6 if prec == "bf16x3" else 1
+    mag = oracle.contract(np.abs(D.astype(np.float64)), np.abs(u.astype(np.float64)), layout)
+    return 2.0 * (npairs * N + 2) * 2.0 ** -24 * mag * 1.01 + 1e-30
+
+
+SHAPES = [(1000, 35, 3), (333, 84, 4), (517, 20, 1), (64, 4, 2), (1, 5, 1), (300, 16, 3), (129, 120, 2),
+          (4099, 10, 3)]
+
+
+@pytest.mark.parametrize("layout", ["elem", "node"])
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
+def test_integer_inputs_bit_exact(lc, layout, prec):
+    kernel = lc.Kernel()
+    for E, N, F in SHAPES:
+        D, u = synth.integer_operands(E, N, F, seed=E + N)
+        uu = synth.to_node_major(u) if layout == "node" else u
+        for stages in (1, 2):
+            v = lc.Variant(engine="tcgen05", layout=layout, precision=prec, tile_e=128, elems_per_thread=1,
+                           split_i=0, unroll=1, prefetch_smem=1, stages=stages)
+            if lc.variant_validate(kernel, E, N, F, v) != 0:
+                continue
+            got = run(lc, kernel, v, D, uu, layout)
+            assert np.array_equal(got, oracle.contract(D, uu, layout)), (E, N, F, stages)
+
+
+@pytest.mark.parametrize("layout", ["elem", "node"])
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
+def test_random_inputs_within_bounds(lc, layout, prec):
+    kernel = lc.Kernel()
+    for si, (E, N, F) in enumerate(SHAPES):
+        D, u = synth.operands(E, N, F, np.float32, seed=200 + si, scale_exp=3.0 if si % 2 else None)
+        uu = synth.to_node_major(u) if layout == "node" else u
+        v = lc.variant_default(kernel, E, N, F, layout, prec)
+        got = run(lc, kernel, v, D, uu, layout)
+        target = oracle.contract_bf16x3(D, uu, layout) if prec == "bf16x3" else oracle.contract_bf16(D, uu, layout)
+        # the operand terms as the kernel sees them
+        if prec == "bf16x3":
+            Ds, us = oracle.bf16_split3(D), oracle.bf16_split3(uu)
+            Dm = np.abs(Ds[0]) + np.abs(Ds[1]) + np.abs(Ds[2])
+            um = np.abs(us[0]) + np.abs(us[1]) + np.abs(us[2])
+        else:
+            Dm, um = np.abs(oracle.bf16_round(D)), np.abs(oracle.bf16_round(uu))
+        bound = accum_bound(Dm, um, layout, prec)
+        assert np.all(np.abs(got - target) <= bound), (E, N, F, float(np.max(np.abs(got - target) / bound)))
+        err = oracle.rel_fro_error(got, oracle.contract(D, uu, layout))
+        assert err <= (1e-6 if prec == "bf16x3" else 1e-2), (E, N, F, err)
+        if prec == "bf16" and E * N > 1000:
+            assert err > 1e-4  # operand rounding to bf16 really happens
+
+
+@pytest.mark.parametrize("split", [1, 2])
+def test_column_blocks_split_operators(lc, split):
+    """Operators split over CTA column blocks (split_i = operators per block)."""
+    kernel = lc.Kernel()
+    D, u = synth.operands(700, 84, 4, np.float32, seed=5)
+    v = lc.Variant(engine="tcgen05", precision="bf16x3", tile_e=128, elems_per_thread=1, split_i=split,
+                   unroll=1, prefetch_smem=1, stages=1)
+    assert lc.variant_validate(kernel, 700, 84, 4, v) == 0
+    got = run(lc, kernel, v, D, u, "elem")
+    assert oracle.rel_fro_error(got, oracle.contract(D, u)) <= 1e-6
+
+
+def test_full_size_precision_sweep_sampled(lc):
+    """E=2^20, N=84, F=4 (u scaled by 10^k): sampled rows against the oracle, both tensor paths."""
+    import torch
+    D, u = synth.precision_sweep()
+    kernel = lc.Kernel()
+    rows = np.unique(np.concatenate([np.arange(130), np.random.default_rng(1).integers(0, 1 << 20, 3000),
+                                     np.arange((1 << 20) - 130, 1 << 20)]))
+    ref = oracle.contract_rows(D, u, rows)
+    idx = torch.from_numpy(rows).cuda()
+    Dd, ud = to_dev(D), to_dev(u)
+    for prec, tol in (("bf16", 1e-2), ("bf16x3", 1e-6)):
+        v = lc.variant_default(kernel, 1 << 20, 84, 4, "elem", prec)
+        out = lc.contract(kernel, v, Dd, ud)
+        torch.cuda.synchronize()
+        got = out.index_select(1, idx).cpu().numpy()
+        assert oracle.rel_fro_error(got, ref) <= tol
+        del out
+    assert lc.device_error() == 0
