@@ -138,7 +138,19 @@ def roofline_for(v, wl, peaks, sms, t_launch_s, workload_key):
     t_hbm = nbytes / (peaks["hbm_gbs"] * 1e9)
     engine = v["engine"]
     if engine == "tcgen05":
-        alu_peak = None
+        # tensor pipe: one bf16 product per kept term pair (1 for bf16, 6 for bf16x3)
+        npairs = 6 if wl["precision"] == "bf16x3" else 1
+        tflops = flops * npairs
+        t_tensor = tflops / (peaks["bf16_tflops"] * 1e12)
+        if t_tensor > t_hbm:
+            ach = tflops / t_launch_s / 1e12
+            return {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                    "frac": ach / peaks["bf16_tflops"], "traffic": None,
+                    "peak_source": peaks["source"] + " bf16 burst"}
+        ach = nbytes / t_launch_s / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": peaks["source"],
+                "tensor_frac": (tflops / t_launch_s / 1e12) / peaks["bf16_tflops"]}
     else:
         # FP32: 128 FMA lanes per SM; FP64: 2 per SM (the part's nominal 1.25 TFLOP/s FP64)
         lanes = 128 if es == 4 else 2
@@ -191,6 +203,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--E", type=int, default=0, help="override the workload's element count (profiling)")
+    ap.add_argument("--precision", default="", choices=["", "fp32", "fp64", "bf16", "bf16x3"],
+                    help="arithmetic path (default: the workload's; fp32 workloads also run bf16/bf16x3)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -199,6 +213,11 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     wl = dict(WORKLOADS[args.workload])
+    wl["storage"] = "fp64" if wl["precision"] == "fp64" else "fp32"
+    if args.precision:
+        if (args.precision == "fp64") != (wl["storage"] == "fp64"):
+            ap.error("fp64 arithmetic needs an fp64 workload and vice versa")
+        wl["precision"] = args.precision
     if args.E:
         wl["E"] = args.E
         wl["desc"] += f" (E overridden to {args.E})"
@@ -327,7 +346,8 @@ def main():
             "metric": "contraction GFLOP/s", "value": value, "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if wl["precision"] == "fp64" else "f32", "data": "synthetic",
+            "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16 (f32 accumulate)",
+                      "bf16x3": "bf16x3 split (f32 accumulate)"}[wl["precision"]], "data": "synthetic",
             "config": {"workload": wl["desc"], "E": E, "N": N, "F": F, "layout": args.layout,
                        "precision": wl["precision"], "variant": vd, "parallelism": f"replicas x{world}",
                        "l2": "inputs+outputs larger than L2 (no flush needed)",

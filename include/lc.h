@@ -119,6 +119,8 @@ struct lc_variant {
                                  assumption "E mod m = 0" with m a multiple of tile_e holds */
     int32_t stages;           /* u tiles in flight in shared memory (TMA ring depth), >= 1 */
     int32_t ctas_per_sm;      /* persistent grid size in CTAs per SM; 0 = one CTA per tile */
+    int32_t out_buffers;      /* tensor-core engine, element-major: output tiles staged in shared
+                                 memory in flight (1 or 2; 0 = the planner's choice) */
 };
 
 /*

@@ -649,6 +649,8 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
     if (need_device && (sms <= 0 || smem_cap == 0))
         return LC_ERR_NO_DEVICE;
 
+    if (v->engine != LC_ENGINE_TCGEN05 && v->out_buffers != 0)
+        return LC_ERR_INVALID_VARIANT;
     if (v->engine == LC_ENGINE_SIMT) {
         if (v->precision != LC_PREC_FP32 && v->precision != LC_PREC_FP64)
             return LC_ERR_INVALID_VARIANT;
@@ -730,9 +732,15 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
     if (v->engine == LC_ENGINE_TCGEN05) {
         if (v->precision != LC_PREC_BF16 && v->precision != LC_PREC_BF16X3)
             return LC_ERR_INVALID_VARIANT;
-        if (v->tile_e != 128 || v->elems_per_thread != 1 || v->unroll != 1 || v->prefetch_smem != 1)
+        // unroll = threads that share one tile row in the conversion and in the epilogue;
+        // elems_per_thread = K-block width (16, 32 or 64 bf16 = 32/64/128-byte swizzle rows),
+        // K padded to a multiple of it; 1 = the widest block that divides K padded to 16
+        const int kbw = v->elems_per_thread;
+        if (v->tile_e != 128 || v->prefetch_smem != 1 || !(kbw == 1 || kbw == 16 || kbw == 32 || kbw == 64) ||
+            !(v->unroll == 1 || v->unroll == 2))
             return LC_ERR_INVALID_VARIANT;
-        if (v->stages < 1 || v->stages > 2 || v->split_i < 0 || v->split_i > F || v->ctas_per_sm > 1)
+        if (v->stages < 1 || v->stages > 3 || v->split_i < 0 || v->split_i > F || v->ctas_per_sm > 1 ||
+            v->out_buffers < 0 || v->out_buffers > 2)
             return LC_ERR_INVALID_VARIANT;
         const bool node = v->layout == LC_LAYOUT_NODE_MAJOR;
         const int NT = v->precision == LC_PREC_BF16X3 ? 3 : 1;
@@ -741,10 +749,16 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         t.N = N;
         t.F = F;
         t.E = E;
-        t.Kp = (N + 15) / 16 * 16;
-        t.KB = t.Kp % 64 == 0 ? 64 : (t.Kp % 32 == 0 ? 32 : 16);
+        if (kbw == 1) {
+            t.Kp = (N + 15) / 16 * 16;
+            t.KB = t.Kp % 64 == 0 ? 64 : (t.Kp % 32 == 0 ? 32 : 16);
+        } else {
+            t.KB = kbw;
+            t.Kp = (N + kbw - 1) / kbw * kbw;
+        }
         t.nkb = t.Kp / t.KB;
         t.stages = v->stages;
+        t.threads_per_row = v->unroll;
         const size_t W = 2 * (size_t)t.KB;
         auto plan = [&](int G, TcArgs &q) -> bool {
             q.G = G;
@@ -756,34 +770,44 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
             while (q.tmem_cols < q.CBp)
                 q.tmem_cols *= 2;
             size_t off = 0;
-            off += (size_t)NT * q.nkb * q.CBp * W;  // B terms
-            off += (size_t)NT * q.nkb * 128 * W;    // A terms
+            off += (size_t)NT * q.nkb * q.CBp * W;          // B terms
+            off += (size_t)q.abufs * NT * q.nkb * 128 * W;  // A terms
             q.off_stage = (unsigned)off;
             off += (size_t)q.stages * 128 * N * 4;
             q.off_out = (unsigned)off;
             if (!node)
-                off += (size_t)G * 128 * N * 4;
+                off += (size_t)q.obufs * G * 128 * N * 4;
             off = (off + 15) / 16 * 16;
             q.off_bar = (unsigned)off;
-            off += 64;
+            off += 128;  // 14 mbarriers, TMEM address, abort flag
             // alignment slack; at least 120 KB so one CTA holds an SM (and its tensor memory)
             q.smem_bytes = (unsigned)std::max<size_t>(off + 1024, 120 * 1024);
             return q.smem_bytes <= smem_cap;
         };
-        int G = v->split_i;
-        if (G == 0) {
-            for (int g = F; g >= 1; --g) {
+        if (v->stages > 3)
+            return LC_ERR_INVALID_VARIANT;
+        // Shared-memory plan, in order of preference: the most operators per CTA (fewer
+        // column blocks re-reading the same u tile), then two A buffers (conversion of
+        // tile k+1 overlaps the MMAs of tile k), then two output staging buffers (the next
+        // tile's epilogue overlaps the bulk stores).
+        static const int combos[4][2] = {{2, 2}, {1, 2}, {2, 1}, {1, 1}};  // {obufs, abufs}
+        bool found = false;
+        const int g_hi = v->split_i ? v->split_i : F, g_lo = v->split_i ? v->split_i : 1;
+        for (int g = g_hi; g >= g_lo && !found; --g)
+            for (int c = 0; c < 4 && !found; ++c) {
                 TcArgs q = t;
+                q.obufs = node ? 1 : combos[c][0];
+                q.abufs = combos[c][1];
+                if (!node && v->out_buffers && q.obufs != v->out_buffers)
+                    continue;
                 if (plan(g, q)) {
-                    G = g;
-                    break;
+                    t = q;
+                    found = true;
                 }
             }
-            if (G == 0)
-                return LC_ERR_INVALID_VARIANT;
-        }
-        if (!plan(G, t))
+        if (!found)
             return LC_ERR_INVALID_VARIANT;
+        const int G = t.G;
         t.nblocks = (F + G - 1) / G;
         t.ntiles = (E + 127) / 128;
         t.bulk_u = node ? (E % 4 == 0) : 1;
@@ -976,8 +1000,8 @@ lc_status lc_kernel_print(const lc_kernel *kh, const lc_variant *v, char *buf, s
         appendf(s, "tags: %s_outer -> g.0 (persistent, %d CTAs/SM), ilp(%s_inner) = %d, ilp(%s) = %d, unr(%s) = %d\n",
                 e, v->ctas_per_sm, e, v->elems_per_thread, K.i_iname.c_str(), v->split_i,
                 K.j_iname.c_str(), v->unroll);
-        appendf(s, "add_prefetch(%s): %s, stages: %d\n", K.u_name.c_str(),
-                v->prefetch_smem ? "shared memory" : "none (global loads)", v->stages);
+        appendf(s, "add_prefetch(%s): %s, stages: %d, output buffers: %d\n", K.u_name.c_str(),
+                v->prefetch_smem ? "shared memory" : "none (global loads)", v->stages, v->out_buffers);
     }
     s += rule;
     if (needed)
@@ -1020,17 +1044,29 @@ lc_status lc_variant_default(const lc_kernel *kh, int64_t E, int32_t N, int32_t 
         d.stages = 2;
     } else if (precision == LC_PREC_FP32) {
         d.engine = LC_ENGINE_SIMT;
-        d.elems_per_thread = 8;
-        d.split_i = 4;
-        d.tile_e = 64;
-        d.stages = 2;
+        d.ctas_per_sm = 2;
+        if (layout == LC_LAYOUT_ELEM_MAJOR) {
+            d.elems_per_thread = 8;
+            d.split_i = 8;
+            d.tile_e = 128;
+            d.unroll = 1;
+            d.stages = 1;
+        } else {
+            d.elems_per_thread = 4;
+            d.split_i = 8;
+            d.tile_e = 64;
+            d.unroll = 4;
+            d.stages = 2;
+        }
     } else {
         d.engine = LC_ENGINE_TCGEN05;
         d.tile_e = 128;
         d.elems_per_thread = 1;
         d.split_i = 0;
-        d.unroll = 1;
-        d.stages = 2;
+        d.unroll = 2;
+        d.stages = 3;
+        if (lc_variant_validate(kh, E, N, F, &d) != LC_OK)
+            d.stages = 2;
         if (lc_variant_validate(kh, E, N, F, &d) != LC_OK)
             d.stages = 1;
         lc_status st = lc_variant_validate(kh, E, N, F, &d);

@@ -84,6 +84,9 @@ struct TcArgs {
     int Kp, KB, nkb;  // K padded to 16, K-block width (16/32/64 -> 32/64/128-byte swizzle), blocks
     int tmem_cols;  // columns per accumulator (power of two >= CBp)
     int stages;     // u stage buffers (1 or 2)
+    int threads_per_row;  // worker threads per tile row (CTA = 128 * threads_per_row + 64)
+    int abufs;      // A-operand buffers (1 or 2)
+    int obufs;      // element-major output staging buffers (1 or 2)
     long long ntiles;
     int bulk_u, bulk_store;
     unsigned int *err;

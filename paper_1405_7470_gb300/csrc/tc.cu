@@ -10,15 +10,21 @@
 //           products hh, hm, mh, hl, lh, mm are accumulated, small ones first; the
 //           dropped products (ml, lm, ll) are below 2^-24 relative.
 //
-// Structure (one CTA of 128 threads per SM; thread r owns tile row / TMEM lane r):
-//   setup    warp 0 allocates 2 accumulators in TMEM; all threads split D into the
-//            B-operand terms in shared memory (K-major, hardware swizzle layout).
-//   loop     the bulk-copy engine fetches the next u tile (fp32) into a stage buffer;
-//            threads convert the tile into the A-operand terms; thread 0 issues the
-//            MMAs for tile k into accumulator k % 2 and commits them to an mbarrier;
-//            meanwhile all threads drain accumulator (k-1) % 2 (tcgen05.ld) and store
-//            it: element-major through shared memory and one bulk store per operator,
-//            node-major straight from registers (coalesced along e).
+// Structure: a persistent, warp-specialised CTA per SM, roles linked by full/empty
+// mbarrier pairs (no CTA-wide barrier inside the tile loop):
+//   producer warp  the bulk-copy engine fetches u tiles (fp32) into a ring of
+//                  `stages` shared-memory buffers;
+//   MMA warp       one lane issues the tcgen05.mma chain of tile k into TMEM
+//                  accumulator k % 2 (two accumulators), then commits to the
+//                  A-buffer-empty and accumulator-full barriers;
+//   4*H converters convert the fp32 tile into the bf16 A-operand terms (K-major,
+//                  hardware swizzle layout; H threads share a tile row's K chunks);
+//   4*H epilogue   drain the accumulator of a finished tile (tcgen05.ld; the H warps
+//                  of a TMEM lane quarter split its columns) and store it: element-
+//                  major through shared memory and one bulk store per operator,
+//                  node-major straight from registers (coalesced along e).
+// Setup: the MMA warp allocates the accumulators; all threads split D into the
+// B-operand terms, resident for the CTA's lifetime.
 // Every mbarrier wait is bounded in time; on a timeout the kernel sets the device
 // error word, frees its tensor memory and returns.
 #include <cuda_bf16.h>
@@ -140,8 +146,18 @@ __device__ __forceinline__ void split8(const float *x, uint4 *t)
 
 // ------------------------------------------------------------------ kernel
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void workers_sync(int nthreads)
+{
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
 template <int LAYOUT, int NT>
-__global__ void __launch_bounds__(128, 1) tc_contract_kernel(const __grid_constant__ TcArgs a)
+__global__ void __launch_bounds__(576, 1) tc_contract_kernel(const __grid_constant__ TcArgs a)
 {
     constexpr bool NODE = LAYOUT == LC_LAYOUT_NODE_MAJOR;
     constexpr int TE = 128;
@@ -151,33 +167,48 @@ __global__ void __launch_bounds__(128, 1) tc_contract_kernel(const __grid_consta
     unsigned char *smem = smem_dyn + (((raw + 1023u) & ~1023u) - raw);
     const uint32_t sbase = smem_addr(smem);
 
-    const int N = a.N, G = a.G, CB = a.CB, CBp = a.CBp, Kp = a.Kp, KB = a.KB, nkb = a.nkb;
+    const int N = a.N, G = a.G, CBp = a.CBp, Kp = a.Kp, KB = a.KB, nkb = a.nkb;
     const int W = 2 * KB;  // bytes per row of a K-block
     const long long E = a.E;
-    const int S = a.stages;
+    const int S = a.stages, NA = a.abufs;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int H = a.threads_per_row;  // threads per tile row in each worker role
+    const int NW = 4 * H;             // epilogue warps 0..NW-1, conversion warps NW..2*NW-1
+    const int NWT = NW * 32;
+    const int row = 32 * (warp & 3) + lane;  // tile row (== TMEM lane for epilogue warps)
+    const int part = (warp % NW) >> 2;       // which share of the row's K chunks / columns
     const int blk = blockIdx.x % a.nblocks;  // this CTA's column block
     const int f0 = blk * G;
-    const int Gb = min(G, a.F - f0);         // operators in this block
-    const int CBb = Gb * N;                  // valid columns
+    const int Gb = min(G, a.F - f0);  // operators in this block
+    const int CBb = Gb * N;           // valid columns
 
-    const uint32_t offB = 0;
     const uint32_t termB = (uint32_t)nkb * CBp * W;  // bytes per B term
-    const uint32_t offA = offB + NT * termB;
-    const uint32_t termA = (uint32_t)nkb * TE * W;
+    const uint32_t offA = NT * termB;
+    const uint32_t termA = (uint32_t)nkb * TE * W;  // bytes per A term
+    const uint32_t bufA = NT * termA;               // bytes per A buffer
     float *stage = reinterpret_cast<float *>(smem + a.off_stage);  // S x [TE*N] fp32
-    float *ost = reinterpret_cast<float *>(smem + a.off_out);      // [G][TE][N] (element-major)
-    uint64_t *bar_u = reinterpret_cast<uint64_t *>(smem + a.off_bar);
-    uint64_t *bar_mma = bar_u + 2;
-    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bar_u + 4);
+    float *ost0 = reinterpret_cast<float *>(smem + a.off_out);     // obufs x [G][TE][N] (element-major)
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + a.off_bar);
+    uint64_t *u_full = bar, *u_empty = bar + 3, *a_full = bar + 6, *a_empty = bar + 8;
+    uint64_t *acc_full = bar + 10, *acc_empty = bar + 12;
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bar + 14);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bar + 15);
 
-    if (warp == 0)
+    const int prod_warp = 2 * NW, mma_warp = 2 * NW + 1;
+    if (warp == mma_warp)
         tmem_alloc(tmem_holder, 2u * a.tmem_cols);
     if (tid == 0) {
-        for (int s = 0; s < 2; ++s) {
-            mbar_init(&bar_u[s], 1);
-            mbar_init(&bar_mma[s], 1);
+        for (int q = 0; q < 3; ++q) {
+            mbar_init(&u_full[q], 1);
+            mbar_init(&u_empty[q], NW);
         }
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&a_full[q], NW);
+            mbar_init(&a_empty[q], 1);
+            mbar_init(&acc_full[q], 1);
+            mbar_init(&acc_empty[q], NW);
+        }
+        *abort_flag = 0;
         fence_mbar_init();
     }
 
@@ -196,7 +227,7 @@ __global__ void __launch_bounds__(128, 1) tc_contract_kernel(const __grid_consta
             uint4 t[3];
             split8<NT>(x, t);
             const int kb = (c8 * 8) / KB, ch = ((c8 * 8) % KB) / 8;
-            const uint32_t off = offB + (uint32_t)kb * CBp * W + swz_off(n, ch, W);
+            const uint32_t off = (uint32_t)kb * CBp * W + swz_off(n, ch, W);
 #pragma unroll
             for (int tt = 0; tt < NT; ++tt)
                 *reinterpret_cast<uint4 *>(smem + off + tt * termB) = t[tt];
@@ -210,197 +241,236 @@ __global__ void __launch_bounds__(128, 1) tc_contract_kernel(const __grid_consta
 
     const long long my_first = blockIdx.x / a.nblocks;
     const long long my_step = gridDim.x / a.nblocks;
-
-    // Fetch u tile t into stage slot s (thread 0). Tiles the bulk engine cannot fetch
-    // (unaligned tails) are read from global memory during the conversion.
+    // bulk-copy bytes of u tile t (0: not fetchable by the bulk engine, read from global)
     auto tile_bulk_bytes = [&](long long t) -> uint32_t {
-        const long long e0 = t * TE;
-        const int TEv = (int)min((long long)TE, E - e0);
+        const int TEv = (int)min((long long)TE, E - t * TE);
         if (!a.bulk_u)
             return 0;
         const uint32_t bytes = (uint32_t)TEv * N * 4u;
         return (bytes & 15u) ? 0u : bytes;
     };
-    auto issue_u = [&](long long t, int s) {
-        const long long e0 = t * TE;
-        const int TEv = (int)min((long long)TE, E - e0);
-        const uint32_t bytes = tile_bulk_bytes(t);
-        mbar_arrive_expect_tx(&bar_u[s], bytes);
-        if (!bytes)
-            return;
-        float *dst = stage + (size_t)s * TE * N;
-        if (NODE) {
-            for (int j = 0; j < N; ++j)
-                bulk_g2s(dst + (size_t)j * TE, a.u + (size_t)j * E + e0, (uint32_t)TEv * 4u, &bar_u[s]);
-        } else {
-            bulk_g2s(dst, a.u + e0 * N, bytes, &bar_u[s]);
-        }
+    auto fail = [&]() {
+        *abort_flag = 1;
+        atomicOr(a.err, 1u);
     };
-    if (tid == 0) {
-        for (int s = 0; s < S; ++s) {
-            const long long t = my_first + s * my_step;
-            if (t < a.ntiles)
-                issue_u(t, s);
-        }
-    }
 
-    const uint32_t idesc = instr_desc(CBp);
-    const int ksteps = Kp / 16;
-    bool failed = false;
-
-    // Drain accumulator `acc` of tile `t` to global memory.
-    auto epilogue = [&](long long t, int acc) {
-        const long long e0 = t * TE;
-        const int TEv = (int)min((long long)TE, E - e0);
-        const int r = tid;  // tile row == TMEM lane
-        const uint32_t tbase = tmem_base + (uint32_t)acc * a.tmem_cols + ((uint32_t)(warp * 32) << 16);
-        if (!NODE) {
-            if (tid == 0)
-                bulk_wait_read0();  // previous bulk stores have read ost
-            __syncthreads();
+    if (warp == prod_warp) {
+        // ---------------- producer: u tiles into the stage ring
+        int k = 0;
+        for (long long t = my_first; t < a.ntiles; t += my_step, ++k) {
+            const int s = k % S;
+            const uint32_t n = (uint32_t)(k / S);
+            if (!mbar_wait(&u_empty[s], (n & 1u) ^ 1u)) {
+                if (lane == 0)
+                    fail();
+                break;
+            }
+            const long long e0 = t * TE;
+            const int TEv = (int)min((long long)TE, E - e0);
+            const uint32_t bytes = tile_bulk_bytes(t);
+            if (lane == 0)
+                mbar_arrive_expect_tx(&u_full[s], bytes);
+            __syncwarp();
+            if (bytes) {
+                float *dst = stage + (size_t)s * TE * N;
+                if (NODE) {
+                    for (int j = lane; j < N; j += 32)
+                        bulk_g2s(dst + (size_t)j * TE, a.u + (size_t)j * E + e0, (uint32_t)TEv * 4u, &u_full[s]);
+                } else if (lane == 0) {
+                    bulk_g2s(dst, a.u + e0 * N, bytes, &u_full[s]);
+                }
+            }
+            if (*abort_flag)
+                break;
         }
-        int fl = 0, i = 0;
-        for (int c0 = 0; c0 < CBp; c0 += 32) {
-            float v[32];
-            tmem_ld32(tbase + (uint32_t)c0, v);
+    } else if (warp == mma_warp) {
+        // ---------------- MMA issuer
+        const uint32_t idesc = instr_desc(CBp);
+        int k = 0;
+        for (long long t = my_first; t < a.ntiles; t += my_step, ++k) {
+            const int b = k & 1, ab = k % NA;
+            const uint32_t n = (uint32_t)(k >> 1), na = (uint32_t)(k / NA);
+            bool ok = mbar_wait(&a_full[ab], na & 1u);
+            ok = ok && mbar_wait(&acc_empty[b], (n & 1u) ^ 1u);
+            if (!ok) {
+                if (lane == 0)
+                    fail();
+                break;
+            }
+            tc_fence_after();
+            if (lane == 0) {
+                // (D term, u term): lh, hl, mm, mh, hm, hh (small products first). A descriptor
+                // advances by adding the byte offset / 16 to its start-address field.
+                const uint32_t dtm = tmem_base + (uint32_t)b * a.tmem_cols;
+                const uint64_t a0 = smem_desc(sbase + offA + (uint32_t)ab * bufA, W);
+                const uint64_t b0 = smem_desc(sbase, W);
+                const uint32_t a_kb = (uint32_t)(TE * W) >> 4, b_kb = (uint32_t)(CBp * W) >> 4;
+                const int kin_steps = KB / 16;
+                constexpr int npairs = NT == 3 ? 6 : 1;
+                uint32_t accumulate = 0;
 #pragma unroll
-            for (int q = 0; q < 32; ++q) {
-                const int c = c0 + q;
-                if (c < CBb) {
-                    if (NODE) {
-                        if (r < TEv)
-                            a.out[((size_t)(f0 + fl) * N + i) * E + e0 + r] = v[q];
-                    } else {
-                        ost[((size_t)fl * TE + r) * N + i] = v[q];
+                for (int p = 0; p < npairs; ++p) {
+                    const int bt = NT == 3 ? (p == 0 ? 2 : (p == 2 || p == 3) ? 1 : 0) : 0;
+                    const int at = NT == 3 ? (p == 1 ? 2 : (p == 2 || p == 4) ? 1 : 0) : 0;
+                    uint64_t ad = a0 + ((at * termA) >> 4), bd = b0 + ((bt * termB) >> 4);
+                    for (int kb = 0; kb < nkb; ++kb) {
+                        for (int ki = 0; ki < kin_steps; ++ki) {
+                            tc_mma(dtm, ad + 2 * ki, bd + 2 * ki, idesc, accumulate);  // +32 bytes per K step
+                            accumulate = 1;
+                        }
+                        ad += a_kb;
+                        bd += b_kb;
                     }
-                    if (++i == N) {
-                        i = 0;
-                        ++fl;
-                    }
                 }
+                tc_commit(&a_empty[ab]);
+                tc_commit(&acc_full[b]);
             }
+            __syncwarp();
+            if (*abort_flag)
+                break;
         }
-        tc_fence_before();
-        if (!NODE) {
-            fence_async_smem();
-            __syncthreads();
-            const int total = TEv * N;
-            const bool bulk = a.bulk_store && ((total * 4) & 15) == 0;
-            if (bulk) {
-                if (tid == 0) {
-                    for (int g = 0; g < Gb; ++g)
-                        bulk_s2g(a.out + ((size_t)(f0 + g) * E + e0) * N, ost + (size_t)g * TE * N,
-                                 (uint32_t)total * 4u);
-                    bulk_commit();
-                }
-            } else {
-                for (int g = 0; g < Gb; ++g) {
-                    const float *src = ost + (size_t)g * TE * N;
-                    float *dst = a.out + ((size_t)(f0 + g) * E + e0) * N;
-                    for (int q = tid; q < total; q += blockDim.x)
-                        dst[q] = src[q];
-                }
+    } else if (warp >= NW) {
+        // ---------------- conversion warps: fp32 u tile -> bf16 A-operand terms
+        int k = 0;
+        for (long long t = my_first; t < a.ntiles; t += my_step, ++k) {
+            const int s = k % S, ab = k % NA;
+            const uint32_t ns = (uint32_t)(k / S), na = (uint32_t)(k / NA);
+            if (!(mbar_wait(&u_full[s], ns & 1u) && mbar_wait(&a_empty[ab], (na & 1u) ^ 1u))) {
+                if (lane == 0)
+                    fail();
+                break;
             }
-        }
-    };
-
-    long long prev_tile = -1;
-    int k = 0;
-    for (long long t = my_first; t < a.ntiles; t += my_step, ++k) {
-        const int acc = k & 1;
-        const int s = S == 2 ? (k & 1) : 0;
-        const long long e0 = t * TE;
-        const int TEv = (int)min((long long)TE, E - e0);
-
-        // u tile landed, and the MMAs of the previous tile (readers of the A terms) are done
-        bool ok = mbar_wait(&bar_u[s], (uint32_t)((k / S) & 1));
-        if (k >= 1)
-            ok = ok && mbar_wait(&bar_mma[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1));
-        if (!__syncthreads_and(ok)) {
-            failed = true;
-            break;
-        }
-        tc_fence_after();
-
-        // convert row r of the u tile into the A terms
-        {
-            const int r = tid;
+            tc_fence_after();
+            const long long e0 = t * TE;
+            const int TEv = (int)min((long long)TE, E - e0);
             const bool from_stage = tile_bulk_bytes(t) != 0;
             const float *st = stage + (size_t)s * TE * N;
+            unsigned char *Ab = smem + offA + (size_t)ab * bufA;
             const int c8n = Kp / 8;
-            for (int c8 = 0; c8 < c8n; ++c8) {
+            for (int c8 = part; c8 < c8n; c8 += H) {
                 float x[8];
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     const int j = c8 * 8 + q;
                     float val = 0.f;
-                    if (j < N && r < TEv) {
+                    if (j < N && row < TEv) {
                         if (from_stage)
-                            val = NODE ? st[j * TE + r] : st[r * N + j];
+                            val = NODE ? st[j * TE + row] : st[row * N + j];
                         else
-                            val = NODE ? a.u[(size_t)j * E + e0 + r] : a.u[(e0 + r) * N + j];
+                            val = NODE ? a.u[(size_t)j * E + e0 + row] : a.u[(e0 + row) * N + j];
                     }
                     x[q] = val;
                 }
                 uint4 tt4[3];
                 split8<NT>(x, tt4);
                 const int kb = (c8 * 8) / KB, ch = ((c8 * 8) % KB) / 8;
-                const uint32_t off = offA + (uint32_t)kb * TE * W + swz_off(r, ch, W);
+                const uint32_t off = (uint32_t)kb * TE * W + swz_off(row, ch, W);
 #pragma unroll
                 for (int tt = 0; tt < NT; ++tt)
-                    *reinterpret_cast<uint4 *>(smem + off + tt * termA) = tt4[tt];
+                    *reinterpret_cast<uint4 *>(Ab + off + tt * termA) = tt4[tt];
             }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&u_empty[s]);
+                mbar_arrive(&a_full[ab]);
+            }
+            if (*abort_flag)
+                break;
         }
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-
-        if (tid == 0) {
-            // stage slot s is consumed: fetch the tile S steps ahead
-            const long long tn = t + (long long)S * my_step;
-            if (tn < a.ntiles)
-                issue_u(tn, s);
-            // MMAs: pairs (D term, u term), small products first
-            // (D term, u term): lh, hl, mm, mh, hm, hh
-            const uint32_t dtm = tmem_base + (uint32_t)acc * a.tmem_cols;
-            constexpr int npairs = NT == 3 ? 6 : 1;
+    } else {
+        // ---------------- epilogue warps: TMEM accumulators -> out
+        int k = 0;
+        bool ok = true;
+        for (long long t = my_first; t < a.ntiles; t += my_step, ++k) {
+            const int b = k & 1;
+            const long long e0 = t * TE;
+            const int TEv = (int)min((long long)TE, E - e0);
+            if (!mbar_wait(&acc_full[b], (uint32_t)((k >> 1) & 1))) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            float *ost = ost0 + (size_t)(k % a.obufs) * G * TE * N;
+            if (!NODE) {
+                if (tid == 0) {
+                    // the bulk stores that last read this staging buffer are done reading
+                    if (a.obufs == 2)
+                        bulk_wait_read1();
+                    else
+                        bulk_wait_read0();
+                }
+                workers_sync(NWT);
+            }
+            const uint32_t tbase = tmem_base + (uint32_t)b * a.tmem_cols + ((uint32_t)((warp & 3) * 32) << 16);
+            for (int c0 = part * 32; c0 < CBp; c0 += 32 * H) {
+                float v[32];
+                tmem_ld32(tbase + (uint32_t)c0, v);
+                if (c0 >= CBb)
+                    continue;
+                int fl = c0 / N, i = c0 - fl * N;
+                if (NODE) {
+                    if (row < TEv) {
+                        float *o = a.out + ((size_t)(f0 + fl) * N + i) * E + e0 + row;
 #pragma unroll
-            for (int p = 0; p < npairs; ++p) {
-                const int bt = NT == 3 ? (p == 0 ? 2 : (p == 2 || p == 3) ? 1 : 0) : 0;
-                const int at = NT == 3 ? (p == 1 ? 2 : (p == 2 || p == 4) ? 1 : 0) : 0;
-                for (int kk = 0; kk < ksteps; ++kk) {
-                    const int kb = (kk * 16) / KB, kin = ((kk * 16) % KB) * 2;  // byte offset in the row
-                    const uint64_t ad = smem_desc(sbase + offA + at * termA + kb * TE * W + kin, W);
-                    const uint64_t bd = smem_desc(sbase + offB + bt * termB + kb * CBp * W + kin, W);
-                    tc_mma(dtm, ad, bd, idesc, (p > 0 || kk > 0) ? 1u : 0u);
+                        for (int q = 0; q < 32; ++q) {
+                            if (c0 + q < CBb)
+                                *o = v[q];
+                            o += E;
+                        }
+                    }
+                } else {
+                    int o = (fl * TE + row) * N + i;
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        if (c0 + q < CBb)
+                            ost[o] = v[q];
+                        ++o;
+                        if (++i == N) {
+                            i = 0;
+                            o += (TE - 1) * N;
+                        }
+                    }
                 }
             }
-            tc_commit(&bar_mma[acc]);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(&acc_empty[b]);
+            if (!NODE) {
+                fence_async_smem();
+                workers_sync(NWT);
+                const int total = TEv * N;
+                if (a.bulk_store && ((total * 4) & 15) == 0) {
+                    if (tid == 0) {
+                        for (int g = 0; g < Gb; ++g)
+                            bulk_s2g(a.out + ((size_t)(f0 + g) * E + e0) * N, ost + (size_t)g * TE * N,
+                                     (uint32_t)total * 4u);
+                        bulk_commit();
+                    }
+                } else {
+                    for (int g = 0; g < Gb; ++g) {
+                        const float *src = ost + (size_t)g * TE * N;
+                        float *dst = a.out + ((size_t)(f0 + g) * E + e0) * N;
+                        for (int q = tid; q < total; q += NWT)
+                            dst[q] = src[q];
+                    }
+                    workers_sync(NWT);
+                }
+            }
+            if (*abort_flag)
+                break;
         }
-
-        if (prev_tile >= 0)
-            epilogue(prev_tile, acc ^ 1);
-        prev_tile = t;
+        if (!ok && lane == 0)
+            fail();
+        if (!NODE && tid == 0)
+            bulk_wait0();
     }
 
-    if (!failed && prev_tile >= 0) {
-        const bool ok = mbar_wait(&bar_mma[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1));
-        if (__syncthreads_and(ok)) {
-            tc_fence_after();
-            epilogue(prev_tile, (k - 1) & 1);
-        } else {
-            failed = true;
-        }
-    }
-    if (failed && tid == 0)
-        atomicOr(a.err, 1u);
-    if (!NODE && tid == 0)
-        bulk_wait0();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0)
+    if (warp == mma_warp)
         tmem_dealloc(tmem_base, 2u * a.tmem_cols);
 }
 
@@ -419,7 +489,7 @@ lc_status tc_launch(const TcArgs &a, int layout, int nterms, int grid, cudaStrea
         return cuda_fail(e);
     TcArgs args = a;
     void *params[] = {&args};
-    e = cudaLaunchKernel(fn, dim3(grid), dim3(128), params, a.smem_bytes, s);
+    e = cudaLaunchKernel(fn, dim3(grid), dim3(256 * a.threads_per_row + 64), params, a.smem_bytes, s);
     if (e != cudaSuccess)
         return cuda_fail(e);
     return LC_OK;

@@ -61,9 +61,9 @@ def test_integer_inputs_bit_exact(lc, layout, prec):
     for E, N, F in SHAPES:
         D, u = synth.integer_operands(E, N, F, seed=E + N)
         uu = synth.to_node_major(u) if layout == "node" else u
-        for stages in (1, 2):
+        for stages, tpr in ((1, 1), (2, 2), (3, 2)):
             v = lc.Variant(engine="tcgen05", layout=layout, precision=prec, tile_e=128, elems_per_thread=1,
-                           split_i=0, unroll=1, prefetch_smem=1, stages=stages)
+                           split_i=0, unroll=tpr, prefetch_smem=1, stages=stages)
             if lc.variant_validate(kernel, E, N, F, v) != 0:
                 continue
             got = run(lc, kernel, v, D, uu, layout)
@@ -77,7 +77,12 @@ def test_random_inputs_within_bounds(lc, layout, prec):
     for si, (E, N, F) in enumerate(SHAPES):
         D, u = synth.operands(E, N, F, np.float32, seed=200 + si, scale_exp=3.0 if si % 2 else None)
         uu = synth.to_node_major(u) if layout == "node" else u
-        v = lc.variant_default(kernel, E, N, F, layout, prec)
+        try:
+            v = lc.variant_default(kernel, E, N, F, layout, prec)
+        except lc.LcError:
+            # the shared-memory plan of the three-term path does not fit for large N
+            assert prec == "bf16x3" and N > 100
+            continue
         got = run(lc, kernel, v, D, uu, layout)
         target = oracle.contract_bf16x3(D, uu, layout) if prec == "bf16x3" else oracle.contract_bf16(D, uu, layout)
         # the operand terms as the kernel sees them
@@ -95,16 +100,18 @@ def test_random_inputs_within_bounds(lc, layout, prec):
             assert err > 1e-4  # operand rounding to bf16 really happens
 
 
-@pytest.mark.parametrize("split", [1, 2])
-def test_column_blocks_split_operators(lc, split):
-    """Operators split over CTA column blocks (split_i = operators per block)."""
+@pytest.mark.parametrize("layout,split", [("elem", 1), ("node", 1), ("node", 2), ("elem", 3)])
+def test_column_blocks_split_operators(lc, layout, split):
+    """Operators split over CTA column blocks (split_i = operators per block, last block partial)."""
     kernel = lc.Kernel()
-    D, u = synth.operands(700, 84, 4, np.float32, seed=5)
-    v = lc.Variant(engine="tcgen05", precision="bf16x3", tile_e=128, elems_per_thread=1, split_i=split,
-                   unroll=1, prefetch_smem=1, stages=1)
-    assert lc.variant_validate(kernel, 700, 84, 4, v) == 0
-    got = run(lc, kernel, v, D, u, "elem")
-    assert oracle.rel_fro_error(got, oracle.contract(D, u)) <= 1e-6
+    N = 84 if split < 3 else 20
+    D, u = synth.operands(700, N, 4, np.float32, seed=5)
+    uu = synth.to_node_major(u) if layout == "node" else u
+    v = lc.Variant(engine="tcgen05", layout=layout, precision="bf16x3", tile_e=128, elems_per_thread=1,
+                   split_i=split, unroll=2, prefetch_smem=1, stages=1)
+    assert lc.variant_validate(kernel, 700, N, 4, v) == 0
+    got = run(lc, kernel, v, D, uu, layout)
+    assert oracle.rel_fro_error(got, oracle.contract(D, uu, layout)) <= 1e-6
 
 
 def test_full_size_precision_sweep_sampled(lc):
