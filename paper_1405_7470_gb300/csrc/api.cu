@@ -1075,9 +1075,17 @@ lc_status lc_variant_default(const lc_kernel *kh, int64_t E, int32_t N, int32_t 
         *v = d;
         return LC_OK;
     }
-    // shrink the tile until the shared-memory plan fits
-    while (d.tile_e > d.elems_per_thread && lc_variant_validate(kh, E, N, F, &d) == LC_ERR_INVALID_VARIANT)
-        d.tile_e /= 2;
+    // shrink the tile (then the register block) until the shared-memory plan fits
+    const lc_variant d0 = d;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        while (d.tile_e > d.elems_per_thread && lc_variant_validate(kh, E, N, F, &d) == LC_ERR_INVALID_VARIANT)
+            d.tile_e /= 2;
+        if (lc_variant_validate(kh, E, N, F, &d) != LC_ERR_INVALID_VARIANT)
+            break;
+        d = d0;
+        d.elems_per_thread = precision == LC_PREC_FP64 ? 2 : 4;
+        d.split_i = precision == LC_PREC_FP64 ? 2 : 4;
+    }
     lc_status st = lc_variant_validate(kh, E, N, F, &d);
     if (st != LC_OK)
         return st;
