@@ -174,6 +174,52 @@ lc_status lc_contract_host(const lc_kernel *k, const lc_variant *v, const void *
 lc_status lc_device_error(int clear);
 
 /* ------------------------------------------------------------------------- */
+/* Grouped launch: several problems of different sizes in one persistent      */
+/* kernel, optionally captured once in a CUDA graph and replayed.             */
+/* ------------------------------------------------------------------------- */
+typedef struct lc_group {
+    int64_t E;            /* elements of this group (>= 0) */
+    int32_t N;            /* nodes, 1..256 */
+    int32_t F;            /* operators, 1..8 */
+    const void *D_dev;    /* [F][N][N] float */
+    const void *u_dev;    /* layout per the variant */
+    void *out_dev;        /* layout per the variant */
+} lc_group;
+
+typedef struct lc_grouped_plan lc_grouped_plan;
+
+/* Workspace bytes lc_grouped_plan_create needs for these groups and variant. */
+lc_status lc_grouped_workspace_size(const lc_kernel *k, const lc_variant *v, const lc_group *groups,
+                                    int32_t ngroups, size_t *bytes);
+
+/*
+ * Plan one persistent launch over all groups: every group gets a SIMT tile shape with
+ * the same CTA size; all (group, tile) work is cut into one contiguous range per CTA,
+ * balanced by estimated cost.  The variant (FP32 SIMT engine) gives the register block
+ * (elems_per_thread, split_i), unroll (1 or 4), prefetch_smem, stages and ctas_per_sm.
+ *   workspace_dev  caller-owned device memory holding the group and work tables
+ *                  (lc_grouped_workspace_size bytes, 16-byte aligned); it must outlive
+ *                  the plan, as must the groups' buffers, which the plan references.
+ *   use_graph      1: capture the launch on `stream` (not the legacy default stream)
+ *                  into a CUDA graph; lc_grouped_run then replays it.
+ * The tables are uploaded synchronously on `stream`.  The plan is a host object;
+ * free it with lc_grouped_plan_destroy.
+ * Errors: LC_ERR_INVALID_ARGUMENT, LC_ERR_INVALID_VARIANT, LC_ERR_ASSUMPTION,
+ * LC_ERR_MISALIGNED, LC_ERR_BUFFER_TOO_SMALL, LC_ERR_NO_DEVICE, LC_ERR_CUDA.
+ */
+lc_status lc_grouped_plan_create(const lc_kernel *k, const lc_variant *v, const lc_group *groups,
+                                 int32_t ngroups, void *workspace_dev, size_t workspace_bytes,
+                                 int32_t use_graph, void *stream, lc_grouped_plan **plan);
+
+/* Enqueue the planned launch (graph replay when captured) on `stream`. */
+lc_status lc_grouped_run(lc_grouped_plan *plan, void *stream);
+
+/* Grid size and number of (group, tile-range) segments of a plan. */
+lc_status lc_grouped_plan_info(const lc_grouped_plan *plan, int32_t *grid, int32_t *segments);
+
+void lc_grouped_plan_destroy(lc_grouped_plan *plan);
+
+/* ------------------------------------------------------------------------- */
 /* FP64 error norm on the GPU.                                               */
 /* ------------------------------------------------------------------------- */
 enum { LC_DTYPE_F32 = 0, LC_DTYPE_F64 = 1 };

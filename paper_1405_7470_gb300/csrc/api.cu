@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cctype>
+#include <cmath>
 #include <map>
 #include <mutex>
 #include <set>
@@ -608,6 +609,48 @@ static bool implies_E_multiple_of(const Kernel &K, long long m)
 
 // ------------------------------------------------------------------ validation
 
+// Warp shape WE x WC and column groups CG (a multiple of WC) for a SIMT tile: the fewest
+// padded columns within `max_threads` (or exactly `req_threads` threads when > 0) and the
+// shared memory left for D^T after `fixed` bytes.
+static bool simt_warp_shape(SimtGeom &g, int C, int N, int es, size_t fixed, size_t smem_cap, int max_threads,
+                            int req_threads)
+{
+    const int ncg = (C + g.RC - 1) / g.RC;
+    const int wcs[6] = {4, 2, 8, 1, 16, 32};
+    long long best_waste = -1;
+    for (int wc : wcs) {
+        const int we = 32 / wc;
+        if (g.EG % we != 0)
+            continue;
+        if (fixed + (size_t)N * g.RC * wc * es > smem_cap)
+            continue;
+        const long long cg_smem = (long long)((smem_cap - fixed) / ((size_t)N * g.RC * es));
+        long long cg;
+        if (req_threads > 0) {
+            if (req_threads % g.EG != 0)
+                continue;
+            cg = req_threads / g.EG;
+            if (cg % wc != 0 || cg > cg_smem)
+                continue;
+        } else {
+            cg = ((ncg + wc - 1) / wc) * (long long)wc;
+            cg = std::min<long long>(cg, (max_threads / g.EG) / wc * (long long)wc);
+            cg = std::min<long long>(cg, cg_smem / wc * (long long)wc);
+            if (cg < wc)
+                continue;
+        }
+        const long long cw = cg * g.RC;
+        const long long nch = (C + cw - 1) / cw;
+        const long long waste = nch * cw - C + (nch - 1) * 4;  // extra chunks reload D
+        if (best_waste < 0 || waste < best_waste) {
+            best_waste = waste;
+            g.WC = wc;
+            g.CG = (int)cg;
+        }
+    }
+    return best_waste >= 0;
+}
+
 struct Resolved {
     int engine, layout, precision;
     SimtGeom g;
@@ -618,7 +661,7 @@ struct Resolved {
 };
 
 static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_variant *v, Resolved &r,
-                         bool need_device)
+                         bool need_device, int req_threads = 0)
 {
     if (!v || v->struct_size != sizeof(lc_variant))
         return LC_ERR_INVALID_ARGUMENT;
@@ -684,33 +727,7 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
                           : (size_t)N * (g.TE + VEC) * es + (size_t)g.stages * g.TE * N * es;
         if (!node)
             fixed += (size_t)F * g.TE * N * es;
-        // Warp shape WE x WC and column groups CG (a multiple of WC): the fewest padded
-        // columns within 512 threads and the shared memory left for D^T.
-        const int ncg = (C + g.RC - 1) / g.RC;
-        const int wcs[6] = {4, 2, 8, 1, 16, 32};
-        long long best_waste = -1;
-        for (int wc : wcs) {
-            const int we = 32 / wc;
-            if (g.EG % we != 0)
-                continue;
-            if (fixed + (size_t)N * g.RC * wc * es > smem_cap)
-                continue;
-            const long long cg_smem = (long long)((smem_cap - fixed) / ((size_t)N * g.RC * es));
-            long long cg = ((ncg + wc - 1) / wc) * (long long)wc;
-            cg = std::min<long long>(cg, (max_threads / g.EG) / wc * (long long)wc);
-            cg = std::min<long long>(cg, cg_smem / wc * (long long)wc);
-            if (cg < wc)
-                continue;
-            const long long cw = cg * g.RC;
-            const long long nch = (C + cw - 1) / cw;
-            const long long waste = nch * cw - C + (nch - 1) * 4;  // extra chunks reload D
-            if (best_waste < 0 || waste < best_waste) {
-                best_waste = waste;
-                g.WC = wc;
-                g.CG = (int)cg;
-            }
-        }
-        if (best_waste < 0)
+        if (!simt_warp_shape(g, C, N, es, fixed, smem_cap, max_threads, req_threads))
             return LC_ERR_INVALID_VARIANT;
         g.threads = g.EG * g.CG;
         g.CW = g.CG * g.RC;
@@ -1202,6 +1219,150 @@ lc_status lc_contract_host(const lc_kernel *kh, const lc_variant *v, const void 
     return LC_OK;
 }
 
+// ------------------------------------------------------------------ grouped launch
+
+struct lc_grouped_plan {
+    void *fn = nullptr;
+    GroupedArgs args{};
+    int grid = 0, threads = 0;
+    size_t smem = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int ngroups = 0, nsegs = 0;
+};
+
+namespace lc {
+
+struct GroupedPlanHost {
+    std::vector<SimtArgs> groups;
+    std::vector<GroupSeg> segs;
+    std::vector<int> cta_seg;
+    size_t smem = 0, bytes = 0;
+    size_t off_groups = 0, off_segs = 0, off_cta = 0;
+    int grid = 0, threads = 256;
+};
+
+static lc_status grouped_plan_host(const Kernel &K, const lc_variant *v, const lc_group *groups, int ng,
+                                   GroupedPlanHost &P)
+{
+    if (!v || v->struct_size != sizeof(lc_variant) || !groups || ng <= 0)
+        return LC_ERR_INVALID_ARGUMENT;
+    if (v->engine != LC_ENGINE_SIMT || v->precision != LC_PREC_FP32 || v->tail_free)
+        return LC_ERR_INVALID_VARIANT;
+    if (!(v->unroll == 1 || v->unroll == 4))
+        return LC_ERR_INVALID_VARIANT;
+    const int sms = sm_count();
+    if (sms <= 0)
+        return LC_ERR_NO_DEVICE;
+    const int T = P.threads;
+    std::vector<double> tile_cost(ng);
+    std::vector<long long> ntiles(ng);
+    P.groups.resize(ng);
+    P.smem = 0;
+    for (int gi = 0; gi < ng; ++gi) {
+        const lc_group &G = groups[gi];
+        if (!G.D_dev || (G.E > 0 && (!G.u_dev || !G.out_dev)))
+            return LC_ERR_INVALID_ARGUMENT;
+        if (!aligned16(G.D_dev) || !aligned16(G.u_dev) || !aligned16(G.out_dev))
+            return LC_ERR_MISALIGNED;
+        // tile of TE = EG * RE elements with exactly T threads: the fewest padded columns,
+        // then the tile closest to 128 elements
+        Resolved best;
+        long long best_key = -1;
+        for (int eg = 4; eg <= T; eg *= 2) {
+            lc_variant vg = *v;
+            vg.tile_e = eg * v->elems_per_thread;
+            vg.ctas_per_sm = 0;
+            Resolved r;
+            if (resolve(K, G.E, G.N, G.F, &vg, r, true, T) != LC_OK)
+                continue;
+            const long long pad = (long long)r.g.nchunks * r.g.CW - (long long)G.F * G.N;
+            const long long key = pad * 64 + std::abs((int)std::log2((double)vg.tile_e / 128.0) * 4);
+            if (best_key < 0 || key < best_key) {
+                best_key = key;
+                best = r;
+            }
+        }
+        if (best_key < 0)
+            return LC_ERR_INVALID_VARIANT;
+        SimtArgs a;
+        memset(&a, 0, sizeof a);
+        a.D = G.D_dev;
+        a.u = G.u_dev;
+        a.out = G.out_dev;
+        a.E = G.E;
+        a.N = G.N;
+        a.F = G.F;
+        a.C = G.F * G.N;
+        a.TE = best.g.TE;
+        a.EG = best.g.EG;
+        a.CG = best.g.CG;
+        a.CW = best.g.CW;
+        a.nchunks = best.g.nchunks;
+        a.WC = best.g.WC;
+        a.stages = best.g.stages;
+        a.bulk = best.g.bulk;
+        a.bulk_store = best.g.bulk_store;
+        a.ntiles = best.g.ntiles;
+        a.tail_free = 0;
+        P.groups[gi] = a;
+        P.smem = std::max(P.smem, best.g.smem);
+        ntiles[gi] = G.E > 0 ? best.g.ntiles : 0;
+        // estimated seconds per tile: FMA pipe (FP32, padded columns) vs HBM
+        const double flops = 2.0 * a.TE * (double)G.N * a.CW * a.nchunks;
+        const double bytes = 4.0 * a.TE * (double)G.N * (1 + G.F);
+        tile_cost[gi] = std::max(flops / (sms * 128 * 2 * 1.9e9), bytes / 6.8e12) + 2e-7 / sms;
+    }
+    double total = 0;
+    long long total_tiles = 0;
+    for (int gi = 0; gi < ng; ++gi) {
+        total += tile_cost[gi] * ntiles[gi];
+        total_tiles += ntiles[gi];
+    }
+    const int per_sm = v->ctas_per_sm > 0 ? v->ctas_per_sm : 2;
+    P.grid = (int)std::max<long long>(1, std::min<long long>((long long)sms * per_sm, total_tiles));
+    // walk the (group, tile) list, cutting it into P.grid contiguous ranges of equal cost
+    P.segs.clear();
+    P.cta_seg.assign(P.grid + 1, 0);
+    const double target = total / P.grid;
+    int b = 0;
+    double acc = 0;
+    for (int gi = 0; gi < ng; ++gi) {
+        long long t = 0;
+        while (t < ntiles[gi]) {
+            // tiles of this group that fit in CTA b's remaining budget (at least one)
+            long long take = ntiles[gi] - t;
+            if (b < P.grid - 1) {
+                const double room = (b + 1) * target - acc;
+                long long fit = (long long)std::ceil(room / tile_cost[gi]);
+                take = std::max<long long>(1, std::min(take, fit));
+            }
+            GroupSeg sg;
+            sg.group = gi;
+            sg.pad = 0;
+            sg.first = t;
+            sg.count = take;
+            P.segs.push_back(sg);
+            t += take;
+            acc += take * tile_cost[gi];
+            if (b < P.grid - 1 && acc >= (b + 1) * target - 1e-15) {
+                P.cta_seg[b + 1] = (int)P.segs.size();
+                ++b;
+            }
+        }
+    }
+    for (int q = b + 1; q <= P.grid; ++q)
+        P.cta_seg[q] = (int)P.segs.size();
+    auto up16 = [](size_t x) { return (x + 15) / 16 * 16; };
+    P.off_groups = 0;
+    P.off_segs = up16(sizeof(SimtArgs) * ng);
+    P.off_cta = P.off_segs + up16(sizeof(GroupSeg) * P.segs.size());
+    P.bytes = P.off_cta + up16(sizeof(int) * (P.grid + 1));
+    return LC_OK;
+}
+
+}  // namespace lc
+
 lc_status lc_device_error(int clear)
 {
     unsigned int *p = error_word();
@@ -1218,6 +1379,126 @@ lc_status lc_device_error(int clear)
             return cuda_fail(e);
     }
     return h ? LC_ERR_TIMEOUT : LC_OK;
+}
+
+lc_status lc_grouped_workspace_size(const lc_kernel *kh, const lc_variant *v, const lc_group *groups,
+                                    int32_t ngroups, size_t *bytes)
+{
+    if (!kh || !bytes)
+        return LC_ERR_INVALID_ARGUMENT;
+    GroupedPlanHost P;
+    lc_status st = grouped_plan_host(kh->k, v, groups, ngroups, P);
+    if (st != LC_OK)
+        return st;
+    *bytes = P.bytes;
+    return LC_OK;
+}
+
+lc_status lc_grouped_plan_create(const lc_kernel *kh, const lc_variant *v, const lc_group *groups,
+                                 int32_t ngroups, void *workspace, size_t workspace_bytes, int32_t use_graph,
+                                 void *stream, lc_grouped_plan **out)
+{
+    if (!kh || !out || !workspace)
+        return LC_ERR_INVALID_ARGUMENT;
+    if (((uintptr_t)workspace & 15u) != 0)
+        return LC_ERR_MISALIGNED;
+    if (use_graph && !stream)
+        return LC_ERR_INVALID_ARGUMENT;  // the legacy default stream cannot be captured
+    int major = 0, minor = 0;
+    if (current_cc(&major, &minor) != 0 || major != 10 || minor != 3)
+        return LC_ERR_NO_DEVICE;
+    GroupedPlanHost P;
+    lc_status st = grouped_plan_host(kh->k, v, groups, ngroups, P);
+    if (st != LC_OK)
+        return st;
+    if (workspace_bytes < P.bytes)
+        return LC_ERR_BUFFER_TOO_SMALL;
+    void *fn = grouped_kernel_ptr(v->layout, v->elems_per_thread, v->split_i, v->unroll, v->prefetch_smem);
+    if (!fn)
+        return LC_ERR_INVALID_VARIANT;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned char *ws = static_cast<unsigned char *>(workspace);
+    std::vector<unsigned char> host(P.bytes, 0);
+    memcpy(host.data() + P.off_groups, P.groups.data(), sizeof(SimtArgs) * P.groups.size());
+    memcpy(host.data() + P.off_segs, P.segs.data(), sizeof(GroupSeg) * P.segs.size());
+    memcpy(host.data() + P.off_cta, P.cta_seg.data(), sizeof(int) * P.cta_seg.size());
+    cudaError_t e = cudaMemcpyAsync(ws, host.data(), P.bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    lc_grouped_plan *plan = new (std::nothrow) lc_grouped_plan;
+    if (!plan)
+        return LC_ERR_INVALID_ARGUMENT;
+    plan->fn = fn;
+    plan->args.groups = reinterpret_cast<const SimtArgs *>(ws + P.off_groups);
+    plan->args.segs = reinterpret_cast<const GroupSeg *>(ws + P.off_segs);
+    plan->args.cta_seg = reinterpret_cast<const int *>(ws + P.off_cta);
+    plan->args.err = error_word();
+    plan->grid = P.grid;
+    plan->threads = P.threads;
+    plan->smem = P.smem;
+    plan->ngroups = ngroups;
+    plan->nsegs = (int)P.segs.size();
+    if (use_graph) {
+        void *params[] = {&plan->args};
+        e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t le = cudaLaunchKernel(fn, dim3(plan->grid), dim3(plan->threads), params, plan->smem, s);
+            e = cudaStreamEndCapture(s, &plan->graph);
+            if (le != cudaSuccess)
+                e = le;
+        }
+        if (e == cudaSuccess)
+            e = cudaGraphInstantiate(&plan->exec, plan->graph, 0);
+        if (e != cudaSuccess) {
+            if (plan->graph)
+                cudaGraphDestroy(plan->graph);
+            delete plan;
+            return cuda_fail(e);
+        }
+    }
+    *out = plan;
+    return LC_OK;
+}
+
+lc_status lc_grouped_run(lc_grouped_plan *plan, void *stream)
+{
+    if (!plan)
+        return LC_ERR_INVALID_ARGUMENT;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if (plan->exec) {
+        e = cudaGraphLaunch(plan->exec, s);
+    } else {
+        void *params[] = {&plan->args};
+        e = cudaLaunchKernel(plan->fn, dim3(plan->grid), dim3(plan->threads), params, plan->smem, s);
+    }
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    return LC_OK;
+}
+
+lc_status lc_grouped_plan_info(const lc_grouped_plan *plan, int32_t *grid, int32_t *segments)
+{
+    if (!plan || !grid || !segments)
+        return LC_ERR_INVALID_ARGUMENT;
+    *grid = plan->grid;
+    *segments = plan->nsegs;
+    return LC_OK;
+}
+
+void lc_grouped_plan_destroy(lc_grouped_plan *plan)
+{
+    if (!plan)
+        return;
+    if (plan->exec)
+        cudaGraphExecDestroy(plan->exec);
+    if (plan->graph)
+        cudaGraphDestroy(plan->graph);
+    delete plan;
 }
 
 lc_status lc_device_info(int32_t *sm, int32_t *major, int32_t *minor)

@@ -95,6 +95,20 @@ struct TcArgs {
 
 lc_status tc_launch(const TcArgs &a, int layout, int nterms, int grid, cudaStream_t s);
 
+// Grouped launch: per-group SIMT arguments, contiguous tile ranges, ranges per CTA.
+struct GroupSeg {
+    int group;
+    int pad;
+    long long first, count;
+};
+struct GroupedArgs {
+    const SimtArgs *groups;
+    const GroupSeg *segs;
+    const int *cta_seg;  // CTA b walks segs[cta_seg[b] .. cta_seg[b+1])
+    unsigned int *err;
+};
+void *grouped_kernel_ptr(int layout, int re, int rc, int unr, int pf);
+
 int sm_count();
 int current_cc(int *major, int *minor);
 unsigned int *error_word();

@@ -50,8 +50,12 @@ struct VecT<double> {
 // Threads per CTA allowed for a register block (the 8 x 8 FP32 block needs > 128 registers).
 __host__ __device__ constexpr int simt_max_threads(int re, int rc) { return re * rc >= 64 ? 256 : 512; }
 
+// One CTA's share of a contraction: tiles t_first, t_first + t_step, ... below t_end.
+// Used by the plain kernel (grid-stride over all tiles) and by the grouped kernel
+// (contiguous tile ranges of several problems, one after the other).
 template <typename T, int RE, int RC, int UNR, int LAYOUT, bool PREFETCH>
-__global__ void __launch_bounds__(simt_max_threads(RE, RC)) simt_contract_kernel(SimtArgs a)
+__device__ __forceinline__ void simt_tiles(const SimtArgs &a, long long t_first, long long t_step, long long t_end,
+                                           unsigned char *smem_raw)
 {
     constexpr int VEC = VecT<T>::n;
     using V = typename VecT<T>::type;
@@ -61,7 +65,6 @@ __global__ void __launch_bounds__(simt_max_threads(RE, RC)) simt_contract_kernel
     constexpr bool NODE = LAYOUT == LC_LAYOUT_NODE_MAJOR;
     constexpr int ES = (int)sizeof(T);
 
-    extern __shared__ __align__(128) unsigned char smem_raw[];
     const int N = a.N, F = a.F, C = a.C, TE = a.TE, EG = a.EG, CG = a.CG, CW = a.CW;
     const long long E = a.E;
     const int S = a.stages;
@@ -141,8 +144,8 @@ __global__ void __launch_bounds__(simt_max_threads(RE, RC)) simt_contract_kernel
     };
     if (bulk && warp == 0) {
         for (int s = 0; s < S; ++s) {
-            const long long t = blockIdx.x + (long long)s * gridDim.x;
-            if (t < a.ntiles)
+            const long long t = t_first + (long long)s * t_step;
+            if (t < t_end)
                 issue(t, s);
         }
     }
@@ -162,7 +165,7 @@ __global__ void __launch_bounds__(simt_max_threads(RE, RC)) simt_contract_kernel
     col_offsets(0);
 
     int k = 0;
-    for (long long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++k) {
+    for (long long tile = t_first; tile < t_end; tile += t_step, ++k) {
         const long long e0 = tile * (long long)TE;
         const bool full = a.tail_free || (e0 + TE <= E);
         const int TEv = full ? TE : (int)(E - e0);
@@ -232,8 +235,8 @@ __global__ void __launch_bounds__(simt_max_threads(RE, RC)) simt_contract_kernel
             __syncthreads();
             if (!NODE && bulk && warp == 0) {
                 // stage[buf] is consumed: fetch the tile S steps ahead into it
-                const long long nt = tile + (long long)S * gridDim.x;
-                if (nt < a.ntiles)
+                const long long nt = tile + (long long)S * t_step;
+                if (nt < t_end)
                     issue(nt, buf);
             }
         } else if (!NODE) {
@@ -338,8 +341,8 @@ __global__ void __launch_bounds__(simt_max_threads(RE, RC)) simt_contract_kernel
             if (bulk) {
                 __syncthreads();  // every warp is done reading stage[buf]
                 if (warp == 0) {
-                    const long long nt = tile + (long long)S * gridDim.x;
-                    if (nt < a.ntiles)
+                    const long long nt = tile + (long long)S * t_step;
+                    if (nt < t_end)
                         issue(nt, buf);
                 }
             }
@@ -373,6 +376,19 @@ __global__ void __launch_bounds__(simt_max_threads(RE, RC)) simt_contract_kernel
     }
     if (!NODE && tid == 0)
         bulk_wait0();
+    // leave the mbarriers and shared memory reusable by the next tile range
+    __syncthreads();
+    if (bulk && tid == 0)
+        for (int s = 0; s < S; ++s)
+            mbar_inval(&bars[s]);
+    __syncthreads();
+}
+
+template <typename T, int RE, int RC, int UNR, int LAYOUT, bool PREFETCH>
+__global__ void __launch_bounds__(simt_max_threads(RE, RC)) simt_contract_kernel(SimtArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    simt_tiles<T, RE, RC, UNR, LAYOUT, PREFETCH>(a, blockIdx.x, gridDim.x, a.ntiles, smem_raw);
 }
 
 // Host-side dispatch over the compiled instances of one element type and layout.

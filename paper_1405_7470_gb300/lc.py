@@ -47,6 +47,11 @@ class lc_variant(ctypes.Structure):
     ]
 
 
+class lc_group(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_int64), ("N", ctypes.c_int32), ("F", ctypes.c_int32),
+                ("D_dev", ctypes.c_void_p), ("u_dev", ctypes.c_void_p), ("out_dev", ctypes.c_void_p)]
+
+
 # Exported symbols and their signatures (argtypes, restype).
 _P, _I32, _I64, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
 _VP = ctypes.POINTER(lc_variant)
@@ -64,6 +69,12 @@ SIGNATURES = {
     "lc_error_norm_workspace_size": ([_I64, ctypes.POINTER(_SZ)], ctypes.c_int),
     "lc_error_norm": ([_P, _I32, _P, _I64, _P, _P, _SZ, _P], ctypes.c_int),
     "lc_device_info": ([ctypes.POINTER(_I32)] * 3, ctypes.c_int),
+    "lc_grouped_workspace_size": ([_P, _VP, ctypes.POINTER(lc_group), _I32, ctypes.POINTER(_SZ)], ctypes.c_int),
+    "lc_grouped_plan_create": ([_P, _VP, ctypes.POINTER(lc_group), _I32, _P, _SZ, _I32, _P, ctypes.POINTER(_P)],
+                               ctypes.c_int),
+    "lc_grouped_run": ([_P, _P], ctypes.c_int),
+    "lc_grouped_plan_info": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)], ctypes.c_int),
+    "lc_grouped_plan_destroy": ([_P], None),
 }
 
 _lib = None
@@ -225,3 +236,47 @@ def device_info():
     a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     check(load().lc_device_info(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "lc_device_info")
     return dict(sm_count=a.value, cc=(b.value, c.value))
+
+
+class GroupedPlan:
+    """One persistent launch over several problems (lc_grouped_plan_create), optionally a CUDA graph.
+
+    groups: list of (D, u, out) torch CUDA tensors (out per the variant's layout). The plan keeps
+    references to the tensors and to its workspace, which must stay alive while it is used.
+    """
+
+    def __init__(self, kernel: Kernel, v: lc_variant, groups, use_graph: bool = True, stream=None):
+        import torch
+        lib = load()
+        node = v.layout == LAYOUT["node"]
+        arr = (lc_group * len(groups))()
+        for k, (D, u, out) in enumerate(groups):
+            F, N, _ = D.shape
+            arr[k].E = u.shape[1] if node else u.shape[0]
+            arr[k].N, arr[k].F = N, F
+            arr[k].D_dev, arr[k].u_dev, arr[k].out_dev = D.data_ptr(), u.data_ptr(), out.data_ptr()
+        need = ctypes.c_size_t(0)
+        check(lib.lc_grouped_workspace_size(kernel.handle, ctypes.byref(v), arr, len(groups), ctypes.byref(need)),
+              "lc_grouped_workspace_size")
+        dev = groups[0][0].device
+        self.workspace = torch.empty(max(16, need.value), dtype=torch.uint8, device=dev)
+        self._keep = (groups, kernel, v)
+        h = ctypes.c_void_p()
+        check(lib.lc_grouped_plan_create(kernel.handle, ctypes.byref(v), arr, len(groups), self.workspace.data_ptr(),
+                                         need.value, 1 if use_graph else 0, _stream_ptr(stream), ctypes.byref(h)),
+              "lc_grouped_plan_create")
+        self._h = h
+        self._lib = lib
+
+    def run(self, stream=None):
+        check(self._lib.lc_grouped_run(self._h, _stream_ptr(stream)), "lc_grouped_run")
+
+    def info(self):
+        g, sgs = ctypes.c_int32(), ctypes.c_int32()
+        check(self._lib.lc_grouped_plan_info(self._h, ctypes.byref(g), ctypes.byref(sgs)), "lc_grouped_plan_info")
+        return dict(grid=g.value, segments=sgs.value)
+
+    def __del__(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.lc_grouped_plan_destroy(self._h)
+            self._h = None

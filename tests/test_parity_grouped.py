@@ -1,0 +1,72 @@
+"""GPU parity of the grouped persistent kernel (several problems of different N in one
+launch, replayed from a CUDA graph) against the CPU FP64 oracle, group by group."""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_util import fma_bound, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1405_7470_gb300 import lc as lcmod
+    lcmod.load()
+    return lcmod
+
+
+SIZES = [(4, 3000), (10, 777), (20, 1), (35, 4096), (56, 513), (84, 2000), (120, 300), (165, 257)]
+
+
+@pytest.mark.parametrize("layout", ["elem", "node"])
+@pytest.mark.parametrize("graph", [True, False])
+def test_grouped_matches_oracle(lc, layout, graph):
+    import torch
+    kernel = lc.Kernel()
+    data = synth.grouped_operands(SIZES, F=3, seed=1)
+    groups, host = [], []
+    for (N, E), (D, u) in zip(SIZES, data):
+        uu = synth.to_node_major(u) if layout == "node" else u
+        out = torch.full((3, N, E) if layout == "node" else (3, E, N), float("nan"), device="cuda")
+        groups.append((to_dev(D), to_dev(uu), out))
+        host.append((D, uu))
+    stream = torch.cuda.Stream()
+    for re_, rc, unr, pf, st in [(8, 4, 4, 1, 2), (4, 8, 1, 0, 1), (8, 8, 1, 1, 1)]:
+        v = lc.Variant(layout=layout, elems_per_thread=re_, split_i=rc, unroll=unr, prefetch_smem=pf, stages=st,
+                       ctas_per_sm=2)
+        plan = lc.GroupedPlan(kernel, v, groups, use_graph=graph, stream=stream)
+        for rep in range(2):  # replay twice: the result must not depend on the previous run
+            for _, _, out in groups:
+                out.fill_(float("nan"))
+            plan.run(stream)
+            stream.synchronize()
+            assert lc.device_error() == 0
+            for (D, uu), (_, _, out) in zip(host, groups):
+                got = out.cpu().numpy().astype(np.float64)
+                ref = oracle.contract(D, uu, layout)
+                assert np.all(np.abs(got - ref) <= fma_bound(D, uu, layout, 2.0 ** -24)), (D.shape, layout)
+        info = plan.info()
+        assert info["segments"] >= len(SIZES) - 1
+        del plan
+
+
+def test_grouped_integer_exact(lc):
+    import torch
+    kernel = lc.Kernel()
+    groups, host = [], []
+    for k, (N, E) in enumerate(SIZES):
+        D, u = synth.integer_operands(E, N, 3, seed=k)
+        groups.append((to_dev(D), to_dev(u), torch.empty((3, E, N), device="cuda")))
+        host.append((D, u))
+    v = lc.Variant(elems_per_thread=8, split_i=4, unroll=4, prefetch_smem=1, stages=2, ctas_per_sm=1)
+    plan = lc.GroupedPlan(kernel, v, groups, use_graph=False)
+    plan.run()
+    torch.cuda.synchronize()
+    for (D, u), (_, _, out) in zip(host, groups):
+        assert np.array_equal(out.cpu().numpy().astype(np.float64), oracle.contract(D, u))
