@@ -241,6 +241,59 @@ lc_status lc_error_norm(const void *out_dev, int32_t out_dtype, const double *re
                         int64_t n, double *sums_dev, void *workspace_dev,
                         size_t workspace_bytes, void *stream);
 
+/* ------------------------------------------------------------------------- */
+/* Variant selection: exhaustive autotuning and the learned cost model.       */
+/* The paper lets the controlling program choose transformations per target   */
+/* and workload (Section 1); these calls make that choice measurable.         */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * The candidate descriptors for a problem (the autotuner's search space), valid ones
+ * only, in a fixed order.  Writes min(count, cap) entries; *count = the number of
+ * candidates.  Errors: LC_ERR_INVALID_ARGUMENT, LC_ERR_BUFFER_TOO_SMALL (cap < count).
+ */
+lc_status lc_enumerate_variants(const lc_kernel *k, int64_t E, int32_t N, int32_t F, int32_t layout,
+                                int32_t precision, lc_variant *out, int32_t cap, int32_t *count);
+
+/*
+ * Time every candidate on the caller's problem buffers (D, u, out as for lc_contract):
+ * one warm-up launch, then the median of `reps` launches timed with CUDA events on
+ * `stream`.  Synchronises the stream.  On return variants[0..count) and ms[0..count)
+ * hold the candidates sorted by time, fastest first.  `out` is overwritten.
+ * Errors: as lc_enumerate_variants and lc_contract.
+ */
+lc_status lc_autotune(const lc_kernel *k, int64_t E, int32_t N, int32_t F, int32_t layout, int32_t precision,
+                      const void *D_dev, const void *u_dev, void *out_dev, int32_t reps, lc_variant *variants,
+                      float *ms, int32_t cap, int32_t *count, void *stream);
+
+/*
+ * MLP cost model: inputs x[din] (1 <= din <= 32), three hidden ReLU layers of width
+ * 64, one linear output (the predicted log run time).  Parameters are one float
+ * vector, in this order: W1[64][din], b1[64], W2[64][64], b2[64], W3[64][64], b3[64],
+ * w4[64], b4[1]; all pointers below are device pointers, arrays row-major.
+ */
+lc_status lc_mlp_param_count(int32_t din, int64_t *count);
+
+/* y[s] = network(X[s][0..din)) for s < n. */
+lc_status lc_mlp_forward(const float *params_dev, const float *X_dev, int64_t n, int32_t din, float *y_dev,
+                         void *stream);
+
+/* Workspace bytes for lc_mlp_loss_grad. */
+lc_status lc_mlp_workspace_size(int32_t din, size_t *bytes);
+
+/*
+ * Mean squared error L = (1/n) sum_s (y_s - t_s)^2 and its gradient by backpropagation:
+ * grad_loss_dev[0..P) = dL/dparams, grad_loss_dev[P] = L (P = lc_mlp_param_count).
+ * Deterministic (fixed per-block partial sums, then an ordered reduction).
+ */
+lc_status lc_mlp_loss_grad(const float *params_dev, const float *X_dev, const float *t_dev, int64_t n,
+                           int32_t din, float *grad_loss_dev, void *workspace_dev, size_t workspace_bytes,
+                           void *stream);
+
+/* One Adam update (bias-corrected, step >= 1) of n parameters with moments m, v. */
+lc_status lc_mlp_adam_step(float *params_dev, const float *grad_dev, float *m_dev, float *v_dev, int64_t n,
+                           int32_t step, float lr, float beta1, float beta2, float eps, void *stream);
+
 /* Number of SMs and compute capability of the current device. */
 lc_status lc_device_info(int32_t *sm_count, int32_t *cc_major, int32_t *cc_minor);
 

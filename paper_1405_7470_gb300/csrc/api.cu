@@ -610,8 +610,9 @@ static bool implies_E_multiple_of(const Kernel &K, long long m)
 // ------------------------------------------------------------------ validation
 
 // Warp shape WE x WC and column groups CG (a multiple of WC) for a SIMT tile: the fewest
-// padded columns within `max_threads` (or exactly `req_threads` threads when > 0) and the
-// shared memory left for D^T after `fixed` bytes.
+// padded columns within `max_threads` (and within `req_threads` when > 0: a CTA of that size
+// whose surplus warps only help with loads) and the shared memory left for D^T after `fixed`
+// bytes.
 static bool simt_warp_shape(SimtGeom &g, int C, int N, int es, size_t fixed, size_t smem_cap, int max_threads,
                             int req_threads)
 {
@@ -625,20 +626,12 @@ static bool simt_warp_shape(SimtGeom &g, int C, int N, int es, size_t fixed, siz
         if (fixed + (size_t)N * g.RC * wc * es > smem_cap)
             continue;
         const long long cg_smem = (long long)((smem_cap - fixed) / ((size_t)N * g.RC * es));
-        long long cg;
-        if (req_threads > 0) {
-            if (req_threads % g.EG != 0)
-                continue;
-            cg = req_threads / g.EG;
-            if (cg % wc != 0 || cg > cg_smem)
-                continue;
-        } else {
-            cg = ((ncg + wc - 1) / wc) * (long long)wc;
-            cg = std::min<long long>(cg, (max_threads / g.EG) / wc * (long long)wc);
-            cg = std::min<long long>(cg, cg_smem / wc * (long long)wc);
-            if (cg < wc)
-                continue;
-        }
+        const int cap = req_threads > 0 ? std::min(max_threads, req_threads) : max_threads;
+        long long cg = ((ncg + wc - 1) / wc) * (long long)wc;
+        cg = std::min<long long>(cg, (cap / g.EG) / wc * (long long)wc);
+        cg = std::min<long long>(cg, cg_smem / wc * (long long)wc);
+        if (cg < wc)
+            continue;
         const long long cw = cg * g.RC;
         const long long nch = (C + cw - 1) / cw;
         const long long waste = nch * cw - C + (nch - 1) * 4;  // extra chunks reload D
@@ -1087,10 +1080,15 @@ lc_status lc_variant_default(const lc_kernel *kh, int64_t E, int32_t N, int32_t 
         if (lc_variant_validate(kh, E, N, F, &d) != LC_OK)
             d.stages = 1;
         lc_status st = lc_variant_validate(kh, E, N, F, &d);
-        if (st != LC_OK)
+        if (st == LC_OK) {
+            *v = d;
+            return LC_OK;
+        }
+        if (st != LC_ERR_INVALID_VARIANT)
             return st;
-        *v = d;
-        return LC_OK;
+        // no tensor-core plan fits (large N): FP32 SIMT, whose error is below both
+        // reduced-precision bounds
+        return lc_variant_default(kh, E, N, F, layout, LC_PREC_FP32, v);
     }
     // shrink the tile (then the register block) until the shared-memory plan fits
     const lc_variant d0 = d;

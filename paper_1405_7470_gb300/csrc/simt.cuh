@@ -78,6 +78,9 @@ __device__ __forceinline__ void simt_tiles(const SimtArgs &a, long long t_first,
     const int nwe = EG / WE;
     const int eg = (warp % nwe) * WE + lane % WE;
     const int cg = (warp / nwe) * WC + lane / WE;
+    // warps beyond the EG x CG thread grid (a grouped CTA sized for a larger group) only
+    // take part in the cooperative loads, copies and barriers
+    const bool active = warp < (EG * CG) / 32;
     const int TEp = TE + VEC;  // padded row of the transposed element-major tile
 
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);  // two mbarriers
@@ -252,6 +255,8 @@ __device__ __forceinline__ void simt_tiles(const SimtArgs &a, long long t_first,
                 col_offsets(ch);
                 __syncthreads();
             }
+            if (!active)
+                continue;
             T acc[RE][RC];
 #pragma unroll
             for (int x = 0; x < RE; ++x)

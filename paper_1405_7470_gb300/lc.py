@@ -75,6 +75,15 @@ SIGNATURES = {
     "lc_grouped_run": ([_P, _P], ctypes.c_int),
     "lc_grouped_plan_info": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)], ctypes.c_int),
     "lc_grouped_plan_destroy": ([_P], None),
+    "lc_enumerate_variants": ([_P, _I64, _I32, _I32, _I32, _I32, _VP, _I32, ctypes.POINTER(_I32)], ctypes.c_int),
+    "lc_autotune": ([_P, _I64, _I32, _I32, _I32, _I32, _P, _P, _P, _I32, _VP, _P, _I32, ctypes.POINTER(_I32), _P],
+                    ctypes.c_int),
+    "lc_mlp_param_count": ([_I32, ctypes.POINTER(_I64)], ctypes.c_int),
+    "lc_mlp_forward": ([_P, _P, _I64, _I32, _P, _P], ctypes.c_int),
+    "lc_mlp_workspace_size": ([_I32, ctypes.POINTER(_SZ)], ctypes.c_int),
+    "lc_mlp_loss_grad": ([_P, _P, _P, _I64, _I32, _P, _P, _SZ, _P], ctypes.c_int),
+    "lc_mlp_adam_step": ([_P, _P, _P, _P, _I64, _I32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                          ctypes.c_float, _P], ctypes.c_int),
 }
 
 _lib = None
@@ -280,3 +289,64 @@ class GroupedPlan:
         if getattr(self, "_h", None) and self._h.value:
             self._lib.lc_grouped_plan_destroy(self._h)
             self._h = None
+
+
+def enumerate_variants(kernel: Kernel, E: int, N: int, F: int, layout="elem", precision="fp32"):
+    """The autotuner's candidate descriptors for a problem (valid ones, fixed order)."""
+    lib = load()
+    cap = 256
+    arr = (lc_variant * cap)()
+    n = ctypes.c_int32(0)
+    check(lib.lc_enumerate_variants(kernel.handle, E, N, F, LAYOUT[layout], PRECISION[precision], arr, cap,
+                                    ctypes.byref(n)), "lc_enumerate_variants")
+    return [arr[q] for q in range(n.value)]
+
+
+def autotune(kernel: Kernel, D, u, out, layout="elem", precision="fp32", reps=3, stream=None):
+    """Time every candidate on (D, u, out); returns [(ms, lc_variant)] fastest first."""
+    lib = load()
+    F, N, _ = D.shape
+    E = u.shape[1] if layout == "node" else u.shape[0]
+    cap = 256
+    arr = (lc_variant * cap)()
+    ms = (ctypes.c_float * cap)()
+    n = ctypes.c_int32(0)
+    check(lib.lc_autotune(kernel.handle, E, N, F, LAYOUT[layout], PRECISION[precision], D.data_ptr(), u.data_ptr(),
+                          out.data_ptr(), reps, arr, ms, cap, ctypes.byref(n), _stream_ptr(stream)), "lc_autotune")
+    return [(float(ms[q]), arr[q]) for q in range(n.value)]
+
+
+def mlp_param_count(din: int) -> int:
+    n = ctypes.c_int64(0)
+    check(load().lc_mlp_param_count(din, ctypes.byref(n)), "lc_mlp_param_count")
+    return n.value
+
+
+def mlp_forward(params, X, stream=None):
+    """Predictions for the rows of X (float32 CUDA tensors)."""
+    import torch
+    n, din = X.shape
+    y = torch.empty(n, dtype=torch.float32, device=X.device)
+    check(load().lc_mlp_forward(params.data_ptr(), X.data_ptr(), n, din, y.data_ptr(), _stream_ptr(stream)),
+          "lc_mlp_forward")
+    return y
+
+
+def mlp_loss_grad(params, X, t, workspace=None, stream=None):
+    """(loss, grad) of the mean squared error, computed by the library's kernels."""
+    import torch
+    lib = load()
+    n, din = X.shape
+    ws = ctypes.c_size_t(0)
+    check(lib.lc_mlp_workspace_size(din, ctypes.byref(ws)), "lc_mlp_workspace_size")
+    if workspace is None or workspace.numel() * workspace.element_size() < ws.value:
+        workspace = torch.empty(ws.value // 4 + 4, dtype=torch.float32, device=X.device)
+    out = torch.empty(params.numel() + 1, dtype=torch.float32, device=X.device)
+    check(lib.lc_mlp_loss_grad(params.data_ptr(), X.data_ptr(), t.data_ptr(), n, din, out.data_ptr(),
+                               workspace.data_ptr(), ws.value, _stream_ptr(stream)), "lc_mlp_loss_grad")
+    return out[-1], out[:-1]
+
+
+def mlp_adam_step(params, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    check(load().lc_mlp_adam_step(params.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(), params.numel(),
+                                  step, lr, beta1, beta2, eps, _stream_ptr(stream)), "lc_mlp_adam_step")

@@ -1,0 +1,230 @@
+"""Learned variant picker: features, exhaustive-autotuning data, MLP training and regret.
+
+The paper's premise (Section 1) is that the controlling program picks the code
+transformations per target and per workload. Here the choice is made two ways:
+  * exhaustively: lc_autotune times every valid descriptor (the judge of regret);
+  * by a small MLP cost model (3 hidden ReLU layers of 64) that predicts log run time
+    from problem and descriptor features; its training and inference run in the
+    library's own CUDA kernels (lc_mlp_loss_grad, lc_mlp_adam_step, lc_mlp_forward).
+
+regret(shape) = t(picked) / t(best) - 1, with both times from the same autotuning pass.
+
+Running ``python -m paper_1405_7470_gb300.picker --out results.json`` on a GPU runs the
+whole experiment on the 600 seeded shapes (first 500 train, last 100 held out).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+from . import lc
+
+PATHS = ("fp32", "bf16", "bf16x3")
+LAYOUTS = ("elem", "node")
+DIN = 24  # feature count (the library supports up to 32)
+
+
+def features(shape: dict, v) -> np.ndarray:
+    """Feature vector of (problem, descriptor); every entry is O(1)."""
+    d = v if isinstance(v, dict) else lc.variant_dict(v)
+    E, N, F = shape["E"], shape["N"], shape["F"]
+    eng = d["engine"]
+    x = [
+        math.log2(max(E, 1)) / 23.0, N / 165.0, (N % 16) / 16.0, F / 4.0,
+        float(shape["path"] == "fp32"), float(shape["path"] == "bf16"), float(shape["path"] == "bf16x3"),
+        float(shape["layout"] == "elem"), float(shape["layout"] == "node"),
+        math.log2(max(E, 1) * N * F) / 32.0, N * F / 660.0, math.log2(N) / 8.0,
+        float(eng == "simt"), float(eng == "tcgen05"), float(eng == "warp"),
+        math.log2(max(d["tile_e"], 1)) / 10.0, d["elems_per_thread"] / 64.0 if eng == "tcgen05" else d["elems_per_thread"] / 8.0,
+        d["split_i"] / 8.0, math.log2(max(d["unroll"], 1)) / 3.0, float(d["prefetch_smem"]), d["stages"] / 3.0,
+        d["ctas_per_sm"] / 4.0, float(d["precision"] == "fp32"), float(d["precision"] in ("bf16", "bf16x3")),
+    ]
+    assert len(x) == DIN
+    return np.asarray(x, dtype=np.float32)
+
+
+def he_uniform(din: int, seed: int) -> np.ndarray:
+    """Initial parameters: He-uniform weights U(-sqrt(6/fan_in), +), zero biases."""
+    rng = np.random.default_rng(seed)
+    H = 64
+    parts = [rng.uniform(-1, 1, H * din) * math.sqrt(6.0 / din), np.zeros(H),
+             rng.uniform(-1, 1, H * H) * math.sqrt(6.0 / H), np.zeros(H),
+             rng.uniform(-1, 1, H * H) * math.sqrt(6.0 / H), np.zeros(H),
+             rng.uniform(-1, 1, H) * math.sqrt(6.0 / H), np.zeros(1)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+class ProblemPool:
+    """Device buffers reused across shapes (sized for the largest one); seeded data."""
+
+    def __init__(self, max_u: int, max_out: int, max_d: int):
+        import torch
+        self.u = torch.empty(max_u, dtype=torch.float32, device="cuda")
+        self.out = torch.empty(max_out, dtype=torch.float32, device="cuda")
+        self.D = torch.empty(max_d, dtype=torch.float32, device="cuda")
+
+    def problem(self, shape: dict, seed: int):
+        import torch
+        E, N, F = shape["E"], shape["N"], shape["F"]
+        g = torch.Generator(device="cuda")
+        g.manual_seed(seed)
+        u = self.u[:E * N]
+        u.normal_(generator=g)
+        D = self.D[:F * N * N]
+        D.uniform_(-1, 1, generator=g)
+        out = self.out[:F * E * N]
+        if shape["layout"] == "node":
+            return D.view(F, N, N), u.view(N, E), out.view(F, N, E)
+        return D.view(F, N, N), u.view(E, N), out.view(F, E, N)
+
+
+def collect(shapes, reps: int = 3, seed: int = 0, log=None):
+    """Autotune every shape; returns per-shape records with all candidate timings."""
+    import torch
+    kernel = lc.Kernel()
+    max_u = max(s["E"] * s["N"] for s in shapes)
+    max_out = max(s["E"] * s["N"] * s["F"] for s in shapes)
+    max_d = max(s["F"] * s["N"] ** 2 for s in shapes)
+    pool = ProblemPool(max_u, max_out, max_d)
+    stream = torch.cuda.Stream()
+    recs = []
+    for k, sh in enumerate(shapes):
+        D, u, out = pool.problem(sh, seed * 100003 + k)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            res = lc.autotune(kernel, D, u, out, sh["layout"], sh["path"], reps=reps, stream=stream)
+        tune_s = time.perf_counter() - t0
+        vd = lc.variant_default(kernel, sh["E"], sh["N"], sh["F"], sh["layout"], sh["path"])
+        # the default descriptor, timed the same way
+        with torch.cuda.stream(stream):
+            for _ in range(1):
+                lc.contract(kernel, vd, D, u, out, stream=stream)
+            ts = []
+            for _ in range(reps):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                lc.contract(kernel, vd, D, u, out, stream=stream)
+                b.record(stream)
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+        recs.append(dict(shape=sh, cands=[(ms, lc.variant_dict(v)) for ms, v in res], tune_s=tune_s,
+                         default=(float(np.median(ts)), lc.variant_dict(vd))))
+        if log and k % 50 == 0:
+            log(f"shape {k}: {sh} best {res[0][0]:.4f} ms of {len(res)} candidates ({tune_s:.2f} s)")
+    if lc.device_error() != 0:
+        raise RuntimeError("device error word set during autotuning")
+    return recs
+
+
+def dataset(recs):
+    X, y = [], []
+    for r in recs:
+        for ms, vd in r["cands"]:
+            X.append(features(r["shape"], vd))
+            y.append(math.log(max(ms, 1e-4)))
+    return np.stack(X), np.asarray(y, dtype=np.float32)
+
+
+def train(X: np.ndarray, y: np.ndarray, epochs: int = 300, batch: int = 512, lr: float = 1e-3, seed: int = 0,
+          log=None):
+    """Adam on the library's MLP kernels; returns (params tensor, loss history)."""
+    import torch
+    n, din = X.shape
+    Xd = torch.from_numpy(X).cuda()
+    yd = torch.from_numpy(y).cuda()
+    params = torch.from_numpy(he_uniform(din, seed)).cuda()
+    m = torch.zeros_like(params)
+    v = torch.zeros_like(params)
+    ws = None
+    rng = np.random.default_rng(seed)
+    step, hist = 0, []
+    for ep in range(epochs):
+        perm = torch.from_numpy(rng.permutation(n)).cuda()
+        tot = 0.0
+        for b0 in range(0, n, batch):
+            idx = perm[b0:b0 + batch]
+            xb, yb = Xd.index_select(0, idx), yd.index_select(0, idx)
+            loss, grad = lc.mlp_loss_grad(params, xb, yb, workspace=ws)
+            step += 1
+            lc.mlp_adam_step(params, grad, m, v, step, lr=lr)
+            tot += float(loss) * len(idx) if (b0 == 0 and ep % 25 == 0) else 0.0
+        if ep % 25 == 0 or ep == epochs - 1:
+            full, _ = lc.mlp_loss_grad(params, Xd, yd)
+            hist.append((ep, float(full)))
+            if log:
+                log(f"epoch {ep}: train mse(log t) {float(full):.4f}")
+    return params, hist
+
+
+def pick(params, shape: dict, cands):
+    """Index of the candidate with the smallest predicted run time."""
+    import torch
+    X = torch.from_numpy(np.stack([features(shape, vd) for _, vd in cands])).cuda()
+    pred = lc.mlp_forward(params, X).cpu().numpy()
+    return int(np.argmin(pred))
+
+
+def regret_stats(r):
+    r = np.asarray(r)
+    return dict(geomean=float(np.exp(np.mean(np.log1p(r))) - 1), median=float(np.median(r)),
+                p90=float(np.percentile(r, 90)), max=float(np.max(r)), mean=float(np.mean(r)))
+
+
+def evaluate(params, recs):
+    mlp, dflt, pick_s = [], [], []
+    for rec in recs:
+        best = rec["cands"][0][0]
+        t0 = time.perf_counter()
+        q = pick(params, rec["shape"], rec["cands"])
+        pick_s.append(time.perf_counter() - t0)
+        mlp.append(rec["cands"][q][0] / best - 1.0)
+        dflt.append(max(rec["default"][0] / best - 1.0, 0.0))
+    return dict(mlp=regret_stats(mlp), default=regret_stats(dflt), pick_wall_s_mean=float(np.mean(pick_s)),
+                mlp_per_shape=mlp)
+
+
+def run_experiment(out_path: str, n_shapes: int = 600, n_train: int = 500, reps: int = 3, epochs: int = 300,
+                   seed: int = 0):
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import synth
+    log = lambda s: print(s, flush=True)
+    shapes = synth.picker_shapes(seed, n_shapes)
+    t0 = time.perf_counter()
+    recs = collect(shapes, reps=reps, seed=seed, log=log)
+    tune_total = time.perf_counter() - t0
+    tr, te = recs[:n_train], recs[n_train:]
+    X, y = dataset(tr)
+    t1 = time.perf_counter()
+    params, hist = train(X, y, epochs=epochs, seed=seed, log=log)
+    train_s = time.perf_counter() - t1
+    ev_te = evaluate(params, te)
+    ev_tr = evaluate(params, tr)
+    res = dict(n_shapes=n_shapes, n_train=n_train, samples=int(len(y)), epochs=epochs,
+               autotune_wall_s=tune_total, autotune_wall_s_per_shape=float(np.mean([r["tune_s"] for r in recs])),
+               train_wall_s=train_s, loss_history=hist, heldout=ev_te, train_fit=dict(mlp=ev_tr["mlp"]),
+               candidates_per_shape=float(np.mean([len(r["cands"]) for r in recs])))
+    with open(out_path, "w") as fh:
+        json.dump(dict(summary=res, records=recs), fh)
+    log(json.dumps({k: v for k, v in res.items() if k != "loss_history"}, default=str)[:2000])
+    return res
+
+
+if __name__ == "__main__":
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default="picker_results.json")
+    ap.add_argument("--shapes", type=int, default=600)
+    ap.add_argument("--train", type=int, default=500)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--epochs", type=int, default=300)
+    a = ap.parse_args()
+    lc.load()
+    run_experiment(a.out, a.shapes, a.train, a.reps, a.epochs)
