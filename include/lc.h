@@ -294,6 +294,25 @@ lc_status lc_mlp_loss_grad(const float *params_dev, const float *X_dev, const fl
 lc_status lc_mlp_adam_step(float *params_dev, const float *grad_dev, float *m_dev, float *v_dev, int64_t n,
                            int32_t step, float lr, float beta1, float beta2, float eps, void *stream);
 
+/*
+ * lc_error_norm without a workspace, for callers that cannot allocate device memory
+ * (cudaMalloc synchronises the device, which latency-bound or real-time callers forbid,
+ * and some host frameworks give their plugins no allocator).  This call has no
+ * counterpart in the paper; it exists only for such callers.
+ *   out_dev, ref_dev, sums_dev   as for lc_error_norm; 1 <= n <= 2^28
+ * The partial sums live in a 64 KiB array in device memory that the library holds on
+ * every GPU it is loaded on until the process exits; nothing is allocated per call.
+ * The array's address is looked up on the first call made on each device (with that
+ * device current); make that first call before any stream capture.  All calls share the
+ * array, so calls that overlap on the GPU race: serialise them.  Each call rewrites the
+ * slots it uses, so no clearing is needed.  Results equal lc_error_norm's up to the
+ * order of the FP64 summation.
+ * Errors: LC_ERR_INVALID_ARGUMENT, LC_ERR_BUFFER_TOO_SMALL (n above 2^28, the array's
+ * capacity), LC_ERR_MISALIGNED, LC_ERR_CUDA.
+ */
+lc_status lc_error_norm_noalloc(const void *out_dev, int32_t out_dtype, const double *ref_dev, int64_t n,
+                                double *sums_dev, void *stream);
+
 /* Number of SMs and compute capability of the current device. */
 lc_status lc_device_info(int32_t *sm_count, int32_t *cc_major, int32_t *cc_minor);
 

@@ -3,6 +3,9 @@
 // same on every call: per-block partial sums, then one block adds them in order.
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
+
 #include "lc_internal.h"
 
 namespace lc {
@@ -93,9 +96,85 @@ lc_status norm_launch(const void *out, int dtype, const double *ref, long long n
     return LC_OK;
 }
 
+// ---------------------------------------------------------------- no-allocation variant
+//
+// Some callers cannot hand the library a workspace: code that runs where cudaMalloc is
+// off limits (it synchronises the whole device, so latency-bound serving loops and
+// real-time callers forbid it), or plugins whose host framework owns every allocation
+// and offers none to its extensions.  For them the same two-kernel reduction can take
+// its partial sums from a fixed array that the library places in device memory.
+//
+// The array holds one (sum of squared differences, sum of squares) pair per block of
+// the first kernel; the grid has one block per kNoallocChunk elements, so one call
+// handles at most kNoallocChunk * kNoallocMaxBlocks elements (2^28).  Every GPU that
+// loads the library keeps these 64 KiB until the process exits.  All calls share the
+// array: calls whose kernels overlap on the GPU (different streams, or threads) race on
+// it and must be serialised by the caller.  Each call overwrites every slot it reads, so
+// nothing needs clearing between calls.
+static constexpr long long kNoallocChunk = 1LL << 16;
+static constexpr int kNoallocMaxBlocks = 4096;
+static __device__ __align__(256) double g_norm_scratch[2 * kNoallocMaxBlocks];
+
+static std::mutex g_scratch_mu;
+static std::map<int, double *> g_scratch_addr;  // device -> address of g_norm_scratch
+
+// The device address of g_norm_scratch on the current device.  Host code must not pass
+// the symbol itself to a kernel: on the host it names a stand-in, not device memory.
+static lc_status norm_scratch(double **ptr)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    auto it = g_scratch_addr.find(dev);
+    if (it != g_scratch_addr.end()) {
+        *ptr = it->second;
+        return LC_OK;
+    }
+    double *p = nullptr;
+    e = cudaGetSymbolAddress((void **)&p, g_norm_scratch);
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    g_scratch_addr[dev] = p;
+    *ptr = p;
+    return LC_OK;
+}
+
 }  // namespace lc
 
 extern "C" {
+
+lc_status lc_error_norm_noalloc(const void *out, int32_t out_dtype, const double *ref, int64_t n, double *sums,
+                                void *stream)
+{
+    if (!out || !ref || !sums || n < 1)
+        return LC_ERR_INVALID_ARGUMENT;
+    if (out_dtype != LC_DTYPE_F32 && out_dtype != LC_DTYPE_F64)
+        return LC_ERR_INVALID_ARGUMENT;
+    if (n > lc::kNoallocChunk * lc::kNoallocMaxBlocks)
+        return LC_ERR_BUFFER_TOO_SMALL;  // more elements than the fixed partial-sum array covers
+    if (((uintptr_t)ref & 7u) || ((uintptr_t)sums & 7u) || ((uintptr_t)out & (out_dtype == LC_DTYPE_F64 ? 7u : 3u)))
+        return LC_ERR_MISALIGNED;
+    double *scratch = nullptr;
+    lc_status st = lc::norm_scratch(&scratch);
+    if (st != LC_OK)
+        return st;
+    const int blocks = (int)((n + lc::kNoallocChunk - 1) / lc::kNoallocChunk);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (out_dtype == LC_DTYPE_F32)
+        lc::norm_partial_kernel<float><<<blocks, lc::kNormThreads, 0, s>>>(static_cast<const float *>(out), ref, n,
+                                                                             scratch);
+    else
+        lc::norm_partial_kernel<double><<<blocks, lc::kNormThreads, 0, s>>>(static_cast<const double *>(out), ref,
+                                                                              n, scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return lc::cuda_fail(e);
+    lc::norm_final_kernel<<<1, lc::kNormThreads, 0, s>>>(scratch, blocks, sums);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? LC_OK : lc::cuda_fail(e);
+}
 
 lc_status lc_error_norm_workspace_size(int64_t n, size_t *bytes)
 {

@@ -68,6 +68,7 @@ SIGNATURES = {
     "lc_device_error": ([ctypes.c_int], ctypes.c_int),
     "lc_error_norm_workspace_size": ([_I64, ctypes.POINTER(_SZ)], ctypes.c_int),
     "lc_error_norm": ([_P, _I32, _P, _I64, _P, _P, _SZ, _P], ctypes.c_int),
+    "lc_error_norm_noalloc": ([_P, _I32, _P, _I64, _P, _P], ctypes.c_int),
     "lc_device_info": ([ctypes.POINTER(_I32)] * 3, ctypes.c_int),
     "lc_grouped_workspace_size": ([_P, _VP, ctypes.POINTER(lc_group), _I32, ctypes.POINTER(_SZ)], ctypes.c_int),
     "lc_grouped_plan_create": ([_P, _VP, ctypes.POINTER(lc_group), _I32, _P, _SZ, _I32, _P, ctypes.POINTER(_P)],
