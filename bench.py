@@ -204,7 +204,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--E", type=int, default=0, help="override the workload's element count (profiling)")
     ap.add_argument("--precision", default="", choices=["", "fp32", "fp64", "bf16", "bf16x3"],
-                    help="arithmetic path (default: the workload's; fp32 workloads also run bf16/bf16x3)")
+                    help="arithmetic path; default: bf16x3 (three-term split on the tensor cores, error "
+                         "within the FP32 bound) for FP32 workloads, fp64 for the FP64 workload")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -214,6 +215,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     wl = dict(WORKLOADS[args.workload])
     wl["storage"] = "fp64" if wl["precision"] == "fp64" else "fp32"
+    if not args.precision and wl["storage"] == "fp32":
+        args.precision = "bf16x3"
     if args.precision:
         if (args.precision == "fp64") != (wl["storage"] == "fp64"):
             ap.error("fp64 arithmetic needs an fp64 workload and vice versa")

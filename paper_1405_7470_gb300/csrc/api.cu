@@ -772,8 +772,9 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         const size_t W = 2 * (size_t)t.KB;
         auto plan = [&](int G, TcArgs &q) -> bool {
             q.G = G;
-            q.CB = G * N;
-            q.CBp = (q.CB + 15) / 16 * 16;
+            q.Np = (N + 15) / 16 * 16;
+            q.CB = G * q.Np;
+            q.CBp = q.CB;
             if (q.CBp > 256)
                 return false;
             q.tmem_cols = 32;

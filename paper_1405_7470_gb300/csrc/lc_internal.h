@@ -80,7 +80,8 @@ struct TcArgs {
     int N, F;
     int G;          // operators per column block
     int nblocks;    // column blocks (ceil(F / G))
-    int CB, CBp;    // columns per block (G * N) and the MMA N (CB rounded up to 16)
+    int Np;         // accumulator columns per operator: N rounded up to 16
+    int CB, CBp;    // columns per block (G * Np) and the MMA N (= CB)
     int Kp, KB, nkb;  // K padded to 16, K-block width (16/32/64 -> 32/64/128-byte swizzle), blocks
     int tmem_cols;  // columns per accumulator (power of two >= CBp)
     int stages;     // u stage buffers (1 or 2)

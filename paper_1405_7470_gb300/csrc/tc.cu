@@ -74,6 +74,19 @@ __device__ __forceinline__ void tc_commit(uint64_t *bar)
                  : "memory");
 }
 
+// 16 consecutive accumulator columns of this thread's TMEM lane (complete after tmem_wait).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 // 32 consecutive accumulator columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
 {
@@ -168,6 +181,7 @@ __global__ void __launch_bounds__(576, 1) tc_contract_kernel(const __grid_consta
     const uint32_t sbase = smem_addr(smem);
 
     const int N = a.N, G = a.G, CBp = a.CBp, Kp = a.Kp, KB = a.KB, nkb = a.nkb;
+    const int Np = a.Np;  // accumulator columns per operator (N rounded up to 16)
     const int W = 2 * KB;  // bytes per row of a K-block
     const long long E = a.E;
     const int S = a.stages, NA = a.abufs;
@@ -180,7 +194,6 @@ __global__ void __launch_bounds__(576, 1) tc_contract_kernel(const __grid_consta
     const int blk = blockIdx.x % a.nblocks;  // this CTA's column block
     const int f0 = blk * G;
     const int Gb = min(G, a.F - f0);  // operators in this block
-    const int CBb = Gb * N;           // valid columns
 
     const uint32_t termB = (uint32_t)nkb * CBp * W;  // bytes per B term
     const uint32_t offA = NT * termB;
@@ -212,17 +225,18 @@ __global__ void __launch_bounds__(576, 1) tc_contract_kernel(const __grid_consta
         fence_mbar_init();
     }
 
-    // B terms: row n = f_local*N + i of this block, column k = j; zero padding.
+    // B terms: row n = f_local*Np + i of this block (i < N), column k = j; zero padding.
     {
         const int c8n = Kp / 8;
         for (int idx = tid; idx < CBp * c8n; idx += blockDim.x) {
             const int n = idx / c8n, c8 = idx - n * c8n;
             float x[8];
-            const int fl = n / N, i = n - fl * N;
+            const int fl = n / Np, i = n - fl * Np;
+            const bool valid = fl < Gb && i < N;
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int j = c8 * 8 + q;
-                x[q] = (n < CBb && j < N) ? a.D[((size_t)(f0 + fl) * N + i) * N + j] : 0.f;
+                x[q] = (valid && j < N) ? a.D[((size_t)(f0 + fl) * N + i) * N + j] : 0.f;
             }
             uint4 t[3];
             split8<NT>(x, t);
@@ -347,19 +361,22 @@ __global__ void __launch_bounds__(576, 1) tc_contract_kernel(const __grid_consta
             const float *st = stage + (size_t)s * TE * N;
             unsigned char *Ab = smem + offA + (size_t)ab * bufA;
             const int c8n = Kp / 8;
+            // this thread's row of u: stage (or global memory for unaligned tail tiles)
+            const float *src = from_stage ? (NODE ? st + row : st + row * N)
+                                          : (NODE ? a.u + e0 + row : a.u + (e0 + row) * N);
+            const long long jstride = from_stage ? (NODE ? TE : 1) : (NODE ? E : 1);
+            const bool rowv = row < TEv;
             for (int c8 = part; c8 < c8n; c8 += H) {
                 float x[8];
+                const float *p8 = src + (long long)c8 * 8 * jstride;
+                if (rowv && c8 * 8 + 8 <= N) {
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int j = c8 * 8 + q;
-                    float val = 0.f;
-                    if (j < N && row < TEv) {
-                        if (from_stage)
-                            val = NODE ? st[j * TE + row] : st[row * N + j];
-                        else
-                            val = NODE ? a.u[(size_t)j * E + e0 + row] : a.u[(e0 + row) * N + j];
-                    }
-                    x[q] = val;
+                    for (int q = 0; q < 8; ++q)
+                        x[q] = p8[q * jstride];
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        x[q] = (rowv && c8 * 8 + q < N) ? p8[q * jstride] : 0.f;
                 }
                 uint4 tt4[3];
                 split8<NT>(x, tt4);
@@ -403,32 +420,42 @@ __global__ void __launch_bounds__(576, 1) tc_contract_kernel(const __grid_consta
                 workers_sync(NWT);
             }
             const uint32_t tbase = tmem_base + (uint32_t)b * a.tmem_cols + ((uint32_t)((warp & 3) * 32) << 16);
-            for (int c0 = part * 32; c0 < CBp; c0 += 32 * H) {
-                float v[32];
-                tmem_ld32(tbase + (uint32_t)c0, v);
-                if (c0 >= CBb)
-                    continue;
-                int fl = c0 / N, i = c0 - fl * N;
-                if (NODE) {
-                    if (row < TEv) {
-                        float *o = a.out + ((size_t)(f0 + fl) * N + i) * E + e0 + row;
+            // this warp's 16-column chunks c0 = 16*(part + H*k); each lies inside one operator
+            for (int c0 = part * 16; c0 < CBp; c0 += 64 * H) {
+                uint32_t r[4][16];
 #pragma unroll
-                        for (int q = 0; q < 32; ++q) {
-                            if (c0 + q < CBb)
-                                *o = v[q];
-                            o += E;
+                for (int k4 = 0; k4 < 4; ++k4)
+                    if (c0 + k4 * 16 * H < CBp)
+                        tmem_ld16(tbase + (uint32_t)(c0 + k4 * 16 * H), r[k4]);
+                tmem_wait();
+#pragma unroll
+                for (int k4 = 0; k4 < 4; ++k4) {
+                    const int cc = c0 + k4 * 16 * H;
+                    if (cc >= CBp)
+                        continue;
+                    const int fl = cc / Np, i0 = cc - fl * Np;
+                    const int nv = min(16, N - i0);  // valid columns of this chunk
+                    if (fl >= Gb || nv <= 0)
+                        continue;
+                    if (NODE) {
+                        if (row < TEv) {
+                            float *o = a.out + ((size_t)(f0 + fl) * N + i0) * E + e0 + row;
+#pragma unroll
+                            for (int q = 0; q < 16; ++q)
+                                if (q < nv)
+                                    o[(size_t)q * E] = __uint_as_float(r[k4][q]);
                         }
-                    }
-                } else {
-                    int o = (fl * TE + row) * N + i;
+                    } else {
+                        float *o = ost + (fl * TE + row) * N + i0;
+                        if (nv == 16) {
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) {
-                        if (c0 + q < CBb)
-                            ost[o] = v[q];
-                        ++o;
-                        if (++i == N) {
-                            i = 0;
-                            o += (TE - 1) * N;
+                            for (int q = 0; q < 16; ++q)
+                                o[q] = __uint_as_float(r[k4][q]);
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 16; ++q)
+                                if (q < nv)
+                                    o[q] = __uint_as_float(r[k4][q]);
                         }
                     }
                 }
