@@ -173,6 +173,14 @@ lc_status lc_contract_host(const lc_kernel *k, const lc_variant *v, const void *
  */
 lc_status lc_device_error(int clear);
 
+/*
+ * Failure-path self-test: enqueue a one-warp kernel whose bounded mbarrier wait is made
+ * to run out (nothing ever arrives) after limit_ns (1 ns .. 1 s).  The kernel then sets
+ * the device error word exactly as a pipeline wait that gave up would, and returns; no
+ * fault, no hang.  lc_device_error(…) then reports LC_ERR_TIMEOUT.
+ */
+lc_status lc_selftest_wait_timeout(int64_t limit_ns, void *stream);
+
 /* ------------------------------------------------------------------------- */
 /* Grouped launch: several problems of different sizes in one persistent      */
 /* kernel, optionally captured once in a CUDA graph and replayed.             */

@@ -7,8 +7,25 @@
 #include <mutex>
 
 #include "lc_internal.h"
+#include "tma.cuh"
 
 namespace lc {
+
+// Self-test of the bounded-wait error path: wait on an mbarrier phase that nothing
+// completes; after limit_ns the wait gives up and the kernel records the timeout in
+// the device error word, as every pipeline wait in the library does.
+__global__ void selftest_wait_kernel(unsigned long long limit_ns, unsigned int *err)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_ns(&bar, 0, limit_ns);
+    if (!__syncthreads_and(ok) && threadIdx.x == 0)
+        atomicOr(err, 1u);
+}
 
 static constexpr int kNormBlocks = 1024;
 static constexpr int kNormThreads = 256;
@@ -173,6 +190,18 @@ lc_status lc_error_norm_noalloc(const void *out, int32_t out_dtype, const double
         return lc::cuda_fail(e);
     lc::norm_final_kernel<<<1, lc::kNormThreads, 0, s>>>(scratch, blocks, sums);
     e = cudaGetLastError();
+    return e == cudaSuccess ? LC_OK : lc::cuda_fail(e);
+}
+
+lc_status lc_selftest_wait_timeout(int64_t limit_ns, void *stream)
+{
+    if (limit_ns < 1 || limit_ns > 1000000000LL)
+        return LC_ERR_INVALID_ARGUMENT;
+    unsigned int *err = lc::error_word();
+    if (!err)
+        return LC_ERR_NO_DEVICE;
+    lc::selftest_wait_kernel<<<1, 32, 0, (cudaStream_t)stream>>>((unsigned long long)limit_ns, err);
+    cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? LC_OK : lc::cuda_fail(e);
 }
 

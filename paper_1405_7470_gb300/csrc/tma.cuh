@@ -73,6 +73,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase)
     }
 }
 
+// Bounded wait with an explicit limit in nanoseconds.
+__device__ __forceinline__ bool mbar_wait_ns(uint64_t *bar, uint32_t phase, uint64_t limit_ns)
+{
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, phase))
+            return true;
+        if (global_ns() - t0 > limit_ns)
+            return false;
+    }
+}
+
 // 1-D bulk copy global -> shared, completing `bytes` on the mbarrier.
 // dst, src 16-byte aligned; bytes a multiple of 16.
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)

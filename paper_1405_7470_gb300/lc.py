@@ -66,6 +66,7 @@ SIGNATURES = {
     "lc_contract": ([_P, _VP, _P, _P, _P, _I64, _I32, _I32, _P], ctypes.c_int),
     "lc_contract_host": ([_P, _VP, _P, _P, _P, _I64, _I32, _I32, _P, _P, _P, _P], ctypes.c_int),
     "lc_device_error": ([ctypes.c_int], ctypes.c_int),
+    "lc_selftest_wait_timeout": ([_I64, _P], ctypes.c_int),
     "lc_error_norm_workspace_size": ([_I64, ctypes.POINTER(_SZ)], ctypes.c_int),
     "lc_error_norm": ([_P, _I32, _P, _I64, _P, _P, _SZ, _P], ctypes.c_int),
     "lc_error_norm_noalloc": ([_P, _I32, _P, _I64, _P, _P], ctypes.c_int),
