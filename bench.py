@@ -123,11 +123,15 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
-def choose_variant(lc, kernel, wl, layout, spec):
+def choose_variant(lc, kernel, wl, layout, spec, D, u, out, stream):
+    """'auto': the autotuner's fastest descriptor on this very problem (timed before, and
+    outside, the benchmark's timed region); 'default': lc_variant_default; else JSON fields."""
+    if spec == "auto":
+        res = lc.autotune(kernel, D, u, out, layout, wl["precision"], reps=3, stream=stream)
+        return res[0][1], len(res)
     if spec and spec != "default":
-        d = json.loads(spec)
-        return lc.Variant(**d)
-    return lc.variant_default(kernel, wl["E"], wl["N"], wl["F"], layout, wl["precision"])
+        return lc.Variant(**json.loads(spec)), 0
+    return lc.variant_default(kernel, wl["E"], wl["N"], wl["F"], layout, wl["precision"]), 0
 
 
 def roofline_for(v, wl, peaks, sms, t_launch_s, workload_key):
@@ -199,7 +203,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fp32_three", choices=sorted(WORKLOADS))
     ap.add_argument("--layout", default="elem", choices=["elem", "node"])
-    ap.add_argument("--variant", default="default", help="JSON descriptor fields or 'default'")
+    ap.add_argument("--variant", default="auto",
+                    help="'auto' (autotuned before timing), 'default', or JSON descriptor fields")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--E", type=int, default=0, help="override the workload's element count (profiling)")
@@ -254,13 +259,13 @@ def main():
     u_in = synth.to_node_major(u) if args.layout == "node" else u
     kernel = lc.Kernel() if F > 1 else lc.Kernel("{ [e,i,j]: 0<=e<E and 0<=i,j<N }",
                                                   "out[e,i] = sum(j, D[i,j]*u[e,j])")
-    v = choose_variant(lc, kernel, wl, args.layout, args.variant)
-    vd = lc.variant_dict(v)
     stream = torch.cuda.Stream()
     Dd = torch.from_numpy(D).cuda()
     ud = torch.from_numpy(np.ascontiguousarray(u_in)).cuda()
     shape = (F, N, E) if args.layout == "node" else (F, E, N)
     out = torch.empty(shape, dtype=ud.dtype, device="cuda")
+    v, n_tuned = choose_variant(lc, kernel, wl, args.layout, args.variant, Dd, ud, out, stream)
+    vd = lc.variant_dict(v)
     flops = 2.0 * E * N * N * F
 
     def step():
@@ -352,7 +357,9 @@ def main():
             "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16 (f32 accumulate)",
                       "bf16x3": "bf16x3 split (f32 accumulate)"}[wl["precision"]], "data": "synthetic",
             "config": {"workload": wl["desc"], "E": E, "N": N, "F": F, "layout": args.layout,
-                       "precision": wl["precision"], "variant": vd, "parallelism": f"replicas x{world}",
+                       "precision": wl["precision"], "variant": vd,
+                       "variant_choice": f"autotuned over {n_tuned} candidates" if n_tuned else args.variant,
+                       "parallelism": f"replicas x{world}",
                        "l2": "inputs+outputs larger than L2 (no flush needed)",
                        "bytes_per_step": (8 if wl["precision"] == "fp64" else 4) * (E * N * (1 + F) + F * N * N)},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
