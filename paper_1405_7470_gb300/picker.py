@@ -147,7 +147,10 @@ def train(X: np.ndarray, y: np.ndarray, epochs: int = 1000, batch: int = 512, lr
     params = torch.from_numpy(he_uniform(din, seed)).cuda()
     m = torch.zeros_like(params)
     v = torch.zeros_like(params)
-    ws = None
+    import ctypes
+    wsb = ctypes.c_size_t(0)
+    lc.check(lc.load().lc_mlp_workspace_size(din, ctypes.byref(wsb)), "lc_mlp_workspace_size")
+    ws = torch.empty(wsb.value // 4 + 4, dtype=torch.float32, device="cuda")
     rng = np.random.default_rng(seed)
     step, hist = 0, []
     for ep in range(epochs):
