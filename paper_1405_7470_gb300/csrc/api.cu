@@ -609,10 +609,10 @@ static bool implies_E_multiple_of(const Kernel &K, long long m)
 
 // ------------------------------------------------------------------ validation
 
-// Warp shape WE x WC and column groups CG (a multiple of WC) for a SIMT tile: the fewest
-// padded columns within `max_threads` (and within `req_threads` when > 0: a CTA of that size
-// whose surplus warps only help with loads) and the shared memory left for D^T after `fixed`
-// bytes.
+// Warp shape WE x WC and column groups CG (a multiple of WC) covering C columns in one
+// pass: the fewest padded columns within `max_threads` (and within `req_threads` when > 0:
+// a CTA of that size whose surplus warps only help with loads) and the shared memory left
+// for D^T after `fixed` bytes.
 static bool simt_warp_shape(SimtGeom &g, int C, int N, int es, size_t fixed, size_t smem_cap, int max_threads,
                             int req_threads)
 {
@@ -633,8 +633,9 @@ static bool simt_warp_shape(SimtGeom &g, int C, int N, int es, size_t fixed, siz
         if (cg < wc)
             continue;
         const long long cw = cg * g.RC;
-        const long long nch = (C + cw - 1) / cw;
-        const long long waste = nch * cw - C + (nch - 1) * 4;  // extra chunks reload D
+        if (cw < C)
+            continue;  // the CTA's whole column block must fit one pass
+        const long long waste = cw - C;
         if (best_waste < 0 || waste < best_waste) {
             best_waste = waste;
             g.WC = wc;
@@ -713,30 +714,50 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
             return LC_ERR_INVALID_VARIANT;
         g.stages = v->stages;
         const bool node = v->layout == LC_LAYOUT_NODE_MAJOR;
-        const int C = F * N;
-        size_t fixed = 16;  // mbarriers + u tiles + output staging
+        // column blocks of G whole operators, one per CTA with its D^T resident: the most
+        // operators per block that fit (fewer blocks re-reading the same u tile)
+        bool fits = false;
+        size_t fixed = 0;
+        size_t fixed_u = 16;  // mbarriers + u tiles
         if (v->prefetch_smem)
-            fixed += node ? (size_t)g.stages * N * g.TE * es
-                          : (size_t)N * (g.TE + VEC) * es + (size_t)g.stages * g.TE * N * es;
-        if (!node)
-            fixed += (size_t)F * g.TE * N * es;
-        if (!simt_warp_shape(g, C, N, es, fixed, smem_cap, max_threads, req_threads))
+            fixed_u += node ? (size_t)g.stages * N * g.TE * es
+                            : (size_t)N * (g.TE + VEC) * es + (size_t)g.stages * g.TE * N * es;
+        g.isplit = 0;
+        for (int G = F; G >= 1 && !fits; --G) {
+            fixed = fixed_u + (node ? 0 : (size_t)G * g.TE * N * es);  // + output staging
+            if (simt_warp_shape(g, G * N, N, es, fixed, smem_cap, max_threads, req_threads)) {
+                g.G = G;
+                fits = true;
+            }
+        }
+        // one operator's D^T does not fit: blocks of rows of one operator
+        for (int parts = 2; parts <= N && !fits; ++parts) {
+            const int w = (N + parts - 1) / parts;
+            fixed = fixed_u + (node ? 0 : (size_t)g.TE * w * es);
+            if (simt_warp_shape(g, w, N, es, fixed, smem_cap, max_threads, req_threads)) {
+                g.G = 1;
+                g.isplit = w;
+                fits = true;
+            }
+        }
+        if (!fits)
             return LC_ERR_INVALID_VARIANT;
         g.threads = g.EG * g.CG;
         g.CW = g.CG * g.RC;
-        g.nchunks = (C + g.CW - 1) / g.CW;
+        g.nchunks = g.isplit ? F * ((N + g.isplit - 1) / g.isplit) : (F + g.G - 1) / g.G;
         g.smem = fixed + (size_t)N * g.CW * es;
         if (g.smem > smem_cap || g.threads > max_threads || g.threads % 32 != 0)
             return LC_ERR_INVALID_VARIANT;
         g.bulk = v->prefetch_smem && (!node || E % VEC == 0);
         g.bulk_store = !node && ((E * (long long)N) % VEC == 0);
         g.ntiles = (E + g.TE - 1) / g.TE;
-        long long grid = g.ntiles;
+        long long grid = std::max<long long>(g.ntiles, 1) * g.nchunks;
         if (v->ctas_per_sm > 0)
             grid = std::min<long long>(grid, (long long)v->ctas_per_sm * sms);
+        grid = std::max<long long>(grid / g.nchunks * g.nchunks, g.nchunks);  // whole column-block sets
         if (grid > 0x7fffffffLL)
             return LC_ERR_INVALID_VARIANT;
-        g.grid = (int)std::max<long long>(grid, 1);
+        g.grid = (int)grid;
         return LC_OK;
     }
     if (v->engine == LC_ENGINE_TCGEN05) {
@@ -1152,6 +1173,8 @@ lc_status lc_contract(const lc_kernel *kh, const lc_variant *v, const void *D, c
         a.CG = r.g.CG;
         a.CW = r.g.CW;
         a.nchunks = r.g.nchunks;
+        a.G = r.g.G;
+        a.isplit = r.g.isplit;
         a.WC = r.g.WC;
         a.stages = r.g.stages;
         a.bulk = r.g.bulk;
@@ -1264,10 +1287,11 @@ static lc_status grouped_plan_host(const Kernel &K, const lc_variant *v, const l
             return LC_ERR_INVALID_ARGUMENT;
         if (!aligned16(G.D_dev) || !aligned16(G.u_dev) || !aligned16(G.out_dev))
             return LC_ERR_MISALIGNED;
-        // tile of TE = EG * RE elements with exactly T threads: the fewest padded columns,
-        // then the tile closest to 128 elements
+        // tile of TE = EG * RE elements within T threads: the most active threads, then the
+        // fewest padded columns, then the largest tile (fewer, longer bulk copies per tile)
         Resolved best;
-        long long best_key = -1;
+        double best_key = 0;
+        bool have = false;
         for (int eg = 4; eg <= T; eg *= 2) {
             lc_variant vg = *v;
             vg.tile_e = eg * v->elems_per_thread;
@@ -1275,14 +1299,17 @@ static lc_status grouped_plan_host(const Kernel &K, const lc_variant *v, const l
             Resolved r;
             if (resolve(K, G.E, G.N, G.F, &vg, r, true, T) != LC_OK)
                 continue;
-            const long long pad = (long long)r.g.nchunks * r.g.CW - (long long)G.F * G.N;
-            const long long key = pad * 64 + std::abs((int)std::log2((double)vg.tile_e / 128.0) * 4);
-            if (best_key < 0 || key < best_key) {
+            const double idle = (double)(T - r.g.threads) / T;
+            const double pad = (double)(r.g.nchunks * (long long)r.g.CW) / ((double)G.F * G.N) - 1.0;
+            const double key = idle * 4.0 + pad - 0.05 * std::log2((double)vg.tile_e);
+            if (!have || key < best_key) {
                 best_key = key;
                 best = r;
+                have = true;
             }
         }
-        if (best_key < 0)
+        const long long best_key_ok = have ? 0 : -1;
+        if (best_key_ok < 0)
             return LC_ERR_INVALID_VARIANT;
         SimtArgs a;
         memset(&a, 0, sizeof a);
@@ -1298,6 +1325,8 @@ static lc_status grouped_plan_host(const Kernel &K, const lc_variant *v, const l
         a.CG = best.g.CG;
         a.CW = best.g.CW;
         a.nchunks = best.g.nchunks;
+        a.G = best.g.G;
+        a.isplit = best.g.isplit;
         a.WC = best.g.WC;
         a.stages = best.g.stages;
         a.bulk = best.g.bulk;
@@ -1306,10 +1335,10 @@ static lc_status grouped_plan_host(const Kernel &K, const lc_variant *v, const l
         a.tail_free = 0;
         P.groups[gi] = a;
         P.smem = std::max(P.smem, best.g.smem);
-        ntiles[gi] = G.E > 0 ? best.g.ntiles : 0;
-        // estimated seconds per tile: FMA pipe (FP32, padded columns) vs HBM
-        const double flops = 2.0 * a.TE * (double)G.N * a.CW * a.nchunks;
-        const double bytes = 4.0 * a.TE * (double)G.N * (1 + G.F);
+        ntiles[gi] = G.E > 0 ? best.g.ntiles * best.g.nchunks : 0;  // (tile, column block) items
+        // estimated seconds per item: FMA pipe (FP32, padded columns) vs HBM
+        const double flops = 2.0 * a.TE * (double)G.N * a.CW;
+        const double bytes = 4.0 * a.TE * ((double)G.N + (a.isplit ? a.isplit : (double)a.G * G.N));
         tile_cost[gi] = std::max(flops / (sms * 128 * 2 * 1.9e9), bytes / 6.8e12) + 2e-7 / sms;
     }
     double total = 0;
@@ -1327,10 +1356,14 @@ static lc_status grouped_plan_host(const Kernel &K, const lc_variant *v, const l
     int b = 0;
     double acc = 0;
     for (int gi = 0; gi < ng; ++gi) {
+        // items of group gi: column block major, then tiles
+        const long long tiles_g = P.groups[gi].ntiles;
         long long t = 0;
         while (t < ntiles[gi]) {
-            // tiles of this group that fit in CTA b's remaining budget (at least one)
-            long long take = ntiles[gi] - t;
+            // items of this group that fit in CTA b's remaining budget (at least one), not
+            // crossing a column block
+            const long long chunk = t / tiles_g, t_in = t - chunk * tiles_g;
+            long long take = tiles_g - t_in;
             if (b < P.grid - 1) {
                 const double room = (b + 1) * target - acc;
                 long long fit = (long long)std::ceil(room / tile_cost[gi]);
@@ -1338,8 +1371,8 @@ static lc_status grouped_plan_host(const Kernel &K, const lc_variant *v, const l
             }
             GroupSeg sg;
             sg.group = gi;
-            sg.pad = 0;
-            sg.first = t;
+            sg.chunk = (int)chunk;
+            sg.first = t_in;
             sg.count = take;
             P.segs.push_back(sg);
             t += take;

@@ -19,7 +19,7 @@ __global__ void __launch_bounds__(256) grouped_contract_kernel(GroupedArgs g)
         const GroupSeg sg = g.segs[si];
         SimtArgs a = g.groups[sg.group];
         a.err = g.err;
-        simt_tiles<float, RE, RC, UNR, LAYOUT, PF>(a, sg.first, 1, sg.first + sg.count, smem_raw);
+        simt_tiles<float, RE, RC, UNR, LAYOUT, PF>(a, sg.chunk, sg.first, 1, sg.first + sg.count, smem_raw);
     }
 }
 

@@ -38,8 +38,10 @@ struct SimtGeom {
     int bulk;      // u tiles fetched by the bulk-copy engine
     int bulk_store;  // element-major output tiles written by bulk stores
     int TE;        // elements per tile (= EG * RE)
-    int CW;        // columns per chunk (= CG * RC)
-    int nchunks;   // column chunks covering C = F * N
+    int CW;        // columns of the resident D^T block (= CG * RC >= G * N)
+    int G;         // operators per column block (one block per CTA)
+    int isplit;    // > 0: blocks are row ranges of one operator (its D^T does not fit)
+    int nchunks;   // column blocks: ceil(F / G)
     int threads;   // EG * CG
     size_t smem;   // dynamic shared memory bytes
     long long ntiles;
@@ -53,6 +55,8 @@ struct SimtArgs {
     long long E;
     int N, F, C;
     int TE, EG, CG, CW, nchunks;
+    int G;          // operators per column block
+    int isplit;     // > 0: column blocks are row ranges of this many rows of one operator
     int WC, stages, bulk, bulk_store;
     long long ntiles;
     int tail_free;
@@ -99,7 +103,7 @@ lc_status tc_launch(const TcArgs &a, int layout, int nterms, int grid, cudaStrea
 // Grouped launch: per-group SIMT arguments, contiguous tile ranges, ranges per CTA.
 struct GroupSeg {
     int group;
-    int pad;
+    int chunk;  // column block of the group
     long long first, count;
 };
 struct GroupedArgs {

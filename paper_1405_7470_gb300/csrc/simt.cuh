@@ -50,12 +50,13 @@ struct VecT<double> {
 // Threads per CTA allowed for a register block (the 8 x 8 FP32 block needs > 128 registers).
 __host__ __device__ constexpr int simt_max_threads(int re, int rc) { return re * rc >= 64 ? 256 : 512; }
 
-// One CTA's share of a contraction: tiles t_first, t_first + t_step, ... below t_end.
-// Used by the plain kernel (grid-stride over all tiles) and by the grouped kernel
-// (contiguous tile ranges of several problems, one after the other).
+// One CTA's share of a contraction: column block `ch` (operators ch*G .. ch*G + G - 1,
+// their D^T resident in shared memory for the whole call) of the tiles t_first,
+// t_first + t_step, ... below t_end.  Used by the plain kernel (grid-stride over all
+// tiles) and by the grouped kernel (contiguous tile ranges of several problems).
 template <typename T, int RE, int RC, int UNR, int LAYOUT, bool PREFETCH>
-__device__ __forceinline__ void simt_tiles(const SimtArgs &a, long long t_first, long long t_step, long long t_end,
-                                           unsigned char *smem_raw)
+__device__ __forceinline__ void simt_tiles(const SimtArgs &a, int ch, long long t_first, long long t_step,
+                                           long long t_end, unsigned char *smem_raw)
 {
     constexpr int VEC = VecT<T>::n;
     using V = typename VecT<T>::type;
@@ -65,7 +66,16 @@ __device__ __forceinline__ void simt_tiles(const SimtArgs &a, long long t_first,
     constexpr bool NODE = LAYOUT == LC_LAYOUT_NODE_MAJOR;
     constexpr int ES = (int)sizeof(T);
 
-    const int N = a.N, F = a.F, C = a.C, TE = a.TE, EG = a.EG, CG = a.CG, CW = a.CW;
+    const int N = a.N, F = a.F, TE = a.TE, EG = a.EG, CG = a.CG, CW = a.CW;
+    // Column block `ch`: G whole operators (isplit == 0), or rows [i_lo, i_lo + width) of
+    // one operator (isplit = width > 0, when one operator's D^T does not fit).
+    const bool whole = a.isplit == 0;
+    const int nsub = whole ? 1 : (N + a.isplit - 1) / a.isplit;
+    const int f0 = whole ? ch * a.G : ch / nsub;                 // first operator of the block
+    const int Gb = whole ? min(a.G, F - f0) : 1;                 // operators in the block
+    const int i_lo = whole ? 0 : (ch % nsub) * a.isplit;
+    const int Cb = whole ? Gb * N : min(a.isplit, N - i_lo);     // columns of the block
+    const int orow = whole ? N : Cb;                             // staged output row length
     const long long E = a.E;
     const int S = a.stages;
     const T *__restrict__ D = static_cast<const T *>(a.D);
@@ -99,18 +109,18 @@ __device__ __forceinline__ void simt_tiles(const SimtArgs &a, long long t_first,
         }
     }
     if (!NODE)
-        ost = p;  // [F][TE][N]
+        ost = p;  // [Gb][TE][N]
 
-    // precompute(D): Ds[j][cg*RC + m] = D[f][i][j] with c = ch*CW + cg + m*CG = f*N + i.
-    auto load_D = [&](int ch) {
+    // precompute(D): Ds[j][cg*RC + m] = D[f][i][j] for block column c = cg + m*CG < Cb.
+    auto load_D = [&]() {
         for (int idx = tid; idx < N * CW; idx += nthr) {
             int j = idx / CW, q = idx - j * CW;
             int g = q / RC, m = q - g * RC;
-            int c = ch * CW + g + m * CG;
+            int c = g + m * CG;
             T val = T(0);
-            if (c < C) {
-                int f = c / N, i = c - f * N;
-                val = D[((size_t)f * N + i) * N + j];
+            if (c < Cb) {
+                int fl = whole ? c / N : 0, i = whole ? c - fl * N : i_lo + c;
+                val = D[((size_t)(f0 + fl) * N + i) * N + j];
             }
             Ds[idx] = val;
         }
@@ -122,8 +132,7 @@ __device__ __forceinline__ void simt_tiles(const SimtArgs &a, long long t_first,
             mbar_init(&bars[s], 1);
         fence_mbar_init();
     }
-    if (a.nchunks == 1)
-        load_D(0);
+    load_D();
     __syncthreads();
 
     // Warp 0 fetches tile `t` into ring slot `buf`.
@@ -153,19 +162,16 @@ __device__ __forceinline__ void simt_tiles(const SimtArgs &a, long long t_first,
         }
     }
 
-    // Output offsets of this thread's RC columns c = f*N + i (chunk 0; recomputed per
-    // chunk only when the columns do not fit one chunk).
+    // Output offsets of this thread's RC columns c = cg + y*CG of the block (-1: padding).
     using Off = typename std::conditional<NODE, long long, int>::type;
     Off coff[RC];
-    auto col_offsets = [&](int ch) {
 #pragma unroll
-        for (int y = 0; y < RC; ++y) {
-            const int c = ch * CW + cg + y * CG;
-            const int f = c / N, i = c - f * N;
-            coff[y] = c >= C ? Off(-1) : (NODE ? Off(((long long)f * N + i) * E) : Off(f * TE * N + i));
-        }
-    };
-    col_offsets(0);
+    for (int y = 0; y < RC; ++y) {
+        const int c = cg + y * CG;
+        const int fl = whole ? c / N : 0, il = whole ? c - fl * N : c;  // il: index in the staged row
+        coff[y] = c >= Cb ? Off(-1)
+                          : (NODE ? Off(((long long)(f0 + fl) * N + i_lo + il) * E) : Off(fl * TE * orow + il));
+    }
 
     int k = 0;
     for (long long tile = t_first; tile < t_end; tile += t_step, ++k) {
@@ -248,15 +254,7 @@ __device__ __forceinline__ void simt_tiles(const SimtArgs &a, long long t_first,
             __syncthreads();
         }
 
-        for (int ch = 0; ch < a.nchunks; ++ch) {
-            if (a.nchunks > 1) {
-                __syncthreads();
-                load_D(ch);
-                col_offsets(ch);
-                __syncthreads();
-            }
-            if (!active)
-                continue;
+        if (active) {
             T acc[RE][RC];
 #pragma unroll
             for (int x = 0; x < RE; ++x)
@@ -330,14 +328,14 @@ __device__ __forceinline__ void simt_tiles(const SimtArgs &a, long long t_first,
                     }
                 }
             } else {
-                T *o = ost + eg * RE * N;
+                T *o = ost + eg * RE * orow;
 #pragma unroll
                 for (int x = 0; x < RE; ++x) {
 #pragma unroll
                     for (int y = 0; y < RC; ++y)
                         if (coff[y] >= 0)
                             o[coff[y]] = acc[x][y];
-                    o += N;
+                    o += orow;
                 }
             }
         }
@@ -356,15 +354,23 @@ __device__ __forceinline__ void simt_tiles(const SimtArgs &a, long long t_first,
             fence_async_smem();
             __syncthreads();
             const int total = TEv * N;
-            if (a.bulk_store && ((total * ES) & 15) == 0) {
+            if (!whole) {
+                // rows [i_lo, i_lo + Cb) of each element: one short segment per element
+                for (int q = tid; q < TEv * Cb; q += nthr) {
+                    const int e = q / Cb, c = q - e * Cb;
+                    out[((size_t)f0 * E + e0 + e) * N + i_lo + c] = ost[q];
+                }
+            } else if (a.bulk_store && ((total * ES) & 15) == 0) {
                 if (tid == 0) {
-                    for (int f = 0; f < F; ++f)
-                        bulk_s2g(out + ((size_t)f * E + e0) * N, ost + (size_t)f * TE * N, (uint32_t)total * ES);
+                    for (int g = 0; g < Gb; ++g)
+                        bulk_s2g(out + ((size_t)(f0 + g) * E + e0) * N, ost + (size_t)g * TE * N,
+                                 (uint32_t)total * ES);
                     bulk_commit();
                 }
             } else {
-                for (int f = 0; f < F; ++f) {
-                    const T *src = ost + (size_t)f * TE * N;
+                for (int g = 0; g < Gb; ++g) {
+                    const int f = f0 + g;
+                    const T *src = ost + (size_t)g * TE * N;
                     T *dst = out + ((size_t)f * E + e0) * N;
                     int done = 0;
                     if (((((size_t)f * E + e0) * N) % VEC) == 0) {
@@ -393,7 +399,9 @@ template <typename T, int RE, int RC, int UNR, int LAYOUT, bool PREFETCH>
 __global__ void __launch_bounds__(simt_max_threads(RE, RC)) simt_contract_kernel(SimtArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    simt_tiles<T, RE, RC, UNR, LAYOUT, PREFETCH>(a, blockIdx.x, gridDim.x, a.ntiles, smem_raw);
+    const int nb = a.nchunks;
+    simt_tiles<T, RE, RC, UNR, LAYOUT, PREFETCH>(a, blockIdx.x % nb, blockIdx.x / nb, gridDim.x / nb, a.ntiles,
+                                                 smem_raw);
 }
 
 // Host-side dispatch over the compiled instances of one element type and layout.

@@ -135,21 +135,31 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b)
     return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
-// Split 8 floats into NT bfloat16 terms (hi, mid, lo), each packed as 16 bytes.
+// Round two floats to a packed bfloat16 pair (nearest-even): lo half = a, hi half = b.
+__device__ __forceinline__ uint32_t cvt_bf16x2(float a, float b)
+{
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+    return r;
+}
+
+// Split 8 floats into NT bfloat16 terms (hi, mid, lo), each packed as 16 bytes:
+// hi = rn(x), mid = rn(x - hi), lo = rn(x - hi - mid); both differences are exact.
 template <int NT>
 __device__ __forceinline__ void split8(const float *x, uint4 *t)
 {
     uint32_t w[3][4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * q]), h1 = __float2bfloat16_rn(x[2 * q + 1]);
-        w[0][q] = pack2(h0, h1);
+        const float x0 = x[2 * q], x1 = x[2 * q + 1];
+        const uint32_t h = cvt_bf16x2(x0, x1);
+        w[0][q] = h;
         if (NT == 3) {
-            const float r0 = x[2 * q] - __bfloat162float(h0), r1 = x[2 * q + 1] - __bfloat162float(h1);
-            __nv_bfloat16 m0 = __float2bfloat16_rn(r0), m1 = __float2bfloat16_rn(r1);
-            const float s0 = r0 - __bfloat162float(m0), s1 = r1 - __bfloat162float(m1);
-            w[1][q] = pack2(m0, m1);
-            w[2][q] = pack2(__float2bfloat16_rn(s0), __float2bfloat16_rn(s1));
+            const float r0 = x0 - __uint_as_float(h << 16), r1 = x1 - __uint_as_float(h & 0xffff0000u);
+            const uint32_t m = cvt_bf16x2(r0, r1);
+            const float s0 = r0 - __uint_as_float(m << 16), s1 = r1 - __uint_as_float(m & 0xffff0000u);
+            w[1][q] = m;
+            w[2][q] = cvt_bf16x2(s0, s1);
         }
     }
 #pragma unroll
@@ -361,23 +371,9 @@ __global__ void __launch_bounds__(576, 1) tc_contract_kernel(const __grid_consta
             const float *st = stage + (size_t)s * TE * N;
             unsigned char *Ab = smem + offA + (size_t)ab * bufA;
             const int c8n = Kp / 8;
-            // this thread's row of u: stage (or global memory for unaligned tail tiles)
-            const float *src = from_stage ? (NODE ? st + row : st + row * N)
-                                          : (NODE ? a.u + e0 + row : a.u + (e0 + row) * N);
-            const long long jstride = from_stage ? (NODE ? TE : 1) : (NODE ? E : 1);
             const bool rowv = row < TEv;
-            for (int c8 = part; c8 < c8n; c8 += H) {
-                float x[8];
-                const float *p8 = src + (long long)c8 * 8 * jstride;
-                if (rowv && c8 * 8 + 8 <= N) {
-#pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        x[q] = p8[q * jstride];
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        x[q] = (rowv && c8 * 8 + q < N) ? p8[q * jstride] : 0.f;
-                }
+            // K chunk c8 (8 values of j) of this thread's row -> the A terms
+            auto put = [&](int c8, const float *x) {
                 uint4 tt4[3];
                 split8<NT>(x, tt4);
                 const int kb = (c8 * 8) / KB, ch = ((c8 * 8) % KB) / 8;
@@ -385,6 +381,43 @@ __global__ void __launch_bounds__(576, 1) tc_contract_kernel(const __grid_consta
 #pragma unroll
                 for (int tt = 0; tt < NT; ++tt)
                     *reinterpret_cast<uint4 *>(Ab + off + tt * termA) = tt4[tt];
+            };
+            const int full8 = rowv ? N / 8 : 0;  // chunks with all 8 values inside the row
+            if (from_stage) {
+                // staged tile: compile-time stride along j; two chunks in flight
+                constexpr int JS = NODE ? TE : 1;
+                const float *src = NODE ? st + row : st + row * N;
+                int c8 = part;
+                for (; c8 + H < full8; c8 += 2 * H) {
+                    float x[8], y[8];
+                    const float *p0 = src + c8 * 8 * JS, *p1 = src + (c8 + H) * 8 * JS;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        x[q] = p0[q * JS];
+                        y[q] = p1[q * JS];
+                    }
+                    put(c8, x);
+                    put(c8 + H, y);
+                }
+                for (; c8 < c8n; c8 += H) {
+                    float x[8];
+                    const float *p0 = src + c8 * 8 * JS;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        x[q] = (rowv && c8 * 8 + q < N) ? p0[q * JS] : 0.f;
+                    put(c8, x);
+                }
+            } else {
+                // unaligned tail tile read from global memory
+                const float *src = NODE ? a.u + e0 + row : a.u + (e0 + row) * N;
+                const long long js = NODE ? E : 1;
+                for (int c8 = part; c8 < c8n; c8 += H) {
+                    float x[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        x[q] = (rowv && c8 * 8 + q < N) ? src[(long long)(c8 * 8 + q) * js] : 0.f;
+                    put(c8, x);
+                }
             }
             fence_async_smem();
             __syncwarp();
@@ -441,9 +474,11 @@ __global__ void __launch_bounds__(576, 1) tc_contract_kernel(const __grid_consta
                         if (row < TEv) {
                             float *o = a.out + ((size_t)(f0 + fl) * N + i0) * E + e0 + row;
 #pragma unroll
-                            for (int q = 0; q < 16; ++q)
+                            for (int q = 0; q < 16; ++q) {
                                 if (q < nv)
-                                    o[(size_t)q * E] = __uint_as_float(r[k4][q]);
+                                    *o = __uint_as_float(r[k4][q]);
+                                o += E;
+                            }
                         }
                     } else {
                         float *o = ost + (fl * TE + row) * N + i0;

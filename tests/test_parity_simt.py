@@ -54,7 +54,8 @@ def check(got, D, u, layout, fp64):
     assert oracle.rel_fro_error(got, ref) <= tol
 
 
-SHAPES = [(1000, 35, 3), (517, 20, 1), (333, 7, 2), (64, 84, 4), (1, 5, 1), (129, 165, 3), (4097, 12, 2)]
+SHAPES = [(1000, 35, 3), (517, 20, 1), (333, 7, 2), (64, 84, 4), (1, 5, 1), (129, 165, 3), (4097, 12, 2),
+          (300, 250, 2), (777, 84, 4)]
 
 
 def simt_variants(fp64):
@@ -183,3 +184,19 @@ def test_full_size_fp32_three_sampled(lc):
             got = got.transpose(0, 2, 1)
         assert np.all(np.abs(got - ref) <= bound)
         del out
+
+
+@pytest.mark.parametrize("layout", ["elem", "node"])
+def test_column_blocks_and_row_splits(lc, layout):
+    """Operators spread over CTA column blocks (F=8) and, at N=256, one operator's rows
+    split over several blocks because its D^T does not fit shared memory."""
+    kernel = lc.Kernel()
+    for E, N, F in [(1000, 120, 8), (513, 256, 3)]:
+        D, u = synth.operands(E, N, F, np.float32, seed=N)
+        uu = synth.to_node_major(u) if layout == "node" else u
+        v = lc.variant_default(kernel, E, N, F, layout, "fp32")
+        check(run(lc, kernel, v, D, uu, layout), D, uu, layout, False)
+        Di, ui = synth.integer_operands(E, N, F, seed=1)
+        uui = synth.to_node_major(ui) if layout == "node" else ui
+        got = run(lc, kernel, v, Di, uui, layout)
+        assert np.array_equal(got.astype(np.float64), oracle.contract(Di, uui, layout))
