@@ -1276,6 +1276,8 @@ static lc_status grouped_plan_host(const Kernel &K, const lc_variant *v, const l
     const int sms = sm_count();
     if (sms <= 0)
         return LC_ERR_NO_DEVICE;
+    // CTA size: the most threads the register block allows (the same bound as the plain kernel)
+    P.threads = v->elems_per_thread * v->split_i >= 64 ? 256 : 512;
     const int T = P.threads;
     std::vector<double> tile_cost(ng);
     std::vector<long long> ntiles(ng);
@@ -1336,55 +1338,123 @@ static lc_status grouped_plan_host(const Kernel &K, const lc_variant *v, const l
         P.groups[gi] = a;
         P.smem = std::max(P.smem, best.g.smem);
         ntiles[gi] = G.E > 0 ? best.g.ntiles * best.g.nchunks : 0;  // (tile, column block) items
+        (void)ntiles[gi];
         // estimated seconds per item: FMA pipe (FP32, padded columns) vs HBM
         const double flops = 2.0 * a.TE * (double)G.N * a.CW;
         const double bytes = 4.0 * a.TE * ((double)G.N + (a.isplit ? a.isplit : (double)a.G * G.N));
         tile_cost[gi] = std::max(flops / (sms * 128 * 2 * 1.9e9), bytes / 6.8e12) + 2e-7 / sms;
     }
+    // units: (group, column block) with its tiles and cost per tile
+    struct Unit {
+        int g, chunk;
+        long long tiles;
+        double cost;
+    };
+    std::vector<Unit> units;
     double total = 0;
-    long long total_tiles = 0;
+    long long total_items = 0;
     for (int gi = 0; gi < ng; ++gi) {
-        total += tile_cost[gi] * ntiles[gi];
-        total_tiles += ntiles[gi];
-    }
-    const int per_sm = v->ctas_per_sm > 0 ? v->ctas_per_sm : 2;
-    P.grid = (int)std::max<long long>(1, std::min<long long>((long long)sms * per_sm, total_tiles));
-    // walk the (group, tile) list, cutting it into P.grid contiguous ranges of equal cost
-    P.segs.clear();
-    P.cta_seg.assign(P.grid + 1, 0);
-    const double target = total / P.grid;
-    int b = 0;
-    double acc = 0;
-    for (int gi = 0; gi < ng; ++gi) {
-        // items of group gi: column block major, then tiles
-        const long long tiles_g = P.groups[gi].ntiles;
-        long long t = 0;
-        while (t < ntiles[gi]) {
-            // items of this group that fit in CTA b's remaining budget (at least one), not
-            // crossing a column block
-            const long long chunk = t / tiles_g, t_in = t - chunk * tiles_g;
-            long long take = tiles_g - t_in;
-            if (b < P.grid - 1) {
-                const double room = (b + 1) * target - acc;
-                long long fit = (long long)std::ceil(room / tile_cost[gi]);
-                take = std::max<long long>(1, std::min(take, fit));
-            }
-            GroupSeg sg;
-            sg.group = gi;
-            sg.chunk = (int)chunk;
-            sg.first = t_in;
-            sg.count = take;
-            P.segs.push_back(sg);
-            t += take;
-            acc += take * tile_cost[gi];
-            if (b < P.grid - 1 && acc >= (b + 1) * target - 1e-15) {
-                P.cta_seg[b + 1] = (int)P.segs.size();
-                ++b;
-            }
+        const long long tiles_g = groups[gi].E > 0 ? P.groups[gi].ntiles : 0;
+        for (int ch = 0; ch < P.groups[gi].nchunks && tiles_g > 0; ++ch) {
+            units.push_back({gi, ch, tiles_g, tile_cost[gi]});
+            total += tiles_g * tile_cost[gi];
+            total_items += tiles_g;
         }
     }
-    for (int q = b + 1; q <= P.grid; ++q)
-        P.cta_seg[q] = (int)P.segs.size();
+    const int per_sm = v->ctas_per_sm > 0 ? v->ctas_per_sm : 2;
+    P.grid = (int)std::max<long long>(1, std::min<long long>((long long)sms * per_sm, total_items));
+    const double budget = total / P.grid;
+    // CTAs per big unit (worth >= 1 CTA), the rest for the small units
+    std::vector<int> alloc(units.size(), 0);
+    double small_work = 0;
+    int nbig = 0;
+    for (size_t q = 0; q < units.size(); ++q) {
+        const double w = units[q].tiles * units[q].cost / budget;
+        if (w >= 1.0) {
+            alloc[q] = (int)std::min<long long>((long long)w, units[q].tiles);
+            ++nbig;
+        } else {
+            small_work += w;
+        }
+    }
+    const int small_ctas = small_work > 0 ? std::max(1, (int)std::ceil(small_work)) : 0;
+    auto used = [&]() {
+        long long sum = small_ctas;
+        for (int x : alloc)
+            sum += x;
+        return sum;
+    };
+    while (used() > P.grid) {  // shrink the unit with the most CTAs
+        size_t m = 0;
+        for (size_t q = 1; q < alloc.size(); ++q)
+            if (alloc[q] > alloc[m])
+                m = q;
+        if (alloc[m] <= 1)
+            break;
+        --alloc[m];
+    }
+    while (nbig > 0 && used() < P.grid) {  // give spare CTAs to the most loaded big unit
+        size_t m = alloc.size();
+        double worst = -1;
+        for (size_t q = 0; q < alloc.size(); ++q) {
+            if (alloc[q] == 0 || alloc[q] >= units[q].tiles)
+                continue;
+            const double load = units[q].tiles * units[q].cost / alloc[q];
+            if (load > worst) {
+                worst = load;
+                m = q;
+            }
+        }
+        if (m == alloc.size())
+            break;
+        ++alloc[m];
+    }
+    P.grid = (int)std::max<long long>(1, used());
+    std::vector<std::vector<GroupSeg>> per_cta(P.grid);
+    int b = 0;
+    for (size_t q = 0; q < units.size(); ++q) {
+        if (alloc[q] == 0)
+            continue;
+        const int n = alloc[q];
+        for (int r = 0; r < n; ++r) {
+            GroupSeg sg;
+            sg.group = units[q].g;
+            sg.chunk = units[q].chunk;
+            sg.first = r;
+            sg.step = n;
+            sg.count = (units[q].tiles - r + n - 1) / n;
+            per_cta[b + r].push_back(sg);
+        }
+        b += n;
+    }
+    // small units: whole, onto the least loaded of the remaining CTAs
+    std::vector<double> load(P.grid, 0.0);
+    for (size_t q = 0; q < units.size(); ++q) {
+        if (alloc[q] != 0)
+            continue;
+        int best = b;
+        for (int c = b; c < P.grid; ++c)
+            if (load[c] < load[best])
+                best = c;
+        if (best >= P.grid)
+            best = P.grid - 1;
+        GroupSeg sg;
+        sg.group = units[q].g;
+        sg.chunk = units[q].chunk;
+        sg.first = 0;
+        sg.step = 1;
+        sg.count = units[q].tiles;
+        per_cta[best].push_back(sg);
+        load[best] += units[q].tiles * units[q].cost;
+    }
+    P.segs.clear();
+    P.cta_seg.assign(P.grid + 1, 0);
+    for (int c = 0; c < P.grid; ++c) {
+        P.cta_seg[c] = (int)P.segs.size();
+        for (const GroupSeg &sg : per_cta[c])
+            P.segs.push_back(sg);
+    }
+    P.cta_seg[P.grid] = (int)P.segs.size();
     auto up16 = [](size_t x) { return (x + 15) / 16 * 16; };
     P.off_groups = 0;
     P.off_segs = up16(sizeof(SimtArgs) * ng);

@@ -1,9 +1,11 @@
 // Grouped persistent kernel: several contraction problems (groups with their own N, E,
-// operators and buffers) in one launch.  The host splits all groups' tiles into one
-// contiguous range of (group, tile) work per CTA, balanced by estimated cost; each CTA
-// walks its ranges in order, staging each group's D^T once per range and running the
-// SIMT tile loop of simt.cuh on it.  The launch can be captured once in a CUDA graph
-// and replayed.
+// operators and buffers) in one launch.  The host cuts the work into (group, column
+// block) units and gives each CTA a list of segments, balanced by estimated cost: a unit
+// worth at least one CTA gets its own set of CTAs, which stride over its tiles (so the
+// CTAs running at one time touch neighbouring tiles, as a grid-stride launch would); the
+// small units are packed whole onto the remaining CTAs.  Each CTA walks its segments in
+// order, staging the group's D^T block once per segment and running the SIMT tile loop of
+// simt.cuh on it.  The launch can be captured once in a CUDA graph and replayed.
 #include <cuda_runtime.h>
 
 #include "simt.cuh"
@@ -11,7 +13,7 @@
 namespace lc {
 
 template <int RE, int RC, int UNR, int LAYOUT, bool PF>
-__global__ void __launch_bounds__(256) grouped_contract_kernel(GroupedArgs g)
+__global__ void __launch_bounds__(simt_max_threads(RE, RC)) grouped_contract_kernel(GroupedArgs g)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int s_begin = g.cta_seg[blockIdx.x], s_end = g.cta_seg[blockIdx.x + 1];
@@ -19,7 +21,8 @@ __global__ void __launch_bounds__(256) grouped_contract_kernel(GroupedArgs g)
         const GroupSeg sg = g.segs[si];
         SimtArgs a = g.groups[sg.group];
         a.err = g.err;
-        simt_tiles<float, RE, RC, UNR, LAYOUT, PF>(a, sg.chunk, sg.first, 1, sg.first + sg.count, smem_raw);
+        simt_tiles<float, RE, RC, UNR, LAYOUT, PF>(a, sg.chunk, sg.first, sg.step, sg.first + sg.count * sg.step,
+                                                   smem_raw);
     }
 }
 

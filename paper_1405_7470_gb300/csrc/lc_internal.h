@@ -104,7 +104,7 @@ lc_status tc_launch(const TcArgs &a, int layout, int nterms, int grid, cudaStrea
 struct GroupSeg {
     int group;
     int chunk;  // column block of the group
-    long long first, count;
+    long long first, count, step;  // tiles first, first + step, ... (count of them)
 };
 struct GroupedArgs {
     const SimtArgs *groups;
