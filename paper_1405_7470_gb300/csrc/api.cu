@@ -768,7 +768,7 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         // K padded to a multiple of it; 1 = the widest block that divides K padded to 16
         const int kbw = v->elems_per_thread;
         if (v->tile_e != 128 || v->prefetch_smem != 1 || !(kbw == 1 || kbw == 16 || kbw == 32 || kbw == 64) ||
-            !(v->unroll == 1 || v->unroll == 2))
+            v->unroll < 1 || v->unroll > 3)
             return LC_ERR_INVALID_VARIANT;
         if (v->stages < 1 || v->stages > 3 || v->split_i < 0 || v->split_i > F || v->ctas_per_sm > 1 ||
             v->out_buffers < 0 || v->out_buffers > 2)

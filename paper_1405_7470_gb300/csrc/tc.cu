@@ -179,8 +179,11 @@ __device__ __forceinline__ void workers_sync(int nthreads)
     asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
 
+// 16-column accumulator chunks an epilogue warp loads before one wait
+static constexpr int kEpiBatch = 2;
+
 template <int LAYOUT, int NT>
-__global__ void __launch_bounds__(576, 1) tc_contract_kernel(const __grid_constant__ TcArgs a)
+__global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_constant__ TcArgs a)
 {
     constexpr bool NODE = LAYOUT == LC_LAYOUT_NODE_MAJOR;
     constexpr int TE = 128;
@@ -454,15 +457,15 @@ __global__ void __launch_bounds__(576, 1) tc_contract_kernel(const __grid_consta
             }
             const uint32_t tbase = tmem_base + (uint32_t)b * a.tmem_cols + ((uint32_t)((warp & 3) * 32) << 16);
             // this warp's 16-column chunks c0 = 16*(part + H*k); each lies inside one operator
-            for (int c0 = part * 16; c0 < CBp; c0 += 64 * H) {
-                uint32_t r[4][16];
+            for (int c0 = part * 16; c0 < CBp; c0 += kEpiBatch * 16 * H) {
+                uint32_t r[kEpiBatch][16];
 #pragma unroll
-                for (int k4 = 0; k4 < 4; ++k4)
+                for (int k4 = 0; k4 < kEpiBatch; ++k4)
                     if (c0 + k4 * 16 * H < CBp)
                         tmem_ld16(tbase + (uint32_t)(c0 + k4 * 16 * H), r[k4]);
                 tmem_wait();
 #pragma unroll
-                for (int k4 = 0; k4 < 4; ++k4) {
+                for (int k4 = 0; k4 < kEpiBatch; ++k4) {
                     const int cc = c0 + k4 * 16 * H;
                     if (cc >= CBp)
                         continue;

@@ -53,7 +53,7 @@ static std::vector<lc_variant> candidates(int N, int layout, int precision)
         }
     } else {
         for (int st : {1, 2, 3})
-            for (int tpr : {1, 2})
+            for (int tpr : {2, 3})
                 for (int g : {0, 1})
                     for (int kbw : {1, 64}) {
                         lc_variant v = b;

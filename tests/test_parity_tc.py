@@ -61,7 +61,7 @@ def test_integer_inputs_bit_exact(lc, layout, prec):
     for E, N, F in SHAPES:
         D, u = synth.integer_operands(E, N, F, seed=E + N)
         uu = synth.to_node_major(u) if layout == "node" else u
-        for stages, tpr in ((1, 1), (2, 2), (3, 2)):
+        for stages, tpr in ((1, 1), (2, 2), (3, 3)):
             v = lc.Variant(engine="tcgen05", layout=layout, precision=prec, tile_e=128, elems_per_thread=1,
                            split_i=0, unroll=tpr, prefetch_smem=1, stages=stages)
             if lc.variant_validate(kernel, E, N, F, v) != 0:
