@@ -110,17 +110,28 @@ struct lc_variant {
                                  split BF16 on the tensor cores with FP32 accumulation */
     int32_t tile_e;           /* split_iname(e, tile_e): e = e_in + tile_e * e_out (Eq. 1),
                                  one tile per CTA step */
-    int32_t elems_per_thread; /* ilp tag on e_in: elements per thread (SIMT register block) */
-    int32_t split_i;          /* ilp tag on i: output columns per thread (SIMT register block) */
-    int32_t unroll;           /* unr tag on the j reduction: 1, 2, 4 or 8 */
+    int32_t elems_per_thread; /* ilp tag on e_in: elements per thread (SIMT register block);
+                                 tensor-core engine: K-block width of the shared-memory
+                                 operands, 16, 32 or 64 (1 = widest dividing N rounded to 16) */
+    int32_t split_i;          /* ilp tag on i: output columns per thread (SIMT register block);
+                                 tensor-core engine: operators per CTA column block (0 = most) */
+    int32_t unroll;           /* unr tag on the j reduction: 1, 2, 4 or 8; tensor-core engine:
+                                 epilogue threads per tile row, 1 to 4 (conversion threads per
+                                 row: the same, 2 for 4) */
     int32_t prefetch_smem;    /* add_prefetch of the u tile into shared memory by TMA (1) or
                                  direct global loads into registers (0) */
     int32_t tail_free;        /* 1: no guard on the last e tile; only accepted when an
                                  assumption "E mod m = 0" with m a multiple of tile_e holds */
     int32_t stages;           /* u tiles in flight in shared memory (TMA ring depth), >= 1 */
     int32_t ctas_per_sm;      /* persistent grid size in CTAs per SM; 0 = one CTA per tile */
-    int32_t out_buffers;      /* tensor-core engine, element-major: output tiles staged in shared
-                                 memory in flight (1 or 2; 0 = the planner's choice) */
+    int32_t out_buffers;      /* tensor-core engine, element-major: shared-memory staging slots of
+                                 one operator's output tile each, whose bulk stores may be in
+                                 flight together (1 to 4; 0 = the planner's choice) */
+    int32_t store_rows;       /* tensor-core engine, element-major: tile rows written by one bulk
+                                 store: 32 or 64 (the warps of 1 or 2 TMEM lane quarters stage
+                                 one operator at a time and store it), or 128 (all epilogue
+                                 warps stage every operator of the block, then store);
+                                 0 = the planner's choice */
 };
 
 /*

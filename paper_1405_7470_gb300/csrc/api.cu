@@ -686,7 +686,7 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
     if (need_device && (sms <= 0 || smem_cap == 0))
         return LC_ERR_NO_DEVICE;
 
-    if (v->engine != LC_ENGINE_TCGEN05 && v->out_buffers != 0)
+    if (v->engine != LC_ENGINE_TCGEN05 && (v->out_buffers != 0 || v->store_rows != 0))
         return LC_ERR_INVALID_VARIANT;
     if (v->engine == LC_ENGINE_SIMT) {
         if (v->precision != LC_PREC_FP32 && v->precision != LC_PREC_FP64)
@@ -763,15 +763,17 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
     if (v->engine == LC_ENGINE_TCGEN05) {
         if (v->precision != LC_PREC_BF16 && v->precision != LC_PREC_BF16X3)
             return LC_ERR_INVALID_VARIANT;
-        // unroll = threads that share one tile row in the conversion and in the epilogue;
+        // unroll = threads that share one tile row in the epilogue (1..4); the conversion
+        // gets as many, up to 26 warps per CTA in all (unroll 4: two conversion threads);
         // elems_per_thread = K-block width (16, 32 or 64 bf16 = 32/64/128-byte swizzle rows),
         // K padded to a multiple of it; 1 = the widest block that divides K padded to 16
         const int kbw = v->elems_per_thread;
         if (v->tile_e != 128 || v->prefetch_smem != 1 || !(kbw == 1 || kbw == 16 || kbw == 32 || kbw == 64) ||
-            v->unroll < 1 || v->unroll > 3)
+            v->unroll < 1 || v->unroll > 4)
             return LC_ERR_INVALID_VARIANT;
         if (v->stages < 1 || v->stages > 3 || v->split_i < 0 || v->split_i > F || v->ctas_per_sm > 1 ||
-            v->out_buffers < 0 || v->out_buffers > 2)
+            v->out_buffers < 0 || v->out_buffers > 4 ||
+            !(v->store_rows == 0 || v->store_rows == 32 || v->store_rows == 64 || v->store_rows == 128))
             return LC_ERR_INVALID_VARIANT;
         const bool node = v->layout == LC_LAYOUT_NODE_MAJOR;
         const int NT = v->precision == LC_PREC_BF16X3 ? 3 : 1;
@@ -790,16 +792,30 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         t.nkb = t.Kp / t.KB;
         t.stages = v->stages;
         t.threads_per_row = v->unroll;
+        t.conv_threads_per_row = std::min(v->unroll, 6 - v->unroll);
         const size_t W = 2 * (size_t)t.KB;
+        // rows per element-major bulk store: whole tiles of every operator of the block for
+        // small N (few, large stores), else 32-row pieces of one operator at a time (the
+        // stores stream, and the staging slots stay small)
+        t.store_quarters = v->store_rows ? v->store_rows / 32 : (N <= 48 ? 4 : 1);
         auto plan = [&](int G, TcArgs &q) -> bool {
             q.G = G;
-            q.Np = (N + 15) / 16 * 16;
+            // operator padding: 16 columns (16-column epilogue chunks), or 8 where that lets
+            // the BF16X3 terms stack (2 CBp <= 256) or the block fit (CBp <= 256) at all
+            auto cbp = [&](int np) { return (G * np + 15) / 16 * 16; };
+            const int np16 = (N + 15) / 16 * 16, np8 = (N + 7) / 8 * 8;
+            if (NT == 3 && 2 * cbp(np16) > 256 && 2 * cbp(np8) <= 256)
+                q.Np = np8;
+            else
+                q.Np = cbp(np16) <= 256 ? np16 : np8;
+            q.chunk = q.Np % 16 == 0 ? 16 : 8;
             q.CB = G * q.Np;
-            q.CBp = q.CB;
+            q.CBp = cbp(q.Np);
             if (q.CBp > 256)
                 return false;
+            q.stack = NT == 3 && 2 * q.CBp <= 256;
             q.tmem_cols = 32;
-            while (q.tmem_cols < q.CBp)
+            while (q.tmem_cols < (q.stack ? 2 : 1) * q.CBp)
                 q.tmem_cols *= 2;
             size_t off = 0;
             off += (size_t)NT * q.nkb * q.CBp * W;          // B terms
@@ -807,8 +823,8 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
             q.off_stage = (unsigned)off;
             off += (size_t)q.stages * 128 * N * 4;
             q.off_out = (unsigned)off;
-            if (!node)
-                off += (size_t)q.obufs * G * 128 * N * 4;
+            if (!node)  // staging slots: every operator of the block (4 quarters per store), else one
+                off += (size_t)q.obufs * (q.store_quarters == 4 ? G : 1) * 128 * N * 4;
             off = (off + 15) / 16 * 16;
             q.off_bar = (unsigned)off;
             off += 128;  // 14 mbarriers, TMEM address, abort flag
@@ -819,14 +835,15 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         if (v->stages > 3)
             return LC_ERR_INVALID_VARIANT;
         // Shared-memory plan, in order of preference: the most operators per CTA (fewer
-        // column blocks re-reading the same u tile), then two A buffers (conversion of
-        // tile k+1 overlaps the MMAs of tile k), then two output staging buffers (the next
-        // tile's epilogue overlaps the bulk stores).
-        static const int combos[4][2] = {{2, 2}, {1, 2}, {2, 1}, {1, 1}};  // {obufs, abufs}
+        // column blocks re-reading the same u tile), then at least two output staging
+        // slots (bulk stores of one operator overlap the staging of the next), then two A
+        // buffers (conversion of tile k+1 overlaps the MMAs of tile k), then more slots.
+        static const int combos[8][2] = {{3, 2}, {2, 2}, {4, 1}, {3, 1}, {2, 1}, {1, 2}, {1, 1}};  // {slots, abufs}
+        const int ncombos = 7;
         bool found = false;
         const int g_hi = v->split_i ? v->split_i : F, g_lo = v->split_i ? v->split_i : 1;
         for (int g = g_hi; g >= g_lo && !found; --g)
-            for (int c = 0; c < 4 && !found; ++c) {
+            for (int c = 0; c < ncombos && !found; ++c) {
                 TcArgs q = t;
                 q.obufs = node ? 1 : combos[c][0];
                 q.abufs = combos[c][1];
@@ -1034,6 +1051,8 @@ lc_status lc_kernel_print(const lc_kernel *kh, const lc_variant *v, char *buf, s
                 K.j_iname.c_str(), v->unroll);
         appendf(s, "add_prefetch(%s): %s, stages: %d, output buffers: %d\n", K.u_name.c_str(),
                 v->prefetch_smem ? "shared memory" : "none (global loads)", v->stages, v->out_buffers);
+        if (v->engine == LC_ENGINE_TCGEN05)
+            appendf(s, "rows per bulk store: %d (0 = planner's choice)\n", v->store_rows);
     }
     s += rule;
     if (needed)
@@ -1093,15 +1112,21 @@ lc_status lc_variant_default(const lc_kernel *kh, int64_t E, int32_t N, int32_t 
     } else {
         d.engine = LC_ENGINE_TCGEN05;
         d.tile_e = 128;
-        d.elems_per_thread = 1;
         d.split_i = 0;
-        d.unroll = 2;
-        d.stages = 3;
-        if (lc_variant_validate(kh, E, N, F, &d) != LC_OK)
-            d.stages = 2;
-        if (lc_variant_validate(kh, E, N, F, &d) != LC_OK)
-            d.stages = 1;
-        lc_status st = lc_variant_validate(kh, E, N, F, &d);
+        d.unroll = 3;
+        // 64-wide K-blocks first: a tcgen05.mma reading 128-byte swizzled rows costs the
+        // fewest cycles; then the narrowest blocks that cover K (least shared memory)
+        lc_status st = LC_ERR_INVALID_VARIANT;
+        for (int kbw : {64, 1})
+            for (int stg : {3, 2, 1}) {
+                if (st == LC_OK)
+                    break;
+                d.elems_per_thread = kbw;
+                d.stages = stg;
+                st = lc_variant_validate(kh, E, N, F, &d);
+                if (st != LC_OK && st != LC_ERR_INVALID_VARIANT)
+                    return st;
+            }
         if (st == LC_OK) {
             *v = d;
             return LC_OK;

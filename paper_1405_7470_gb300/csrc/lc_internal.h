@@ -84,14 +84,18 @@ struct TcArgs {
     int N, F;
     int G;          // operators per column block
     int nblocks;    // column blocks (ceil(F / G))
-    int Np;         // accumulator columns per operator: N rounded up to 16
-    int CB, CBp;    // columns per block (G * Np) and the MMA N (= CB)
-    int Kp, KB, nkb;  // K padded to 16, K-block width (16/32/64 -> 32/64/128-byte swizzle), blocks
-    int tmem_cols;  // columns per accumulator (power of two >= CBp)
+    int Np;         // accumulator columns per operator: N rounded up to 16 (or to 8)
+    int chunk;      // epilogue chunk: 16 columns when Np is a multiple of 16, else 8
+    int CB, CBp;    // columns per block (G * Np) and the MMA N (CB rounded up to 16)
+    int Kp, KB, nkb;  // K padded to the block width, K-block width (16/32/64 -> 32/64/128-byte swizzle), blocks
+    int stack;      // BF16X3 with two B terms stacked along N (2 * CBp <= 256): 4 MMAs per K step, not 6
+    int tmem_cols;  // columns per accumulator (power of two >= CBp, or >= 2 * CBp when stacked)
     int stages;     // u stage buffers (1 or 2)
-    int threads_per_row;  // worker threads per tile row (CTA = 128 * threads_per_row + 64)
+    int threads_per_row;       // epilogue threads per tile row
+    int conv_threads_per_row;  // conversion threads per tile row (CTA = 128 * (both) + 64 threads)
     int abufs;      // A-operand buffers (1 or 2)
-    int obufs;      // element-major output staging buffers (1 or 2)
+    int obufs;      // element-major output staging slots of one operator-tile (1 to 4)
+    int store_quarters;  // element-major: TMEM lane quarters (32 rows each) per bulk store: 1, 2 or 4
     long long ntiles;
     int bulk_u, bulk_store;
     unsigned int *err;

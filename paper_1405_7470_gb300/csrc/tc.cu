@@ -17,9 +17,9 @@
 //   MMA warp       one lane issues the tcgen05.mma chain of tile k into TMEM
 //                  accumulator k % 2 (two accumulators), then commits to the
 //                  A-buffer-empty and accumulator-full barriers;
-//   4*H converters convert the fp32 tile into the bf16 A-operand terms (K-major,
-//                  hardware swizzle layout; H threads share a tile row's K chunks);
-//   4*H epilogue   drain the accumulator of a finished tile (tcgen05.ld; the H warps
+//   4*Hc converters convert the fp32 tile into the bf16 A-operand terms (K-major,
+//                  hardware swizzle layout; Hc threads share a tile row's K chunks);
+//   4*He epilogue  drain the accumulator of a finished tile (tcgen05.ld; the He warps
 //                  of a TMEM lane quarter split its columns) and store it: element-
 //                  major through shared memory and one bulk store per operator,
 //                  node-major straight from registers (coalesced along e).
@@ -83,6 +83,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r)
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr)
         : "memory");
+}
+
+// 8 consecutive accumulator columns of this thread's TMEM lane (complete after tmem_wait).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t *r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
 }
 
 __device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
@@ -174,15 +183,54 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-__device__ __forceinline__ void workers_sync(int nthreads)
+// Named barrier `id` (immediate) over `nthreads` threads that also returns the OR of `v`
+// over them.
+#define LC_BAR_OR(ID)                                                                              \
+    __device__ __forceinline__ bool bar_or_##ID(int nthreads, bool v)                              \
+    {                                                                                              \
+        uint32_t r;                                                                                \
+        asm volatile("{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, " #ID          \
+                     ", %2, p;\nselp.u32 %0, 1, 0, q;\n}\n"                                            \
+                     : "=r"(r)                                                                     \
+                     : "r"((uint32_t)v), "r"(nthreads)                                             \
+                     : "memory");                                                                  \
+        return r != 0;                                                                             \
+    }
+LC_BAR_OR(1)
+LC_BAR_OR(2)
+LC_BAR_OR(3)
+LC_BAR_OR(4)
+LC_BAR_OR(5)
+#undef LC_BAR_OR
+
+__device__ __forceinline__ bool bar_or(int id, int nthreads, bool v)
 {
-    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+    switch (id) {
+    case 1: return bar_or_1(nthreads, v);
+    case 2: return bar_or_2(nthreads, v);
+    case 3: return bar_or_3(nthreads, v);
+    case 4: return bar_or_4(nthreads, v);
+    default: return bar_or_5(nthreads, v);
+    }
 }
 
-// 16-column accumulator chunks an epilogue warp loads before one wait
-static constexpr int kEpiBatch = 2;
+// Accumulator chunks (CW columns each) an epilogue warp loads before one wait: 32 registers
+// of loaded values, half of them per region when the BF16X3 terms are stacked.
+template <int NT, int CW>
+struct EpiBatch {
+    static constexpr int value = (NT == 3 ? 16 : 32) / CW;
+};
 
-template <int LAYOUT, int NT>
+template <int CW>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t *r)
+{
+    if (CW == 16)
+        tmem_ld16(taddr, r);
+    else
+        tmem_ld8(taddr, r);
+}
+
+template <int LAYOUT, int NT, int CW>
 __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_constant__ TcArgs a)
 {
     constexpr bool NODE = LAYOUT == LC_LAYOUT_NODE_MAJOR;
@@ -193,43 +241,46 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
     unsigned char *smem = smem_dyn + (((raw + 1023u) & ~1023u) - raw);
     const uint32_t sbase = smem_addr(smem);
 
-    const int N = a.N, G = a.G, CBp = a.CBp, Kp = a.Kp, KB = a.KB, nkb = a.nkb;
+    const int N = a.N, G = a.G, CBp = a.CBp, KB = a.KB, nkb = a.nkb;
     const int Np = a.Np;  // accumulator columns per operator (N rounded up to 16)
+    // K columns the MMAs read: N rounded up to the 16 of one instruction.  A K-block
+    // wider than that keeps its last columns unread, so nothing writes them.
+    const int Kn = (N + 15) & ~15;
     const int W = 2 * KB;  // bytes per row of a K-block
     const long long E = a.E;
     const int S = a.stages, NA = a.abufs;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int H = a.threads_per_row;  // threads per tile row in each worker role
-    const int NW = 4 * H;             // epilogue warps 0..NW-1, conversion warps NW..2*NW-1
-    const int NWT = NW * 32;
+    const int He = a.threads_per_row, Hc = a.conv_threads_per_row;  // threads per tile row per role
+    const int NW = 4 * He, NC = 4 * Hc;  // epilogue warps 0..NW-1, conversion warps NW..NW+NC-1
     const int row = 32 * (warp & 3) + lane;  // tile row (== TMEM lane for epilogue warps)
-    const int part = (warp % NW) >> 2;       // which share of the row's K chunks / columns
+    const int part = (warp < NW ? warp : warp - NW) >> 2;  // which share of the row's K chunks / columns
     const int blk = blockIdx.x % a.nblocks;  // this CTA's column block
     const int f0 = blk * G;
     const int Gb = min(G, a.F - f0);  // operators in this block
 
-    const uint32_t termB = (uint32_t)nkb * CBp * W;  // bytes per B term
-    const uint32_t offA = NT * termB;
+    // B: per K-block, the NT terms of D^T stacked along rows (term t, column n -> row t*CBp + n)
+    const uint32_t bkb = (uint32_t)NT * CBp * W;  // bytes per K-block of B
+    const uint32_t offA = (uint32_t)nkb * bkb;
     const uint32_t termA = (uint32_t)nkb * TE * W;  // bytes per A term
     const uint32_t bufA = NT * termA;               // bytes per A buffer
     float *stage = reinterpret_cast<float *>(smem + a.off_stage);  // S x [TE*N] fp32
-    float *ost0 = reinterpret_cast<float *>(smem + a.off_out);     // obufs x [G][TE][N] (element-major)
+    float *ost0 = reinterpret_cast<float *>(smem + a.off_out);     // obufs x [4][32][N] slots (element-major)
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + a.off_bar);
     uint64_t *u_full = bar, *u_empty = bar + 3, *a_full = bar + 6, *a_empty = bar + 8;
     uint64_t *acc_full = bar + 10, *acc_empty = bar + 12;
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bar + 14);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(bar + 15);
 
-    const int prod_warp = 2 * NW, mma_warp = 2 * NW + 1;
+    const int prod_warp = NW + NC, mma_warp = NW + NC + 1;
     if (warp == mma_warp)
         tmem_alloc(tmem_holder, 2u * a.tmem_cols);
     if (tid == 0) {
         for (int q = 0; q < 3; ++q) {
             mbar_init(&u_full[q], 1);
-            mbar_init(&u_empty[q], NW);
+            mbar_init(&u_empty[q], NC);
         }
         for (int q = 0; q < 2; ++q) {
-            mbar_init(&a_full[q], NW);
+            mbar_init(&a_full[q], NC);
             mbar_init(&a_empty[q], 1);
             mbar_init(&acc_full[q], 1);
             mbar_init(&acc_empty[q], NW);
@@ -238,9 +289,9 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
         fence_mbar_init();
     }
 
-    // B terms: row n = f_local*Np + i of this block (i < N), column k = j; zero padding.
+    // B terms: column n = f_local*Np + i of this block (i < N), K index = j; zero padding.
     {
-        const int c8n = Kp / 8;
+        const int c8n = Kn / 8;
         for (int idx = tid; idx < CBp * c8n; idx += blockDim.x) {
             const int n = idx / c8n, c8 = idx - n * c8n;
             float x[8];
@@ -254,10 +305,9 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
             uint4 t[3];
             split8<NT>(x, t);
             const int kb = (c8 * 8) / KB, ch = ((c8 * 8) % KB) / 8;
-            const uint32_t off = (uint32_t)kb * CBp * W + swz_off(n, ch, W);
 #pragma unroll
             for (int tt = 0; tt < NT; ++tt)
-                *reinterpret_cast<uint4 *>(smem + off + tt * termB) = t[tt];
+                *reinterpret_cast<uint4 *>(smem + (uint32_t)kb * bkb + swz_off(tt * CBp + n, ch, W)) = t[tt];
         }
     }
     fence_async_smem();
@@ -312,7 +362,7 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
         }
     } else if (warp == mma_warp) {
         // ---------------- MMA issuer
-        const uint32_t idesc = instr_desc(CBp);
+        const uint32_t idesc = instr_desc(CBp), idesc2 = instr_desc(2 * CBp);
         int k = 0;
         for (long long t = my_first; t < a.ntiles; t += my_step, ++k) {
             const int b = k & 1, ab = k % NA;
@@ -326,27 +376,40 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
             }
             tc_fence_after();
             if (lane == 0) {
-                // (D term, u term): lh, hl, mm, mh, hm, hh (small products first). A descriptor
-                // advances by adding the byte offset / 16 to its start-address field.
                 const uint32_t dtm = tmem_base + (uint32_t)b * a.tmem_cols;
                 const uint64_t a0 = smem_desc(sbase + offA + (uint32_t)ab * bufA, W);
                 const uint64_t b0 = smem_desc(sbase, W);
-                const uint32_t a_kb = (uint32_t)(TE * W) >> 4, b_kb = (uint32_t)(CBp * W) >> 4;
-                const int kin_steps = KB / 16;
-                constexpr int npairs = NT == 3 ? 6 : 1;
-                uint32_t accumulate = 0;
-#pragma unroll
-                for (int p = 0; p < npairs; ++p) {
-                    const int bt = NT == 3 ? (p == 0 ? 2 : (p == 2 || p == 3) ? 1 : 0) : 0;
-                    const int at = NT == 3 ? (p == 1 ? 2 : (p == 2 || p == 4) ? 1 : 0) : 0;
-                    uint64_t ad = a0 + ((at * termA) >> 4), bd = b0 + ((bt * termB) >> 4);
+                const uint32_t a_kb = (uint32_t)(TE * W) >> 4, b_kb = bkb >> 4;
+                // One product over all K: A term `at` times the B rows starting at `brow`,
+                // into accumulator columns dcol.. (descriptors advance by byte offset / 16).
+                auto chain = [&](int at, int brow, uint32_t id, uint32_t dcol, uint32_t accumulate) {
+                    uint64_t ad = a0 + ((at * termA) >> 4), bd = b0 + ((uint32_t)(brow * W) >> 4);
                     for (int kb = 0; kb < nkb; ++kb) {
+                        const int kin_steps = min(KB, Kn - kb * KB) / 16;  // all-zero K steps skipped
                         for (int ki = 0; ki < kin_steps; ++ki) {
-                            tc_mma(dtm, ad + 2 * ki, bd + 2 * ki, idesc, accumulate);  // +32 bytes per K step
+                            tc_mma(dtm + dcol, ad + 2 * ki, bd + 2 * ki, id, accumulate);  // +32 bytes per K step
                             accumulate = 1;
                         }
                         ad += a_kb;
                         bd += b_kb;
+                    }
+                };
+                if (NT == 1) {
+                    chain(0, 0, idesc, 0, 0);
+                } else if (a.stack) {
+                    // two regions R0 = columns [0, CBp), R1 = [CBp, 2 CBp), summed by the epilogue:
+                    // R0 <- u_lo D_hi, R1 <- u_hi D_lo, then u_mid and u_hi times [D_hi; D_mid]
+                    chain(2, 0, idesc, 0, 0);
+                    chain(0, 2 * CBp, idesc, (uint32_t)CBp, 0);
+                    chain(1, 0, idesc2, 0, 1);
+                    chain(0, 0, idesc2, 0, 1);
+                } else {
+                    // (D term, u term): lh, hl, mm, mh, hm, hh (small products first)
+#pragma unroll
+                    for (int p = 0; p < 6; ++p) {
+                        const int bt = p == 0 ? 2 : (p == 2 || p == 3) ? 1 : 0;
+                        const int at = p == 1 ? 2 : (p == 2 || p == 4) ? 1 : 0;
+                        chain(at, bt * CBp, idesc, 0, p == 0 ? 0u : 1u);
                     }
                 }
                 tc_commit(&a_empty[ab]);
@@ -373,7 +436,7 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
             const bool from_stage = tile_bulk_bytes(t) != 0;
             const float *st = stage + (size_t)s * TE * N;
             unsigned char *Ab = smem + offA + (size_t)ab * bufA;
-            const int c8n = Kp / 8;
+            const int c8n = Kn / 8;
             const bool rowv = row < TEv;
             // K chunk c8 (8 values of j) of this thread's row -> the A terms
             auto put = [&](int c8, const float *x) {
@@ -391,18 +454,18 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
                 constexpr int JS = NODE ? TE : 1;
                 const float *src = NODE ? st + row : st + row * N;
                 int c8 = part;
-                for (; c8 + H < full8; c8 += 2 * H) {
+                for (; c8 + Hc < full8; c8 += 2 * Hc) {
                     float x[8], y[8];
-                    const float *p0 = src + c8 * 8 * JS, *p1 = src + (c8 + H) * 8 * JS;
+                    const float *p0 = src + c8 * 8 * JS, *p1 = src + (c8 + Hc) * 8 * JS;
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         x[q] = p0[q * JS];
                         y[q] = p1[q * JS];
                     }
                     put(c8, x);
-                    put(c8 + H, y);
+                    put(c8 + Hc, y);
                 }
-                for (; c8 < c8n; c8 += H) {
+                for (; c8 < c8n; c8 += Hc) {
                     float x[8];
                     const float *p0 = src + c8 * 8 * JS;
 #pragma unroll
@@ -414,7 +477,7 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
                 // unaligned tail tile read from global memory
                 const float *src = NODE ? a.u + e0 + row : a.u + (e0 + row) * N;
                 const long long js = NODE ? E : 1;
-                for (int c8 = part; c8 < c8n; c8 += H) {
+                for (int c8 = part; c8 < c8n; c8 += Hc) {
                     float x[8];
 #pragma unroll
                     for (int q = 0; q < 8; ++q)
@@ -433,103 +496,207 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
         }
     } else {
         // ---------------- epilogue warps: TMEM accumulators -> out
-        int k = 0;
-        bool ok = true;
-        for (long long t = my_first; t < a.ntiles; t += my_step, ++k) {
-            const int b = k & 1;
-            const long long e0 = t * TE;
-            const int TEv = (int)min((long long)TE, E - e0);
-            if (!mbar_wait(&acc_full[b], (uint32_t)((k >> 1) & 1))) {
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-            float *ost = ost0 + (size_t)(k % a.obufs) * G * TE * N;
-            if (!NODE) {
-                if (tid == 0) {
-                    // the bulk stores that last read this staging buffer are done reading
-                    if (a.obufs == 2)
-                        bulk_wait_read1();
-                    else
-                        bulk_wait_read0();
-                }
-                workers_sync(NWT);
-            }
-            const uint32_t tbase = tmem_base + (uint32_t)b * a.tmem_cols + ((uint32_t)((warp & 3) * 32) << 16);
-            // this warp's 16-column chunks c0 = 16*(part + H*k); each lies inside one operator
-            for (int c0 = part * 16; c0 < CBp; c0 += kEpiBatch * 16 * H) {
-                uint32_t r[kEpiBatch][16];
+        // Warp w reads TMEM lane quarter q = w % 4 (tile rows 32q..32q+31); the He warps of a
+        // quarter split the CW-column chunks of the accumulator (with stacked BF16X3 terms a
+        // chunk is the sum of regions R0 and R1).
+        //   node-major        stores straight from registers, coalesced along e;
+        //   element-major     staged in shared memory, then bulk stores of contiguous rows:
+        //     store_quarters = 4   all epilogue warps stage every operator of the tile into
+        //                          one of R slots, then one thread issues G stores;
+        //     store_quarters < 4   a store group of SQ quarters stages one operator at a time
+        //                          into its own ring of R slots and stores 32 SQ rows of it,
+        //                          with no CTA-wide barrier.
+        const int q = warp & 3;
+        const int R = a.obufs;
+        const int SQ = NODE ? 4 : a.store_quarters;
+        const int NWT = NW * 32;
+        const bool stack = NT == 3 && a.stack;
+        // Load, sum and store the chunks of columns [c_begin, c_end) of this warp's lane
+        // quarter; element-major values go to stage + ((operator - f_stage) * TE + row) * N.
+        auto drain = [&](int c_begin, int c_end, const uint32_t tbase, float *stage, int f_stage, long long e0,
+                         int TEv) {
+            constexpr int EB = EpiBatch<NT, CW>::value;
+            for (int c0 = c_begin + part * CW; c0 < c_end; c0 += EB * CW * He) {
+                uint32_t r[EB][CW], r2[EB][CW];
 #pragma unroll
-                for (int k4 = 0; k4 < kEpiBatch; ++k4)
-                    if (c0 + k4 * 16 * H < CBp)
-                        tmem_ld16(tbase + (uint32_t)(c0 + k4 * 16 * H), r[k4]);
+                for (int k4 = 0; k4 < EB; ++k4)
+                    if (c0 + k4 * CW * He < c_end) {
+                        tmem_ld<CW>(tbase + (uint32_t)(c0 + k4 * CW * He), r[k4]);
+                        if (stack)
+                            tmem_ld<CW>(tbase + (uint32_t)(CBp + c0 + k4 * CW * He), r2[k4]);
+                    }
                 tmem_wait();
 #pragma unroll
-                for (int k4 = 0; k4 < kEpiBatch; ++k4) {
-                    const int cc = c0 + k4 * 16 * H;
-                    if (cc >= CBp)
+                for (int k4 = 0; k4 < EB; ++k4) {
+                    const int cc = c0 + k4 * CW * He;
+                    if (cc >= c_end)
                         continue;
                     const int fl = cc / Np, i0 = cc - fl * Np;
-                    const int nv = min(16, N - i0);  // valid columns of this chunk
-                    if (fl >= Gb || nv <= 0)
-                        continue;
+                    const int nv = min(CW, N - i0);  // valid columns of this chunk (>= 1)
+                    if (stack) {
+#pragma unroll
+                        for (int qq = 0; qq < CW; ++qq)
+                            r[k4][qq] = __float_as_uint(__uint_as_float(r[k4][qq]) + __uint_as_float(r2[k4][qq]));
+                    }
                     if (NODE) {
                         if (row < TEv) {
                             float *o = a.out + ((size_t)(f0 + fl) * N + i0) * E + e0 + row;
 #pragma unroll
-                            for (int q = 0; q < 16; ++q) {
-                                if (q < nv)
-                                    *o = __uint_as_float(r[k4][q]);
+                            for (int qq = 0; qq < CW; ++qq) {
+                                if (qq < nv)
+                                    *o = __uint_as_float(r[k4][qq]);
                                 o += E;
                             }
                         }
                     } else {
-                        float *o = ost + (fl * TE + row) * N + i0;
-                        if (nv == 16) {
+                        float *o = stage + ((fl - f_stage) * TE + row) * N + i0;
+                        if ((N & 3) == 0) {
+                            // 16-byte aligned rows: vector stores (nv is a multiple of 4)
 #pragma unroll
-                            for (int q = 0; q < 16; ++q)
-                                o[q] = __uint_as_float(r[k4][q]);
+                            for (int h = 0; h < CW / 4; ++h)
+                                if (4 * h < nv)
+                                    *reinterpret_cast<uint4 *>(o + 4 * h) =
+                                        make_uint4(r[k4][4 * h], r[k4][4 * h + 1], r[k4][4 * h + 2], r[k4][4 * h + 3]);
+                        } else if (nv == CW) {
+#pragma unroll
+                            for (int qq = 0; qq < CW; ++qq)
+                                o[qq] = __uint_as_float(r[k4][qq]);
                         } else {
 #pragma unroll
-                            for (int q = 0; q < 16; ++q)
-                                if (q < nv)
-                                    o[q] = __uint_as_float(r[k4][q]);
+                            for (int qq = 0; qq < CW; ++qq)
+                                if (qq < nv)
+                                    o[qq] = __uint_as_float(r[k4][qq]);
                         }
                     }
                 }
             }
+        };
+        auto release_acc = [&](int b) {
             tc_fence_before();
             __syncwarp();
             if (lane == 0)
                 mbar_arrive(&acc_empty[b]);
-            if (!NODE) {
-                fence_async_smem();
-                workers_sync(NWT);
-                const int total = TEv * N;
-                if (a.bulk_store && ((total * 4) & 15) == 0) {
-                    if (tid == 0) {
-                        for (int g = 0; g < Gb; ++g)
-                            bulk_s2g(a.out + ((size_t)(f0 + g) * E + e0) * N, ost + (size_t)g * TE * N,
-                                     (uint32_t)total * 4u);
-                        bulk_commit();
+        };
+        int k = 0;
+        bool ok = true;
+        if (SQ == 4) {
+            // ---- node-major, or element-major with whole-tile slots
+            for (long long t = my_first; t < a.ntiles; t += my_step, ++k) {
+                const int b = k & 1;
+                const long long e0 = t * TE;
+                const int TEv = (int)min((long long)TE, E - e0);
+                const bool got = mbar_wait(&acc_full[b], (uint32_t)((k >> 1) & 1));
+                float *ost = ost0 + (size_t)(k % R) * G * TE * N;
+                if (NODE) {
+                    if (!got || *abort_flag) {  // node-major warps meet at no named barrier
+                        ok = got;
+                        break;
                     }
                 } else {
-                    for (int g = 0; g < Gb; ++g) {
-                        const float *src = ost + (size_t)g * TE * N;
-                        float *dst = a.out + ((size_t)(f0 + g) * E + e0) * N;
-                        for (int q = tid; q < total; q += NWT)
-                            dst[q] = src[q];
+                    if (tid == 0)
+                        bulk_wait_read(R - 1);  // the stores that last read this slot are done reading
+                    // the epilogue warps leave together (they meet at named barriers)
+                    if (bar_or(1, NWT, !got || *abort_flag)) {
+                        ok = got;
+                        break;
                     }
-                    workers_sync(NWT);
+                }
+                tc_fence_after();
+                const uint32_t tbase = tmem_base + (uint32_t)b * a.tmem_cols + ((uint32_t)(q * 32) << 16);
+                drain(0, Gb * Np, tbase, ost, 0, e0, TEv);
+                release_acc(b);
+                if (!NODE) {
+                    fence_async_smem();
+                    asm volatile("bar.sync 1, %0;" ::"r"(NWT) : "memory");
+                    const int total = TEv * N;
+                    if (a.bulk_store && ((total * 4) & 15) == 0) {
+                        if (tid == 0) {
+                            for (int g = 0; g < Gb; ++g)
+                                bulk_s2g(a.out + ((size_t)(f0 + g) * E + e0) * N, ost + (size_t)g * TE * N,
+                                         (uint32_t)total * 4u);
+                            bulk_commit();
+                        }
+                    } else {
+                        // unaligned tail: plain copy; the next barrier on this slot orders reuse
+                        for (int g = 0; g < Gb; ++g) {
+                            const float *src = ost + (size_t)g * TE * N;
+                            float *dst = a.out + ((size_t)(f0 + g) * E + e0) * N;
+                            for (int idx = tid; idx < total; idx += NWT)
+                                dst[idx] = src[idx];
+                        }
+                    }
                 }
             }
-            if (*abort_flag)
-                break;
+            if (!NODE && tid == 0)
+                bulk_wait0();
+        } else {
+            // ---- element-major, one operator per slot, store groups of SQ quarters
+            const int gq = q / SQ, qin = q % SQ;  // store group, quarter within it
+            const int gthreads = 32 * He * SQ;
+            const bool leader = part == 0 && lane == 0 && qin == 0;  // issues and waits on the group's stores
+            // named barrier 2 + gq (immediate operands)
+            auto group_sync = [&]() {
+                switch (gq) {
+                case 0: asm volatile("bar.sync 2, %0;" ::"r"(gthreads) : "memory"); break;
+                case 1: asm volatile("bar.sync 3, %0;" ::"r"(gthreads) : "memory"); break;
+                case 2: asm volatile("bar.sync 4, %0;" ::"r"(gthreads) : "memory"); break;
+                default: asm volatile("bar.sync 5, %0;" ::"r"(gthreads) : "memory"); break;
+                }
+            };
+            const int r0 = 32 * SQ * gq;  // first tile row of this store group
+            int ns = 0;                   // slots used by this store group
+            for (long long t = my_first; t < a.ntiles; t += my_step, ++k) {
+                const int b = k & 1;
+                const long long e0 = t * TE;
+                const int TEv = (int)min((long long)TE, E - e0);
+                const int rows_g = max(0, min(32 * SQ, TEv - r0));  // valid rows of this store group
+                const bool got = mbar_wait(&acc_full[b], (uint32_t)((k >> 1) & 1));
+                const uint32_t tbase = tmem_base + (uint32_t)b * a.tmem_cols + ((uint32_t)(q * 32) << 16);
+                bool stop = false;
+                for (int g = 0; g < Gb; ++g) {
+                    float *slot = ost0 + (size_t)(ns % R) * TE * N;  // [TE][N], this group's rows r0..
+                    ++ns;
+                    if (leader)
+                        bulk_wait_read(R - 1);  // the store that last read this slot is done reading
+                    if (g > 0) {
+                        group_sync();
+                    } else {
+                        // the warps of a store group leave together (they meet at named barriers)
+                        if (bar_or(2 + gq, gthreads, !got || *abort_flag)) {
+                            stop = true;
+                            break;
+                        }
+                        tc_fence_after();
+                    }
+                    drain(g * Np, (g + 1) * Np, tbase, slot, g, e0, TEv);
+                    if (g == Gb - 1)
+                        release_acc(b);
+                    fence_async_smem();
+                    group_sync();
+                    const uint32_t bytes = (uint32_t)rows_g * N * 4u;
+                    float *dst = a.out + ((size_t)(f0 + g) * E + e0 + r0) * N;
+                    const float *src = slot + (size_t)r0 * N;
+                    if (a.bulk_store && (bytes & 15u) == 0) {
+                        if (leader && bytes) {
+                            bulk_s2g(dst, src, bytes);
+                            bulk_commit();
+                        }
+                    } else {
+                        // unaligned tail: plain copy; the next barrier on this slot orders reuse
+                        for (int idx = (qin * He + part) * 32 + lane; idx < rows_g * N; idx += gthreads)
+                            dst[idx] = src[idx];
+                    }
+                }
+                if (stop) {
+                    ok = got;
+                    break;
+                }
+            }
+            if (leader)
+                bulk_wait0();
         }
         if (!ok && lane == 0)
             fail();
-        if (!NODE && tid == 0)
-            bulk_wait0();
     }
 
     tc_fence_before();
@@ -541,20 +708,23 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
 
 lc_status tc_launch(const TcArgs &a, int layout, int nterms, int grid, cudaStream_t s)
 {
-    void *fn;
-    const bool node = layout == LC_LAYOUT_NODE_MAJOR;
-    if (nterms == 3)
-        fn = node ? reinterpret_cast<void *>(&tc_contract_kernel<LC_LAYOUT_NODE_MAJOR, 3>)
-                  : reinterpret_cast<void *>(&tc_contract_kernel<LC_LAYOUT_ELEM_MAJOR, 3>);
-    else
-        fn = node ? reinterpret_cast<void *>(&tc_contract_kernel<LC_LAYOUT_NODE_MAJOR, 1>)
-                  : reinterpret_cast<void *>(&tc_contract_kernel<LC_LAYOUT_ELEM_MAJOR, 1>);
+    // kernel instance per (layout, terms, epilogue chunk width)
+    static void *const fns[2][2][2] = {
+        {{reinterpret_cast<void *>(&tc_contract_kernel<LC_LAYOUT_ELEM_MAJOR, 1, 8>),
+          reinterpret_cast<void *>(&tc_contract_kernel<LC_LAYOUT_ELEM_MAJOR, 1, 16>)},
+         {reinterpret_cast<void *>(&tc_contract_kernel<LC_LAYOUT_ELEM_MAJOR, 3, 8>),
+          reinterpret_cast<void *>(&tc_contract_kernel<LC_LAYOUT_ELEM_MAJOR, 3, 16>)}},
+        {{reinterpret_cast<void *>(&tc_contract_kernel<LC_LAYOUT_NODE_MAJOR, 1, 8>),
+          reinterpret_cast<void *>(&tc_contract_kernel<LC_LAYOUT_NODE_MAJOR, 1, 16>)},
+         {reinterpret_cast<void *>(&tc_contract_kernel<LC_LAYOUT_NODE_MAJOR, 3, 8>),
+          reinterpret_cast<void *>(&tc_contract_kernel<LC_LAYOUT_NODE_MAJOR, 3, 16>)}}};
+    void *fn = fns[layout == LC_LAYOUT_NODE_MAJOR][nterms == 3][a.chunk == 16];
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.smem_bytes);
     if (e != cudaSuccess)
         return cuda_fail(e);
     TcArgs args = a;
     void *params[] = {&args};
-    e = cudaLaunchKernel(fn, dim3(grid), dim3(256 * a.threads_per_row + 64), params, a.smem_bytes, s);
+    e = cudaLaunchKernel(fn, dim3(grid), dim3(128 * (a.threads_per_row + a.conv_threads_per_row) + 64), params, a.smem_bytes, s);
     if (e != cudaSuccess)
         return cuda_fail(e);
     return LC_OK;

@@ -52,20 +52,25 @@ static std::vector<lc_variant> candidates(int N, int layout, int precision)
             }
         }
     } else {
+        const bool node = layout == LC_LAYOUT_NODE_MAJOR;
         for (int st : {1, 2, 3})
-            for (int tpr : {2, 3})
+            for (int tpr : {2, 3, 4})
                 for (int g : {0, 1})
-                    for (int kbw : {1, 64}) {
-                        lc_variant v = b;
-                        v.engine = LC_ENGINE_TCGEN05;
-                        v.tile_e = 128;
-                        v.elems_per_thread = kbw;
-                        v.split_i = g;
-                        v.unroll = tpr;
-                        v.prefetch_smem = 1;
-                        v.stages = st;
-                        out.push_back(v);
-                    }
+                    for (int kbw : {1, 64})
+                        for (int rows : {32, 128}) {
+                            if (node && rows != 32)
+                                continue;  // node-major stores from registers
+                            lc_variant v = b;
+                            v.engine = LC_ENGINE_TCGEN05;
+                            v.tile_e = 128;
+                            v.elems_per_thread = kbw;
+                            v.split_i = g;
+                            v.unroll = tpr;
+                            v.prefetch_smem = 1;
+                            v.stages = st;
+                            v.store_rows = node ? 0 : rows;
+                            out.push_back(v);
+                        }
     }
     return out;
 }

@@ -30,7 +30,7 @@ from . import lc
 
 PATHS = ("fp32", "bf16", "bf16x3")
 LAYOUTS = ("elem", "node")
-DIN = 24  # feature count (the library supports up to 32)
+DIN = 25  # feature count (the library supports up to 32)
 
 
 def features(shape: dict, v) -> np.ndarray:
@@ -47,6 +47,7 @@ def features(shape: dict, v) -> np.ndarray:
         math.log2(max(d["tile_e"], 1)) / 10.0, d["elems_per_thread"] / 64.0 if eng == "tcgen05" else d["elems_per_thread"] / 8.0,
         d["split_i"] / 8.0, math.log2(max(d["unroll"], 1)) / 3.0, float(d["prefetch_smem"]), d["stages"] / 3.0,
         d["ctas_per_sm"] / 4.0, float(d["precision"] == "fp32"), float(d["precision"] in ("bf16", "bf16x3")),
+        d.get("store_rows", 0) / 128.0,
     ]
     assert len(x) == DIN
     return np.asarray(x, dtype=np.float32)

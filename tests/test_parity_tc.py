@@ -61,13 +61,14 @@ def test_integer_inputs_bit_exact(lc, layout, prec):
     for E, N, F in SHAPES:
         D, u = synth.integer_operands(E, N, F, seed=E + N)
         uu = synth.to_node_major(u) if layout == "node" else u
-        for stages, tpr in ((1, 1), (2, 2), (3, 3)):
-            v = lc.Variant(engine="tcgen05", layout=layout, precision=prec, tile_e=128, elems_per_thread=1,
+        # K-block widths: 1 = widest that divides K padded to 16; 32 and 64 leave all-zero K steps
+        for stages, tpr, kbw in ((1, 1, 1), (2, 2, 64), (3, 3, 1), (2, 3, 32), (1, 4, 64)):
+            v = lc.Variant(engine="tcgen05", layout=layout, precision=prec, tile_e=128, elems_per_thread=kbw,
                            split_i=0, unroll=tpr, prefetch_smem=1, stages=stages)
             if lc.variant_validate(kernel, E, N, F, v) != 0:
                 continue
             got = run(lc, kernel, v, D, uu, layout)
-            assert np.array_equal(got, oracle.contract(D, uu, layout)), (E, N, F, stages)
+            assert np.array_equal(got, oracle.contract(D, uu, layout)), (E, N, F, stages, kbw)
 
 
 @pytest.mark.parametrize("layout", ["elem", "node"])
@@ -132,3 +133,24 @@ def test_full_size_precision_sweep_sampled(lc):
         assert oracle.rel_fro_error(got, ref) <= tol
         del out
     assert lc.device_error() == 0
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
+def test_store_groups_and_slots(lc, prec):
+    """Element-major epilogue: bulk stores of 32, 64 or 128 tile rows from 1, 2 or 4 staging
+    slots; ragged last tiles, and the plain-copy path (E*N not a multiple of 4)."""
+    kernel = lc.Kernel()
+    for E, N, F in ((1000, 35, 3), (1001, 35, 3), (333, 84, 4), (515, 20, 2)):
+        D, u = synth.integer_operands(E, N, F, seed=E + 7 * N)
+        ref = oracle.contract(D, u, "elem")
+        ran = 0
+        for rows in (32, 64, 128):
+            for ob in (1, 2, 4):
+                v = lc.Variant(engine="tcgen05", layout="elem", precision=prec, tile_e=128, elems_per_thread=1,
+                               split_i=0, unroll=2, prefetch_smem=1, stages=1, out_buffers=ob, store_rows=rows)
+                if lc.variant_validate(kernel, E, N, F, v) != 0:
+                    continue
+                got = run(lc, kernel, v, D, u, "elem")
+                assert np.array_equal(got, ref), (E, N, F, rows, ob)
+                ran += 1
+        assert ran >= 3, (E, N, F, ran)
