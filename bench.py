@@ -43,7 +43,8 @@ WORKLOADS = {
 }
 
 # DRAM bytes per launch from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum),
-# keyed by (workload, variant key); valid only while the kernel sources hash to `src`.
+# keyed by (workload, layout, precision, engine); valid only while the kernel sources hash
+# to `src`.  `variant` records the descriptor the capture ran.
 NCU_TRAFFIC = {}
 
 
@@ -141,6 +142,10 @@ def roofline_for(v, wl, peaks, sms, t_launch_s, workload_key):
     nbytes = es * E * N * (1 + F) + es * F * N * N
     t_hbm = nbytes / (peaks["hbm_gbs"] * 1e9)
     engine = v["engine"]
+    traffic = None
+    rec = NCU_TRAFFIC.get((workload_key, v["layout"], v["precision"], engine))
+    if rec and rec.get("src") == csrc_hash():
+        traffic = rec["bytes"]
     if engine == "tcgen05":
         # tensor pipe: one bf16 product per kept term pair (1 for bf16, 6 for bf16x3)
         npairs = 6 if wl["precision"] == "bf16x3" else 1
@@ -149,22 +154,17 @@ def roofline_for(v, wl, peaks, sms, t_launch_s, workload_key):
         if t_tensor > t_hbm:
             ach = tflops / t_launch_s / 1e12
             return {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-                    "frac": ach / peaks["bf16_tflops"], "traffic": None,
+                    "frac": ach / peaks["bf16_tflops"], "traffic": traffic,
                     "peak_source": peaks["source"] + " bf16 burst"}
         ach = nbytes / t_launch_s / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": peaks["source"],
+                "frac": ach / peaks["hbm_gbs"], "traffic": traffic, "peak_source": peaks["source"],
                 "tensor_frac": (tflops / t_launch_s / 1e12) / peaks["bf16_tflops"]}
     else:
         # FP32: 128 FMA lanes per SM; FP64: 2 per SM (the part's nominal 1.25 TFLOP/s FP64)
         lanes = 128 if es == 4 else 2
         alu_peak = sms * lanes * 2 * peaks["sm_max_mhz"] * 1e6
     t_alu = flops / alu_peak if alu_peak else 0.0
-    traffic = None
-    key = (workload_key, json.dumps(v, sort_keys=True))
-    rec = NCU_TRAFFIC.get(key)
-    if rec and rec.get("src") == csrc_hash():
-        traffic = rec["bytes"]
     if t_alu > t_hbm:
         ach = flops / t_launch_s / 1e12
         return {"bound": "alu", "achieved": ach, "peak": alu_peak / 1e12, "unit": "TFLOP/s",

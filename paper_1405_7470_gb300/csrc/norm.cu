@@ -27,7 +27,7 @@ __global__ void selftest_wait_kernel(unsigned long long limit_ns, unsigned int *
         atomicOr(err, 1u);
 }
 
-static constexpr int kNormBlocks = 1024;
+static constexpr int kNormBlocks = 2048;
 static constexpr int kNormThreads = 256;
 
 __device__ __forceinline__ void block_sum2(double &a, double &b, double *sh)
@@ -63,7 +63,23 @@ __global__ void __launch_bounds__(kNormThreads) norm_partial_kernel(const T *__r
     __shared__ double sh[2 * (kNormThreads / 32)];
     double s0 = 0.0, s1 = 0.0;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    // four grid-strided elements per step: eight independent loads in flight per thread
+    for (; k + 3 * stride < n; k += 4 * stride) {
+        double r[4], o[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            r[q] = __ldcs(ref + k + q * stride);
+            o[q] = (double)__ldcs(out + k + q * stride);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const double d = o[q] - r[q];
+            s0 = fma(d, d, s0);
+            s1 = fma(r[q], r[q], s1);
+        }
+    }
+    for (; k < n; k += stride) {
         const double r = ref[k];
         const double d = (double)out[k] - r;
         s0 = fma(d, d, s0);
