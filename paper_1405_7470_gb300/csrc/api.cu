@@ -790,6 +790,8 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
             t.Kp = (N + kbw - 1) / kbw * kbw;
         }
         t.nkb = t.Kp / t.KB;
+        if (t.nkb > 16)
+            return LC_ERR_INVALID_VARIANT;  // more K-blocks than the kernel has barrier pairs for
         t.stages = v->stages;
         t.threads_per_row = v->unroll;
         t.conv_threads_per_row = std::min(v->unroll, 6 - v->unroll);
@@ -827,7 +829,7 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
                 off += (size_t)q.obufs * (q.store_quarters == 4 ? G : 1) * 128 * N * 4;
             off = (off + 15) / 16 * 16;
             q.off_bar = (unsigned)off;
-            off += 128;  // 14 mbarriers, TMEM address, abort flag
+            off += 1024;  // 10 mbarriers, TMEM address, abort flag; 2 x 2 x 16 A-block mbarriers
             // alignment slack; at least 120 KB so one CTA holds an SM (and its tensor memory)
             q.smem_bytes = (unsigned)std::max<size_t>(off + 1024, 120 * 1024);
             return q.smem_bytes <= smem_cap;

@@ -214,6 +214,9 @@ __device__ __forceinline__ bool bar_or(int id, int nthreads, bool v)
     }
 }
 
+// K-blocks per A buffer with their own full/empty barrier pair
+static constexpr int kTcMaxKB = 16;
+
 // Accumulator chunks (CW columns each) an epilogue warp loads before one wait: 32 registers
 // of loaded values, half of them per region when the BF16X3 terms are stacked.
 template <int NT, int CW>
@@ -266,10 +269,11 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
     float *stage = reinterpret_cast<float *>(smem + a.off_stage);  // S x [TE*N] fp32
     float *ost0 = reinterpret_cast<float *>(smem + a.off_out);     // obufs x [4][32][N] slots (element-major)
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + a.off_bar);
-    uint64_t *u_full = bar, *u_empty = bar + 3, *a_full = bar + 6, *a_empty = bar + 8;
-    uint64_t *acc_full = bar + 10, *acc_empty = bar + 12;
-    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bar + 14);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(bar + 15);
+    uint64_t *u_full = bar, *u_empty = bar + 3, *acc_full = bar + 6, *acc_empty = bar + 8;
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bar + 10);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bar + 11);
+    // A buffers are handed over per K-block: a_full/a_empty[ab * kTcMaxKB + kb]
+    uint64_t *a_full = bar + 16, *a_empty = bar + 16 + 2 * kTcMaxKB;
 
     const int prod_warp = NW + NC, mma_warp = NW + NC + 1;
     if (warp == mma_warp)
@@ -280,10 +284,12 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
             mbar_init(&u_empty[q], NC);
         }
         for (int q = 0; q < 2; ++q) {
-            mbar_init(&a_full[q], NC);
-            mbar_init(&a_empty[q], 1);
             mbar_init(&acc_full[q], 1);
             mbar_init(&acc_empty[q], NW);
+        }
+        for (int q = 0; q < 2 * kTcMaxKB; ++q) {
+            mbar_init(&a_full[q], NC);
+            mbar_init(&a_empty[q], 1);
         }
         *abort_flag = 0;
         fence_mbar_init();
@@ -362,81 +368,86 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
         }
     } else if (warp == mma_warp) {
         // ---------------- MMA issuer
+        // K-blocks outermost: the MMAs of block kb (every product) are followed by a commit
+        // that hands that block of the A buffer back to the conversion warps, which refill it
+        // for a later tile while the remaining blocks are multiplied.
         const uint32_t idesc = instr_desc(CBp), idesc2 = instr_desc(2 * CBp);
         int k = 0;
         for (long long t = my_first; t < a.ntiles; t += my_step, ++k) {
             const int b = k & 1, ab = k % NA;
             const uint32_t n = (uint32_t)(k >> 1), na = (uint32_t)(k / NA);
-            bool ok = mbar_wait(&a_full[ab], na & 1u);
-            ok = ok && mbar_wait(&acc_empty[b], (n & 1u) ^ 1u);
+            bool ok = mbar_wait(&acc_empty[b], (n & 1u) ^ 1u);
+            const uint32_t dtm = tmem_base + (uint32_t)b * a.tmem_cols;
+            const uint64_t a0 = smem_desc(sbase + offA + (uint32_t)ab * bufA, W);
+            const uint64_t b0 = smem_desc(sbase, W);
+            for (int kb = 0; kb < nkb && ok; ++kb) {
+                ok = mbar_wait(&a_full[ab * kTcMaxKB + kb], na & 1u);
+                if (!ok)
+                    break;
+                tc_fence_after();
+                if (lane == 0) {
+                    const int steps = min(KB, Kn - kb * KB) / 16;  // all-zero K steps skipped
+                    // the K steps of block kb of one product: A term `at` times the B rows from
+                    // `brow`, into accumulator columns dcol.. (descriptor += byte offset / 16)
+                    auto mma_block = [&](int at, int brow, uint32_t id, uint32_t dcol, uint32_t accumulate) {
+                        const uint64_t ad = a0 + ((uint32_t)(at * termA + kb * TE * W) >> 4);
+                        const uint64_t bd = b0 + ((uint32_t)(brow * W + kb * bkb) >> 4);
+                        for (int ki = 0; ki < steps; ++ki) {
+                            tc_mma(dtm + dcol, ad + 2 * ki, bd + 2 * ki, id, accumulate);  // +32 bytes per K step
+                            accumulate = 1;
+                        }
+                    };
+                    const uint32_t acc = kb > 0;  // the first block of a region's first product overwrites
+                    if (NT == 1) {
+                        mma_block(0, 0, idesc, 0, acc);
+                    } else if (a.stack) {
+                        // two regions R0 = columns [0, CBp), R1 = [CBp, 2 CBp), summed by the
+                        // epilogue: R0 <- u_lo D_hi, R1 <- u_hi D_lo, then u_mid and u_hi times
+                        // [D_hi; D_mid] into both
+                        mma_block(2, 0, idesc, 0, acc);
+                        mma_block(0, 2 * CBp, idesc, (uint32_t)CBp, acc);
+                        mma_block(1, 0, idesc2, 0, 1);
+                        mma_block(0, 0, idesc2, 0, 1);
+                    } else {
+                        // (D term, u term): lh, hl, mm, mh, hm, hh (small products first)
+#pragma unroll
+                        for (int p = 0; p < 6; ++p) {
+                            const int bt = p == 0 ? 2 : (p == 2 || p == 3) ? 1 : 0;
+                            const int at = p == 1 ? 2 : (p == 2 || p == 4) ? 1 : 0;
+                            mma_block(at, bt * CBp, idesc, 0, p == 0 ? acc : 1u);
+                        }
+                    }
+                    tc_commit(&a_empty[ab * kTcMaxKB + kb]);
+                }
+                __syncwarp();
+            }
             if (!ok) {
                 if (lane == 0)
                     fail();
                 break;
             }
-            tc_fence_after();
-            if (lane == 0) {
-                const uint32_t dtm = tmem_base + (uint32_t)b * a.tmem_cols;
-                const uint64_t a0 = smem_desc(sbase + offA + (uint32_t)ab * bufA, W);
-                const uint64_t b0 = smem_desc(sbase, W);
-                const uint32_t a_kb = (uint32_t)(TE * W) >> 4, b_kb = bkb >> 4;
-                // One product over all K: A term `at` times the B rows starting at `brow`,
-                // into accumulator columns dcol.. (descriptors advance by byte offset / 16).
-                auto chain = [&](int at, int brow, uint32_t id, uint32_t dcol, uint32_t accumulate) {
-                    uint64_t ad = a0 + ((at * termA) >> 4), bd = b0 + ((uint32_t)(brow * W) >> 4);
-                    for (int kb = 0; kb < nkb; ++kb) {
-                        const int kin_steps = min(KB, Kn - kb * KB) / 16;  // all-zero K steps skipped
-                        for (int ki = 0; ki < kin_steps; ++ki) {
-                            tc_mma(dtm + dcol, ad + 2 * ki, bd + 2 * ki, id, accumulate);  // +32 bytes per K step
-                            accumulate = 1;
-                        }
-                        ad += a_kb;
-                        bd += b_kb;
-                    }
-                };
-                if (NT == 1) {
-                    chain(0, 0, idesc, 0, 0);
-                } else if (a.stack) {
-                    // two regions R0 = columns [0, CBp), R1 = [CBp, 2 CBp), summed by the epilogue:
-                    // R0 <- u_lo D_hi, R1 <- u_hi D_lo, then u_mid and u_hi times [D_hi; D_mid]
-                    chain(2, 0, idesc, 0, 0);
-                    chain(0, 2 * CBp, idesc, (uint32_t)CBp, 0);
-                    chain(1, 0, idesc2, 0, 1);
-                    chain(0, 0, idesc2, 0, 1);
-                } else {
-                    // (D term, u term): lh, hl, mm, mh, hm, hh (small products first)
-#pragma unroll
-                    for (int p = 0; p < 6; ++p) {
-                        const int bt = p == 0 ? 2 : (p == 2 || p == 3) ? 1 : 0;
-                        const int at = p == 1 ? 2 : (p == 2 || p == 4) ? 1 : 0;
-                        chain(at, bt * CBp, idesc, 0, p == 0 ? 0u : 1u);
-                    }
-                }
-                tc_commit(&a_empty[ab]);
+            if (lane == 0)
                 tc_commit(&acc_full[b]);
-            }
             __syncwarp();
             if (*abort_flag)
                 break;
         }
     } else if (warp >= NW) {
-        // ---------------- conversion warps: fp32 u tile -> bf16 A-operand terms
+        // ---------------- conversion warps: fp32 u tile -> bf16 A-operand terms, K-block by K-block
         int k = 0;
-        for (long long t = my_first; t < a.ntiles; t += my_step, ++k) {
+        bool ok = true;
+        for (long long t = my_first; t < a.ntiles && ok; t += my_step, ++k) {
             const int s = k % S, ab = k % NA;
             const uint32_t ns = (uint32_t)(k / S), na = (uint32_t)(k / NA);
-            if (!(mbar_wait(&u_full[s], ns & 1u) && mbar_wait(&a_empty[ab], (na & 1u) ^ 1u))) {
-                if (lane == 0)
-                    fail();
+            if (!mbar_wait(&u_full[s], ns & 1u)) {
+                ok = false;
                 break;
             }
-            tc_fence_after();
             const long long e0 = t * TE;
             const int TEv = (int)min((long long)TE, E - e0);
             const bool from_stage = tile_bulk_bytes(t) != 0;
             const float *st = stage + (size_t)s * TE * N;
             unsigned char *Ab = smem + offA + (size_t)ab * bufA;
-            const int c8n = Kn / 8;
             const bool rowv = row < TEv;
             // K chunk c8 (8 values of j) of this thread's row -> the A terms
             auto put = [&](int c8, const float *x) {
@@ -449,51 +460,65 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
                     *reinterpret_cast<uint4 *>(Ab + off + tt * termA) = tt4[tt];
             };
             const int full8 = rowv ? N / 8 : 0;  // chunks with all 8 values inside the row
-            if (from_stage) {
-                // staged tile: compile-time stride along j; two chunks in flight
-                constexpr int JS = NODE ? TE : 1;
-                const float *src = NODE ? st + row : st + row * N;
-                int c8 = part;
-                for (; c8 + Hc < full8; c8 += 2 * Hc) {
-                    float x[8], y[8];
-                    const float *p0 = src + c8 * 8 * JS, *p1 = src + (c8 + Hc) * 8 * JS;
+            for (int kb = 0; kb < nkb; ++kb) {
+                if (!mbar_wait(&a_empty[ab * kTcMaxKB + kb], (na & 1u) ^ 1u)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const int c8_lo = kb * KB / 8, c8_hi = min(Kn, (kb + 1) * KB) / 8;
+                if (from_stage) {
+                    // staged tile: compile-time stride along j; two chunks in flight
+                    constexpr int JS = NODE ? TE : 1;
+                    const float *src = NODE ? st + row : st + row * N;
+                    const int f_hi = min(full8, c8_hi);
+                    int c8 = c8_lo + part;
+                    for (; c8 + Hc < f_hi; c8 += 2 * Hc) {
+                        float x[8], y[8];
+                        const float *p0 = src + c8 * 8 * JS, *p1 = src + (c8 + Hc) * 8 * JS;
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        x[q] = p0[q * JS];
-                        y[q] = p1[q * JS];
+                        for (int q = 0; q < 8; ++q) {
+                            x[q] = p0[q * JS];
+                            y[q] = p1[q * JS];
+                        }
+                        put(c8, x);
+                        put(c8 + Hc, y);
                     }
-                    put(c8, x);
-                    put(c8 + Hc, y);
-                }
-                for (; c8 < c8n; c8 += Hc) {
-                    float x[8];
-                    const float *p0 = src + c8 * 8 * JS;
+                    for (; c8 < c8_hi; c8 += Hc) {
+                        float x[8];
+                        const float *p0 = src + c8 * 8 * JS;
 #pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        x[q] = (rowv && c8 * 8 + q < N) ? p0[q * JS] : 0.f;
-                    put(c8, x);
-                }
-            } else {
-                // unaligned tail tile read from global memory
-                const float *src = NODE ? a.u + e0 + row : a.u + (e0 + row) * N;
-                const long long js = NODE ? E : 1;
-                for (int c8 = part; c8 < c8n; c8 += Hc) {
-                    float x[8];
+                        for (int q = 0; q < 8; ++q)
+                            x[q] = (rowv && c8 * 8 + q < N) ? p0[q * JS] : 0.f;
+                        put(c8, x);
+                    }
+                } else {
+                    // unaligned tail tile read from global memory
+                    const float *src = NODE ? a.u + e0 + row : a.u + (e0 + row) * N;
+                    const long long js = NODE ? E : 1;
+                    for (int c8 = c8_lo + part; c8 < c8_hi; c8 += Hc) {
+                        float x[8];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        x[q] = (rowv && c8 * 8 + q < N) ? src[(long long)(c8 * 8 + q) * js] : 0.f;
-                    put(c8, x);
+                        for (int q = 0; q < 8; ++q)
+                            x[q] = (rowv && c8 * 8 + q < N) ? src[(long long)(c8 * 8 + q) * js] : 0.f;
+                        put(c8, x);
+                    }
                 }
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(&a_full[ab * kTcMaxKB + kb]);
             }
-            fence_async_smem();
+            if (!ok)
+                break;
             __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(&u_empty[s]);
-                mbar_arrive(&a_full[ab]);
-            }
+            if (lane == 0)
+                mbar_arrive(&u_empty[s]);  // every block of this tile has been read from the stage
             if (*abort_flag)
                 break;
         }
+        if (!ok && lane == 0)
+            fail();
     } else {
         // ---------------- epilogue warps: TMEM accumulators -> out
         // Warp w reads TMEM lane quarter q = w % 4 (tile rows 32q..32q+31); the He warps of a
