@@ -40,7 +40,18 @@ WORKLOADS = {
                       desc="precision-sweep problem E=2^20 N=84 F=4 (u scaled 10^k)"),
     "fp64_single": dict(E=4096, N=20, F=1, precision="fp64",
                         desc="FP64 single-operator contraction E=4096 N=20 F=1"),
+    # eight groups, N in {4,...,165}, E_g log-uniform in [2^14, 2^21] (seed 0), F = 3: E and N
+    # here are totals / maxima for the record; the groups come from synth.grouped_sizes(0)
+    "grouped": dict(E=0, N=165, F=3, precision="fp32",
+                    desc="uneven batching: 8 groups N in {4,10,20,35,56,84,120,165}, E_g log-uniform "
+                         "in [2^14,2^21] (seed 0), F=3; one persistent grouped launch replayed from a "
+                         "CUDA graph"),
 }
+
+# FP32 SIMT descriptors tried for the grouped launch: (elems_per_thread, split_i, unroll,
+# prefetch_smem, stages, ctas_per_sm)
+GROUPED_CANDIDATES = [(8, 4, 4, 1, 2, 2), (4, 8, 4, 1, 2, 2), (8, 8, 1, 1, 1, 1), (8, 4, 4, 1, 1, 3),
+                      (8, 8, 1, 1, 2, 1)]
 
 # DRAM bytes per launch from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum),
 # keyed by (workload, layout, precision, engine); valid only while the kernel sources hash
@@ -220,7 +231,7 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     wl = dict(WORKLOADS[args.workload])
     wl["storage"] = "fp64" if wl["precision"] == "fp64" else "fp32"
-    if not args.precision and wl["storage"] == "fp32":
+    if not args.precision and wl["storage"] == "fp32" and args.workload != "grouped":
         args.precision = "bf16x3"
     if args.precision:
         if (args.precision == "fp64") != (wl["storage"] == "fp64"):
@@ -234,6 +245,10 @@ def main():
         if rank != 0:
             return
         return run_reference(args, wl)
+    if args.workload == "grouped":
+        if args.precision not in ("", "fp32", "bf16x3"):
+            ap.error("the grouped launch runs the FP32 SIMT engine")
+        return run_grouped(args, wl, world, rank, local_rank)
 
     import torch
     import torch.distributed as dist
@@ -279,6 +294,26 @@ def main():
     if lc.device_error() != 0:
         raise RuntimeError("device error word set during warm-up")
 
+    # A step shorter than the host's launch latency would time the host, not the GPU: such
+    # steps are captured back to back in one CUDA graph and replayed (device time / K).
+    e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        step()
+        e_a.record(stream)
+        for _ in range(8):
+            step()
+        e_b.record(stream)
+    torch.cuda.synchronize()
+    use_graph = e_a.elapsed_time(e_b) / 8 < 0.1
+    graph = None
+    if use_graph:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            for _ in range(args.steps):
+                step()
+        graph.replay()
+        torch.cuda.synchronize()
+
     clocks = ClockSampler(local_rank)
     clocks.start()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -286,16 +321,24 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    for k in range(args.steps):
-        starts[k].record(stream)
-        step()
-        ends[k].record(stream)
+    if use_graph:
+        starts[0].record(stream)
+        graph.replay()
+        ends[-1].record(stream)
+    else:
+        for k in range(args.steps):
+            starts[k].record(stream)
+            step()
+            ends[k].record(stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
     total_ms = starts[0].elapsed_time(ends[-1])
-    per_launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    if use_graph:
+        per_launch_ms = [total_ms / args.steps]
+    else:
+        per_launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     if world > 1:
         t = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -360,12 +403,193 @@ def main():
                        "precision": wl["precision"], "variant": vd,
                        "variant_choice": f"autotuned over {n_tuned} candidates" if n_tuned else args.variant,
                        "parallelism": f"replicas x{world}",
-                       "l2": "inputs+outputs larger than L2 (no flush needed)",
+                       "l2": ("inputs+outputs larger than L2 (no flush needed)" if not use_graph else
+                              "inputs+outputs fit in L2 (1.3 MB); L2-resident by design of this small case"),
+                       "timing": (f"one CUDA graph of {args.steps} back-to-back steps, device time / steps"
+                                  if use_graph else "CUDA events around every step on the launching stream"),
                        "bytes_per_step": (8 if wl["precision"] == "fp64" else 4) * (E * N * (1 + F) + F * N * N)},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
             "clocks": clk, "rel_error_vs_oracle": rel_err,
             "hbm_gbs_achieved": ((8 if wl["precision"] == "fp64" else 4) * (E * N * (1 + F) + F * N * N))
             / (ms_per_step * 1e-3) / 1e9,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_grouped(args, wl, world, rank, local_rank):
+    """Grouped workload: one persistent launch over all groups (CUDA graph replay) per step."""
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    import synth
+    from paper_1405_7470_gb300 import lc
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    lc.load()
+    sms = lc.device_info()["sm_count"]
+    peaks = load_peaks()
+    F = wl["F"]
+    sizes = synth.grouped_sizes(0)
+    data = synth.grouped_operands(sizes, F=F, seed=0)
+    node = args.layout == "node"
+    flops = sum(2.0 * E * N * N * F for N, E in sizes)
+    nbytes = sum(4.0 * (E * N * (1 + F) + F * N * N) for N, E in sizes)
+    kernel = lc.Kernel()
+    stream = torch.cuda.Stream()
+    hosts, groups = [], []
+    for (N, E), (D, u) in zip(sizes, data):
+        uu = np.ascontiguousarray(synth.to_node_major(u) if node else u)
+        hosts.append((D, uu))
+        groups.append((torch.from_numpy(D).cuda(), torch.from_numpy(uu).cuda(),
+                       torch.empty((F, N, E) if node else (F, E, N), device="cuda")))
+
+    def timed(fn, reps):
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                fn()
+        stream.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        stream.synchronize()
+        return a.elapsed_time(b) / reps
+
+    # descriptor: the fastest of a few SIMT tile shapes, each planned and captured once
+    best = None
+    for re_, rc, unr, pf, st, cps in GROUPED_CANDIDATES:
+        v = lc.Variant(layout=args.layout, elems_per_thread=re_, split_i=rc, unroll=unr, prefetch_smem=pf,
+                       stages=st, ctas_per_sm=cps)
+        try:
+            plan = lc.GroupedPlan(kernel, v, groups, use_graph=True, stream=stream)
+        except lc.LcError:
+            continue
+        t = timed(lambda: plan.run(stream), 3)
+        if best is None or t < best[0]:
+            best = (t, v, plan)
+        else:
+            del plan
+    if best is None:
+        raise RuntimeError("no grouped plan fits")
+    _, v, plan = best
+    vd = lc.variant_dict(v)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            plan.run(stream)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        starts[k].record(stream)
+        plan.run(stream)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = starts[0].elapsed_time(ends[-1])
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    launch_s = statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends)) * 1e-3
+
+    # the same groups as one launch per group, each with its default descriptor
+    vs = [lc.variant_default(kernel, E, N, F, args.layout, "fp32") for N, E in sizes]
+
+    def per_group():
+        for vg, (D, u, out) in zip(vs, groups):
+            lc.contract(kernel, vg, D, u, out, stream=stream)
+    per_group_ms = timed(per_group, 5)
+    plan.run(stream)
+    torch.cuda.synchronize()
+
+    # error: sampled rows of every group against the FP64 oracle; CPU baseline: the oracle
+    # on a bounded sample of each group (the same number of elements from every group)
+    rel_err, cpu = None, None
+    if rank == 0 and not args.no_cpu_baseline:
+        errs = []
+        for (N, E), (D, uu), (_, _, out) in zip(sizes, hosts, groups):
+            rows = np.random.default_rng(N).integers(0, E, 1000)
+            u_rows = uu[:, rows].T if node else uu[rows]
+            ref = oracle.contract_rows(D, np.ascontiguousarray(u_rows), np.arange(len(rows)))
+            o = out.cpu().numpy()
+            got = o[:, :, rows].transpose(0, 2, 1) if node else o[:, rows, :]
+            errs.append(oracle.rel_fro_error(got, ref))
+        rel_err = max(errs)
+        per = 1 << 14
+        t0 = time.perf_counter()
+        sflops = 0.0
+        for (N, E), (D, uu) in zip(sizes, hosts):
+            sub = np.ascontiguousarray(uu[:, :per] if node else uu[:per], dtype=np.float64)
+            oracle.contract(D.astype(np.float64), sub, args.layout)
+            sflops += 2.0 * min(per, E) * N * N * F
+        dt = time.perf_counter() - t0
+        cpu = {"value": sflops / dt / 1e9, "unit": "GFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"first {per} elements of each of the 8 groups, {dt:.1f} s, OpenMP over elements"}
+
+    # end to end: host u and D in, host out back, around the same graph launch
+    e2e = None
+    if not args.no_e2e:
+        pinned = [(torch.from_numpy(D).pin_memory(), torch.from_numpy(uu).pin_memory(),
+                   torch.empty(tuple(g[2].shape)).pin_memory()) for (D, uu), g in zip(hosts, groups)]
+
+        def estep():
+            with torch.cuda.stream(stream):
+                for (Dh, uh, _), (D, u, _) in zip(pinned, groups):
+                    D.copy_(Dh, non_blocking=True)
+                    u.copy_(uh, non_blocking=True)
+                plan.run(stream)
+                for (_, _, oh), (_, _, out) in zip(pinned, groups):
+                    oh.copy_(out, non_blocking=True)
+        es = timed(estep, max(3, args.steps // 4))
+        e2e = {"value": flops / (es * 1e-3) / 1e9, "unit": "GFLOP/s",
+               "h2d_bytes_per_step": int(sum(4 * (E * N + F * N * N) for N, E in sizes)),
+               "d2h_bytes_per_step": int(sum(4 * F * E * N for N, E in sizes)), "ms_per_step": es}
+    if lc.device_error() != 0:
+        raise RuntimeError("device error word set during the timed region")
+
+    if rank == 0:
+        alu_peak = sms * 128 * 2 * peaks["sm_max_mhz"] * 1e6
+        t_alu, t_hbm = flops / alu_peak, nbytes / (peaks["hbm_gbs"] * 1e9)
+        if t_alu > t_hbm:
+            ach = flops / launch_s / 1e12
+            roof = {"bound": "alu", "achieved": ach, "peak": alu_peak / 1e12, "unit": "TFLOP/s",
+                    "frac": ach / (alu_peak / 1e12), "traffic": None,
+                    "peak_source": f"derived: {sms} SMs x 128 FMA lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz",
+                    "hbm_frac": (nbytes / launch_s / 1e9) / peaks["hbm_gbs"]}
+        else:
+            ach = nbytes / launch_s / 1e9
+            roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": peaks["source"]}
+        line = {
+            "metric": "contraction GFLOP/s", "value": flops * world / (ms_per_step * 1e-3) / 1e9, "unit": "GFLOP/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": wl["desc"], "groups": [{"N": N, "E": E} for N, E in sizes],
+                       "E_total": int(sum(E for _, E in sizes)), "F": F, "layout": args.layout,
+                       "precision": "fp32", "variant": vd,
+                       "variant_choice": f"fastest of {len(GROUPED_CANDIDATES)} grouped tile shapes",
+                       "parallelism": f"replicas x{world}",
+                       "l2": "inputs+outputs larger than L2 (no flush needed)", "bytes_per_step": nbytes,
+                       "per_group_launches_ms": per_group_ms, "grouped_plan": plan.info()},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+            "clocks": clk, "rel_error_vs_oracle": rel_err,
+            "hbm_gbs_achieved": nbytes / (ms_per_step * 1e-3) / 1e9,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -383,6 +607,8 @@ def run_reference(args, wl):
         D, u = synth.fp64_single()
     else:
         D, u = synth.fp32_three()
+    if args.workload == "grouped":
+        return run_reference_grouped(args, wl)
     Es = min(E, 1 << 18)
     sub = u[:Es]
     u_in = synth.to_node_major(sub) if args.layout == "node" else sub
@@ -405,6 +631,47 @@ def run_reference(args, wl):
         "impl": "reference",
         "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": "GFLOP/s",
                          "sample": f"first {Es} of {E} elements per step, OpenMP over elements"},
+        "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_grouped(args, wl):
+    """CPU FP64 oracle over a bounded sample of every group (the first 2^14 elements of each)."""
+    import oracle
+    import synth
+    F = wl["F"]
+    sizes = synth.grouped_sizes(0)
+    data = synth.grouped_operands(sizes, F=F, seed=0)
+    per = 1 << 14
+    subs = []
+    for (N, E), (D, u) in zip(sizes, data):
+        sub = u[:per]
+        subs.append((D.astype(np.float64),
+                     np.ascontiguousarray(synth.to_node_major(sub) if args.layout == "node" else sub,
+                                          dtype=np.float64)))
+    flops = sum(2.0 * min(per, E) * N * N * F for N, E in sizes)
+
+    def one():
+        for D64, u64 in subs:
+            oracle.contract(D64, u64, args.layout)
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    dt = (time.perf_counter() - t0) / args.steps
+    value = flops / dt / 1e9
+    cores = oracle.num_threads()
+    line = {
+        "metric": "contraction GFLOP/s", "value": value, "unit": "GFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["desc"], "layout": args.layout, "precision": "fp32",
+                   "sample_elements_per_group": per},
+        "impl": "reference",
+        "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": "GFLOP/s",
+                         "sample": f"first {per} elements of each of the 8 groups per step, OpenMP over elements"},
         "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

@@ -150,6 +150,37 @@ lc_status lc_variant_validate(const lc_kernel *k, int64_t E, int32_t N, int32_t 
                               const lc_variant *v);
 
 /*
+ * The launch plan a valid descriptor resolves to for a problem size: what the split,
+ * ilp and prefetch transformations of Section 2.4 amount to on this GPU (the CUDA
+ * device current on the calling thread; without one, a 148-SM, 227 KB part is assumed).
+ * Nothing is launched.  The caller sets p->struct_size = sizeof(lc_plan).
+ * Errors: those of lc_variant_validate; LC_ERR_INVALID_ARGUMENT for a null or
+ * mis-sized p.
+ */
+typedef struct lc_plan {
+    uint32_t struct_size;    /* sizeof(lc_plan) */
+    int32_t grid;            /* CTAs launched */
+    int32_t threads;         /* threads per CTA */
+    int32_t smem_bytes;      /* dynamic shared memory per CTA */
+    int64_t tiles;           /* element tiles (ceil(E / tile)) */
+    int32_t column_blocks;   /* CTAs that share one element tile (operator or row blocks) */
+    int32_t ops_per_block;   /* operators per column block (0: blocks are row ranges) */
+    /* tensor-core engine only (0 otherwise) */
+    int32_t k_mma;           /* K the MMAs read: N rounded up to 16 */
+    int32_t k_block;         /* K-block width (bf16 values per swizzled row) */
+    int32_t cols_per_op;     /* accumulator columns per operator */
+    int32_t mma_n;           /* MMA N: accumulator columns per column block */
+    int32_t stacked;         /* 1: BF16X3 D terms stacked along N (4 MMAs per K step) */
+    int32_t a_buffers;       /* A-operand buffers */
+    int32_t out_slots;       /* element-major output staging slots */
+    int32_t store_rows;      /* element-major tile rows per bulk store */
+    int32_t mma_per_tile;    /* tcgen05.mma instructions per tile and column block */
+} lc_plan;
+
+lc_status lc_variant_plan(const lc_kernel *k, int64_t E, int32_t N, int32_t F, const lc_variant *v,
+                          lc_plan *p);
+
+/*
  * The contraction itself: enqueue out = contraction(D, u) on `stream`.
  *   D_dev    [F][N][N] operators (double for FP64, else float)
  *   u_dev    input, layout per v->layout

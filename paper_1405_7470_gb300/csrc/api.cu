@@ -1075,6 +1075,50 @@ lc_status lc_variant_validate(const lc_kernel *kh, int64_t E, int32_t N, int32_t
     return resolve(kh->k, E, N, F, v, r, false);
 }
 
+lc_status lc_variant_plan(const lc_kernel *kh, int64_t E, int32_t N, int32_t F, const lc_variant *v,
+                          lc_plan *p)
+{
+    if (!kh || !p || p->struct_size != sizeof(lc_plan))
+        return LC_ERR_INVALID_ARGUMENT;
+    Resolved r;
+    lc_status st = resolve(kh->k, E, N, F, v, r, true);
+    if (st == LC_ERR_NO_DEVICE)
+        st = resolve(kh->k, E, N, F, v, r, false);
+    if (st != LC_OK)
+        return st;
+    lc_plan q;
+    memset(&q, 0, sizeof q);
+    q.struct_size = sizeof(lc_plan);
+    if (r.engine == LC_ENGINE_TCGEN05) {
+        const TcArgs &t = r.tc;
+        const int nt = r.precision == LC_PREC_BF16X3 ? 3 : 1;
+        q.grid = r.tc_grid;
+        q.threads = 128 * (t.threads_per_row + t.conv_threads_per_row) + 64;
+        q.smem_bytes = (int32_t)t.smem_bytes;
+        q.tiles = t.ntiles;
+        q.column_blocks = t.nblocks;
+        q.ops_per_block = t.G;
+        q.k_mma = (N + 15) / 16 * 16;
+        q.k_block = t.KB;
+        q.cols_per_op = t.Np;
+        q.mma_n = t.CBp;
+        q.stacked = t.stack;
+        q.a_buffers = t.abufs;
+        q.out_slots = r.layout == LC_LAYOUT_ELEM_MAJOR ? t.obufs : 0;
+        q.store_rows = r.layout == LC_LAYOUT_ELEM_MAJOR ? 32 * t.store_quarters : 0;
+        q.mma_per_tile = (nt == 1 ? 1 : (t.stack ? 4 : 6)) * (q.k_mma / 16);
+    } else {
+        q.grid = r.g.grid;
+        q.threads = r.g.threads;
+        q.smem_bytes = (int32_t)r.g.smem;
+        q.tiles = r.g.ntiles;
+        q.column_blocks = r.engine == LC_ENGINE_SIMT ? r.g.nchunks : 1;
+        q.ops_per_block = r.engine == LC_ENGINE_SIMT ? (r.g.isplit ? 0 : r.g.G) : F;
+    }
+    *p = q;
+    return LC_OK;
+}
+
 lc_status lc_variant_default(const lc_kernel *kh, int64_t E, int32_t N, int32_t F, int32_t layout,
                              int32_t precision, lc_variant *v)
 {
@@ -1120,7 +1164,7 @@ lc_status lc_variant_default(const lc_kernel *kh, int64_t E, int32_t N, int32_t 
         // fewest cycles; then the narrowest blocks that cover K (least shared memory)
         lc_status st = LC_ERR_INVALID_VARIANT;
         for (int kbw : {64, 1})
-            for (int stg : {3, 2, 1}) {
+            for (int stg : {2, 3, 1}) {
                 if (st == LC_OK)
                     break;
                 d.elems_per_thread = kbw;

@@ -47,6 +47,15 @@ class lc_variant(ctypes.Structure):
     ]
 
 
+class lc_plan(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("grid", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("smem_bytes", ctypes.c_int32), ("tiles", ctypes.c_int64)] + [
+        (n, ctypes.c_int32) for n in (
+            "column_blocks", "ops_per_block", "k_mma", "k_block", "cols_per_op", "mma_n", "stacked", "a_buffers",
+            "out_slots", "store_rows", "mma_per_tile")
+    ]
+
+
 class lc_group(ctypes.Structure):
     _fields_ = [("E", ctypes.c_int64), ("N", ctypes.c_int32), ("F", ctypes.c_int32),
                 ("D_dev", ctypes.c_void_p), ("u_dev", ctypes.c_void_p), ("out_dev", ctypes.c_void_p)]
@@ -63,6 +72,7 @@ SIGNATURES = {
     "lc_kernel_print": ([_P, _VP, ctypes.c_char_p, _SZ, ctypes.POINTER(_SZ)], ctypes.c_int),
     "lc_variant_default": ([_P, _I64, _I32, _I32, _I32, _I32, _VP], ctypes.c_int),
     "lc_variant_validate": ([_P, _I64, _I32, _I32, _VP], ctypes.c_int),
+    "lc_variant_plan": ([_P, _I64, _I32, _I32, _VP, ctypes.POINTER(lc_plan)], ctypes.c_int),
     "lc_contract": ([_P, _VP, _P, _P, _P, _I64, _I32, _I32, _P], ctypes.c_int),
     "lc_contract_host": ([_P, _VP, _P, _P, _P, _I64, _I32, _I32, _P, _P, _P, _P], ctypes.c_int),
     "lc_device_error": ([ctypes.c_int], ctypes.c_int),
@@ -184,6 +194,14 @@ def variant_default(kernel: Kernel, E: int, N: int, F: int, layout="elem", preci
 
 def variant_validate(kernel: Kernel, E: int, N: int, F: int, v: lc_variant) -> int:
     return load().lc_variant_validate(kernel.handle, E, N, F, ctypes.byref(v))
+
+
+def variant_plan(kernel: Kernel, E: int, N: int, F: int, v: lc_variant) -> dict:
+    """The launch plan (lc_variant_plan) of a valid descriptor, as a dict."""
+    p = lc_plan()
+    p.struct_size = ctypes.sizeof(lc_plan)
+    check(load().lc_variant_plan(kernel.handle, E, N, F, ctypes.byref(v), ctypes.byref(p)), "lc_variant_plan")
+    return {n: getattr(p, n) for n, _ in lc_plan._fields_ if n != "struct_size"}
 
 
 def lc_contract(kernel: Kernel, v: lc_variant, D_ptr: int, u_ptr: int, out_ptr: int, E: int, N: int, F: int,

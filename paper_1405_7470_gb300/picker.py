@@ -30,27 +30,59 @@ from . import lc
 
 PATHS = ("fp32", "bf16", "bf16x3")
 LAYOUTS = ("elem", "node")
-DIN = 25  # feature count (the library supports up to 32)
+DIN = 32  # feature count (the library's limit)
 
 
-def features(shape: dict, v) -> np.ndarray:
-    """Feature vector of (problem, descriptor); every entry is O(1)."""
+def features(shape: dict, v, plan: dict | None = None) -> np.ndarray:
+    """Feature vector of (problem, descriptor, resolved launch plan); every entry is O(1).
+
+    `plan` is lc_variant_plan's result for the descriptor (computed here when omitted).
+    """
     d = v if isinstance(v, dict) else lc.variant_dict(v)
     E, N, F = shape["E"], shape["N"], shape["F"]
+    if plan is None:
+        plan = _plan(shape, v)
     eng = d["engine"]
+    units = plan["tiles"] * plan["column_blocks"] / max(plan["grid"], 1)  # tiles per CTA
     x = [
         math.log2(max(E, 1)) / 23.0, N / 165.0, (N % 16) / 16.0, F / 4.0,
         float(shape["path"] == "fp32"), float(shape["path"] == "bf16"), float(shape["path"] == "bf16x3"),
         float(shape["layout"] == "elem"), float(shape["layout"] == "node"),
-        math.log2(max(E, 1) * N * F) / 32.0, N * F / 660.0, math.log2(N) / 8.0,
+        math.log2(max(E, 1) * N * F) / 32.0, float(plan["stacked"]), math.log2(N) / 8.0,
         float(eng == "simt"), float(eng == "tcgen05"), float(eng == "warp"),
         math.log2(max(d["tile_e"], 1)) / 10.0, d["elems_per_thread"] / 64.0 if eng == "tcgen05" else d["elems_per_thread"] / 8.0,
         d["split_i"] / 8.0, math.log2(max(d["unroll"], 1)) / 3.0, float(d["prefetch_smem"]), d["stages"] / 3.0,
         d["ctas_per_sm"] / 4.0, float(d["precision"] == "fp32"), float(d["precision"] in ("bf16", "bf16x3")),
         d.get("store_rows", 0) / 128.0,
+        math.log2(max(plan["grid"], 1)) / 10.0, math.log2(1.0 + units) / 16.0, plan["column_blocks"] / 8.0,
+        plan["smem_bytes"] / 232448.0, plan["threads"] / 1024.0,
+        math.log2(1.0 + plan["mma_per_tile"] * units) / 20.0, plan["a_buffers"] / 2.0 + plan["out_slots"] / 8.0,
     ]
     assert len(x) == DIN
     return np.asarray(x, dtype=np.float32)
+
+
+_KERNELS = {}
+
+
+def _plan(shape: dict, v) -> dict:
+    """lc_variant_plan for a shape's kernel (one kernel handle per operator count)."""
+    F = shape["F"]
+    if F not in _KERNELS:
+        _KERNELS[F] = lc.Kernel() if F > 1 else lc.Kernel("{ [e,i,j]: 0<=e<E and 0<=i,j<N }",
+                                                          "out[e,i] = sum(j, D[i,j]*u[e,j])")
+    vv = v if not isinstance(v, dict) else _variant_from_dict(v)
+    try:
+        return lc.variant_plan(_KERNELS[F], shape["E"], shape["N"], F, vv)
+    except lc.LcError:
+        # not a valid descriptor for this shape (never a candidate): an all-zero plan
+        return dict(grid=0, threads=0, smem_bytes=0, tiles=0, column_blocks=0, ops_per_block=0, k_mma=0,
+                    k_block=0, cols_per_op=0, mma_n=0, stacked=0, a_buffers=0, out_slots=0, store_rows=0,
+                    mma_per_tile=0)
+
+
+def _variant_from_dict(d: dict):
+    return lc.Variant(**d)
 
 
 def he_uniform(din: int, seed: int) -> np.ndarray:

@@ -149,3 +149,26 @@ def test_default_variant_fits(lib):
         for layout in ("elem", "node"):
             v = lc.variant_default(k, E, N, F, layout, "fp32")
             assert lc.variant_validate(k, E, N, F, v) == 0
+
+
+def test_variant_plan_reports_the_resolved_launch(lib):
+    """lc_variant_plan: the tensor plan of the default BF16X3 descriptor, a SIMT plan, and
+    the argument checks (host only; without a GPU a 148-SM part is assumed)."""
+    k = lc.Kernel()
+    v = lc.Variant(engine="tcgen05", layout="elem", precision="bf16x3", tile_e=128, elems_per_thread=64,
+                   split_i=0, unroll=4, prefetch_smem=1, stages=1, store_rows=128)
+    p = lc.variant_plan(k, 1 << 21, 35, 3, v)
+    assert p["tiles"] == (1 << 21) // 128 and p["column_blocks"] == 1 and p["ops_per_block"] == 3
+    assert p["k_mma"] == 48 and p["k_block"] == 64
+    # N = 35 pads to 40 columns per operator so that the D terms stack: 4 MMAs per K step
+    assert p["cols_per_op"] == 40 and p["mma_n"] == 128 and p["stacked"] == 1 and p["mma_per_tile"] == 12
+    assert p["threads"] == 128 * (4 + 2) + 64 and p["store_rows"] == 128
+    assert 0 < p["smem_bytes"] <= 232448
+    s = lc.variant_plan(k, 1 << 21, 35, 3, lc.variant_default(k, 1 << 21, 35, 3, "elem", "fp32"))
+    assert s["mma_per_tile"] == 0 and s["grid"] > 0 and s["tiles"] > 0
+    bad = lc.lc_plan()
+    bad.struct_size = 3
+    assert lib.lc_variant_plan(k.handle, 1 << 21, 35, 3, ctypes.byref(v), ctypes.byref(bad)) == 1
+    v.unroll = 9
+    with pytest.raises(lc.LcError):
+        lc.variant_plan(k, 1 << 21, 35, 3, v)
