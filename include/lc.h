@@ -170,7 +170,7 @@ typedef struct lc_plan {
     int32_t k_block;         /* K-block width (bf16 values per swizzled row) */
     int32_t cols_per_op;     /* accumulator columns per operator */
     int32_t mma_n;           /* MMA N: accumulator columns per column block */
-    int32_t stacked;         /* 1: BF16X3 D terms stacked along N (4 MMAs per K step) */
+    int32_t stacked;         /* 1: BF16X3 D terms stacked along N (5 MMAs per K step, not 6) */
     int32_t a_buffers;       /* A-operand buffers */
     int32_t out_slots;       /* element-major output staging slots */
     int32_t store_rows;      /* element-major tile rows per bulk store */

@@ -1106,7 +1106,7 @@ lc_status lc_variant_plan(const lc_kernel *kh, int64_t E, int32_t N, int32_t F, 
         q.a_buffers = t.abufs;
         q.out_slots = r.layout == LC_LAYOUT_ELEM_MAJOR ? t.obufs : 0;
         q.store_rows = r.layout == LC_LAYOUT_ELEM_MAJOR ? 32 * t.store_quarters : 0;
-        q.mma_per_tile = (nt == 1 ? 1 : (t.stack ? 4 : 6)) * (q.k_mma / 16);
+        q.mma_per_tile = (nt == 1 ? 1 : (t.stack ? 5 : 6)) * (q.k_mma / 16);
     } else {
         q.grid = r.g.grid;
         q.threads = r.g.threads;

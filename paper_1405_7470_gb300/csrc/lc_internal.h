@@ -88,7 +88,7 @@ struct TcArgs {
     int chunk;      // epilogue chunk: 16 columns when Np is a multiple of 16, else 8
     int CB, CBp;    // columns per block (G * Np) and the MMA N (CB rounded up to 16)
     int Kp, KB, nkb;  // K padded to the block width, K-block width (16/32/64 -> 32/64/128-byte swizzle), blocks
-    int stack;      // BF16X3 with two B terms stacked along N (2 * CBp <= 256): 4 MMAs per K step, not 6
+    int stack;      // BF16X3 with two B terms stacked along N (2 * CBp <= 256): 5 MMAs per K step, not 6
     int tmem_cols;  // columns per accumulator (power of two >= CBp, or >= 2 * CBp when stacked)
     int stages;     // u stage buffers (1 or 2)
     int threads_per_row;       // epilogue threads per tile row

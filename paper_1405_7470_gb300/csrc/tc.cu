@@ -7,8 +7,9 @@
 // Precision paths (FP32 accumulation in both):
 //   BF16    operands rounded to bfloat16 (nearest-even), one product.
 //   BF16X3  x = hi + mid + lo (three bfloat16 terms, exact for binary32); the six
-//           products hh, hm, mh, hl, lh, mm are accumulated, small ones first; the
-//           dropped products (ml, lm, ll) are below 2^-24 relative.
+//           products hh, hm, mh, hl, lh, mm are accumulated with the large hh sum kept
+//           apart from (or after) the others; the dropped products (ml, lm, ll) are
+//           below 2^-24 relative.
 //
 // Structure: a persistent, warp-specialised CTA per SM, roles linked by full/empty
 // mbarrier pairs (no CTA-wide barrier inside the tile loop):
@@ -368,10 +369,26 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
         }
     } else if (warp == mma_warp) {
         // ---------------- MMA issuer
-        // K-blocks outermost: the MMAs of block kb (every product) are followed by a commit
-        // that hands that block of the A buffer back to the conversion warps, which refill it
-        // for a later tile while the remaining blocks are multiplied.
+        // BF16 and stacked BF16X3: K-blocks outermost; the MMAs of block kb (every product)
+        // are followed by a commit that hands that block of the A buffer back to the
+        // conversion warps, which refill it for a later tile while the remaining blocks are
+        // multiplied.  Unstacked BF16X3: products outermost, small ones first over all of K
+        // (the large hh sum is accumulated last); a block is handed back after its last
+        // product.
         const uint32_t idesc = instr_desc(CBp), idesc2 = instr_desc(2 * CBp);
+        // the K steps of block kb of one product: A term `at` times the B rows from `brow`,
+        // into accumulator columns dcol.. (a descriptor advances by byte offset / 16)
+        auto mma_block = [&](uint32_t dtm, uint64_t a0, uint64_t b0, int kb, int at, int brow, uint32_t id,
+                             uint32_t dcol, uint32_t accumulate) {
+            const int steps = min(KB, Kn - kb * KB) / 16;  // all-zero K steps skipped
+            const uint64_t ad = a0 + ((uint32_t)(at * termA + kb * TE * W) >> 4);
+            const uint64_t bd = b0 + ((uint32_t)(brow * W + kb * bkb) >> 4);
+            for (int ki = 0; ki < steps; ++ki) {
+                tc_mma(dtm + dcol, ad + 2 * ki, bd + 2 * ki, id, accumulate);  // +32 bytes per K step
+                accumulate = 1;
+            }
+        };
+        const bool k_outer = NT == 1 || a.stack;
         int k = 0;
         for (long long t = my_first; t < a.ntiles; t += my_step, ++k) {
             const int b = k & 1, ab = k % NA;
@@ -380,46 +397,40 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
             const uint32_t dtm = tmem_base + (uint32_t)b * a.tmem_cols;
             const uint64_t a0 = smem_desc(sbase + offA + (uint32_t)ab * bufA, W);
             const uint64_t b0 = smem_desc(sbase, W);
-            for (int kb = 0; kb < nkb && ok; ++kb) {
-                ok = mbar_wait(&a_full[ab * kTcMaxKB + kb], na & 1u);
-                if (!ok)
-                    break;
-                tc_fence_after();
-                if (lane == 0) {
-                    const int steps = min(KB, Kn - kb * KB) / 16;  // all-zero K steps skipped
-                    // the K steps of block kb of one product: A term `at` times the B rows from
-                    // `brow`, into accumulator columns dcol.. (descriptor += byte offset / 16)
-                    auto mma_block = [&](int at, int brow, uint32_t id, uint32_t dcol, uint32_t accumulate) {
-                        const uint64_t ad = a0 + ((uint32_t)(at * termA + kb * TE * W) >> 4);
-                        const uint64_t bd = b0 + ((uint32_t)(brow * W + kb * bkb) >> 4);
-                        for (int ki = 0; ki < steps; ++ki) {
-                            tc_mma(dtm + dcol, ad + 2 * ki, bd + 2 * ki, id, accumulate);  // +32 bytes per K step
-                            accumulate = 1;
-                        }
-                    };
-                    const uint32_t acc = kb > 0;  // the first block of a region's first product overwrites
-                    if (NT == 1) {
-                        mma_block(0, 0, idesc, 0, acc);
-                    } else if (a.stack) {
-                        // two regions R0 = columns [0, CBp), R1 = [CBp, 2 CBp), summed by the
-                        // epilogue: R0 <- u_lo D_hi, R1 <- u_hi D_lo, then u_mid and u_hi times
-                        // [D_hi; D_mid] into both
-                        mma_block(2, 0, idesc, 0, acc);
-                        mma_block(0, 2 * CBp, idesc, (uint32_t)CBp, acc);
-                        mma_block(1, 0, idesc2, 0, 1);
-                        mma_block(0, 0, idesc2, 0, 1);
-                    } else {
-                        // (D term, u term): lh, hl, mm, mh, hm, hh (small products first)
-#pragma unroll
-                        for (int p = 0; p < 6; ++p) {
+            const int npass = k_outer ? 1 : 6;
+            for (int p = 0; p < npass && ok; ++p) {
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (p == 0) {
+                        ok = mbar_wait(&a_full[ab * kTcMaxKB + kb], na & 1u);
+                        if (!ok)
+                            break;
+                        tc_fence_after();
+                    }
+                    if (lane == 0) {
+                        const uint32_t acc = kb > 0;  // block 0 of a region's first product overwrites
+                        if (NT == 1) {
+                            mma_block(dtm, a0, b0, kb, 0, 0, idesc, 0, acc);
+                        } else if (a.stack) {
+                            // regions R0 = columns [0, CBp) and R1 = [CBp, 2 CBp), summed by the
+                            // epilogue: u_hi x [D_hi; D_mid] puts hh in R0 and hm in R1; the
+                            // smaller products lh, hl, mm, mh all go to R1, so the large R0 sum
+                            // takes one rounding per K step, as a plain FP32 dot product would
+                            mma_block(dtm, a0, b0, kb, 0, 0, idesc2, 0, acc);
+                            mma_block(dtm, a0, b0, kb, 2, 0, idesc, (uint32_t)CBp, 1);
+                            mma_block(dtm, a0, b0, kb, 0, 2 * CBp, idesc, (uint32_t)CBp, 1);
+                            mma_block(dtm, a0, b0, kb, 1, CBp, idesc, (uint32_t)CBp, 1);
+                            mma_block(dtm, a0, b0, kb, 1, 0, idesc, (uint32_t)CBp, 1);
+                        } else {
+                            // (D term, u term) of pass p: lh, hl, mm, mh, hm, hh
                             const int bt = p == 0 ? 2 : (p == 2 || p == 3) ? 1 : 0;
                             const int at = p == 1 ? 2 : (p == 2 || p == 4) ? 1 : 0;
-                            mma_block(at, bt * CBp, idesc, 0, p == 0 ? acc : 1u);
+                            mma_block(dtm, a0, b0, kb, at, bt * CBp, idesc, 0, p == 0 ? acc : 1u);
                         }
+                        if (p == npass - 1)
+                            tc_commit(&a_empty[ab * kTcMaxKB + kb]);
                     }
-                    tc_commit(&a_empty[ab * kTcMaxKB + kb]);
+                    __syncwarp();
                 }
-                __syncwarp();
             }
             if (!ok) {
                 if (lane == 0)

@@ -160,8 +160,8 @@ def test_variant_plan_reports_the_resolved_launch(lib):
     p = lc.variant_plan(k, 1 << 21, 35, 3, v)
     assert p["tiles"] == (1 << 21) // 128 and p["column_blocks"] == 1 and p["ops_per_block"] == 3
     assert p["k_mma"] == 48 and p["k_block"] == 64
-    # N = 35 pads to 40 columns per operator so that the D terms stack: 4 MMAs per K step
-    assert p["cols_per_op"] == 40 and p["mma_n"] == 128 and p["stacked"] == 1 and p["mma_per_tile"] == 12
+    # N = 35 pads to 40 columns per operator so that the D terms stack: 5 MMAs per K step
+    assert p["cols_per_op"] == 40 and p["mma_n"] == 128 and p["stacked"] == 1 and p["mma_per_tile"] == 15
     assert p["threads"] == 128 * (4 + 2) + 64 and p["store_rows"] == 128
     assert 0 < p["smem_bytes"] <= 232448
     s = lc.variant_plan(k, 1 << 21, 35, 3, lc.variant_default(k, 1 << 21, 35, 3, "elem", "fp32"))
