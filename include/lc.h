@@ -196,12 +196,20 @@ lc_status lc_contract(const lc_kernel *k, const lc_variant *v, const void *D_dev
                       void *stream);
 
 /*
- * The contraction on host arrays: copies D and u from host to the caller's
- * device buffers, enqueues lc_contract, and copies out back to the host, all in
- * order on `stream` (asynchronous with respect to the host when the host
- * buffers are page-locked; synchronise the stream before reading out_host).
+ * The contraction on host arrays: copies D and u from host to the caller's device
+ * buffers, contracts, and copies out back to the host.  Large batches are cut into up to
+ * 8 element chunks (whole tiles, >= 2^16 elements each) whose copies in, contractions
+ * and copies out overlap: the copies run on two library-owned streams (one per
+ * direction and device, created on first use and kept until exit), the contractions on `stream`,
+ * ordered by events; all of it starts after the work already queued on `stream`, and
+ * `stream` resumes after the last copy out.  Asynchronous with respect to the host when
+ * the host buffers are page-locked; synchronise `stream` before reading out_host.  Not
+ * for use inside a stream capture.
  *   D_host, u_host, out_host   host arrays with the layouts of lc_contract
- *   D_dev, u_dev, out_dev      device buffers of the same sizes (caller-owned)
+ *   D_dev, u_dev, out_dev      device scratch of the same sizes (caller-owned); each chunk
+ *                              packs its u and out at its element offset, so after the
+ *                              call u_dev and out_dev hold chunk-packed data, not the
+ *                              lc_contract layout (the same as it when there is one chunk)
  * Errors: as lc_contract, plus LC_ERR_CUDA for a failed copy.
  */
 lc_status lc_contract_host(const lc_kernel *k, const lc_variant *v, const void *D_host,

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cctype>
 #include <cmath>
+#include <array>
 #include <map>
 #include <mutex>
 #include <set>
@@ -1284,6 +1285,39 @@ lc_status lc_contract(const lc_kernel *kh, const lc_variant *v, const void *D, c
     return LC_ERR_INVALID_VARIANT;
 }
 
+namespace lc {
+
+// Copy streams of the host-array entry point, one per direction and device, created on
+// first use and kept for the life of the process.  (A second stream per direction, with
+// chunks alternating, measured no faster: the host link, not one copy engine, is the limit.)
+static constexpr int kCopyStreams = 2;  // in, out
+static std::mutex g_copy_mu;
+static std::map<int, std::array<cudaStream_t, kCopyStreams>> g_copy_streams;
+
+static lc_status copy_streams(cudaStream_t *cs)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    std::lock_guard<std::mutex> lk(g_copy_mu);
+    auto it = g_copy_streams.find(dev);
+    if (it == g_copy_streams.end()) {
+        std::array<cudaStream_t, kCopyStreams> a{};
+        for (auto &x : a)
+            if (e == cudaSuccess)
+                e = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking);
+        if (e != cudaSuccess)
+            return cuda_fail(e);
+        it = g_copy_streams.emplace(dev, a).first;
+    }
+    for (int i = 0; i < kCopyStreams; ++i)
+        cs[i] = it->second[i];
+    return LC_OK;
+}
+
+}  // namespace lc
+
 lc_status lc_contract_host(const lc_kernel *kh, const lc_variant *v, const void *D_host, const void *u_host,
                            void *out_host, int64_t E, int32_t N, int32_t F, void *D_dev, void *u_dev,
                            void *out_dev, void *stream)
@@ -1296,19 +1330,106 @@ lc_status lc_contract_host(const lc_kernel *kh, const lc_variant *v, const void 
     lc_status st = resolve(kh->k, E, N, F, v, r, true);
     if (st != LC_OK)
         return st;
+    if (E == 0)
+        return LC_OK;
     const size_t es = v->precision == LC_PREC_FP64 ? 8 : 4;
+    const bool node = v->layout == LC_LAYOUT_NODE_MAJOR;
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaMemcpyAsync(D_dev, D_host, (size_t)F * N * N * es, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(u_dev, u_host, (size_t)E * N * es, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess)
-        return cuda_fail(e);
-    st = lc_contract(kh, v, D_dev, u_dev, out_dev, E, N, F, stream);
+
+    // Element chunks (whole 128-element tiles, at least 2^16 elements, at most 8): the
+    // copy of chunk c+1 in, the contraction of chunk c and the copy of chunk c-1 out run
+    // at the same time (two copy streams and the caller's stream, ordered by events).
+    // Each chunk's u and out are packed in the caller's device buffers at its element
+    // offset, so chunks never share device memory.
+    long long chunk = E;
+    int nchunks = 1;
+    {
+        const long long want = std::min<long long>(8, E >> 16);
+        if (want > 1) {
+            const long long c = ((E + want - 1) / want + 127) / 128 * 128;
+            Resolved r1, r2;
+            const long long last = E - (long long)((E - 1) / c) * c;
+            if (resolve(kh->k, c, N, F, v, r1, true) == LC_OK && resolve(kh->k, last, N, F, v, r2, true) == LC_OK) {
+                chunk = c;
+                nchunks = (int)((E + c - 1) / c);
+            }
+        }
+    }
+    cudaStream_t cs[lc::kCopyStreams];
+    st = lc::copy_streams(cs);
     if (st != LC_OK)
         return st;
-    e = cudaMemcpyAsync(out_host, out_dev, (size_t)F * E * N * es, cudaMemcpyDeviceToHost, s);
+    std::vector<cudaEvent_t> ev(2 * (size_t)nchunks + 2, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (auto &x : ev)
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+    auto cleanup = [&]() {
+        for (auto &x : ev)
+            if (x)
+                cudaEventDestroy(x);  // released once the recorded work completes
+    };
+    auto fail = [&](cudaError_t err) {
+        cleanup();
+        return lc::cuda_fail(err);
+    };
     if (e != cudaSuccess)
-        return cuda_fail(e);
+        return fail(e);
+    cudaEvent_t ev_start = ev[2 * nchunks], ev_done = ev[2 * nchunks + 1];
+    // nothing starts before the work already queued on the caller's stream
+    e = cudaEventRecord(ev_start, s);
+    for (int i = 0; i < lc::kCopyStreams; ++i)
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(cs[i], ev_start, 0);
+    if (e == cudaSuccess)  // before chunk 0's input on the same stream; every contraction follows chunk 0's
+        e = cudaMemcpyAsync(D_dev, D_host, (size_t)F * N * N * es, cudaMemcpyHostToDevice, cs[0]);
+    if (e != cudaSuccess)
+        return fail(e);
+    const char *uh = static_cast<const char *>(u_host);
+    char *ud = static_cast<char *>(u_dev), *oh = static_cast<char *>(out_host), *od = static_cast<char *>(out_dev);
+    for (int c = 0; c < nchunks; ++c) {
+        const long long e0 = (long long)c * chunk, ec = std::min(chunk, E - e0);
+        char *u_c = ud + (size_t)e0 * N * es;      // packed chunk input  (elem: [ec][N], node: [N][ec])
+        char *o_c = od + (size_t)e0 * F * N * es;  // packed chunk output (elem: [F][ec][N], node: [F][N][ec])
+        cudaEvent_t ev_in = ev[2 * c], ev_comp = ev[2 * c + 1];
+        cudaStream_t s_in = cs[0], s_out = cs[1];
+        if (node)
+            e = cudaMemcpy2DAsync(u_c, (size_t)ec * es, uh + (size_t)e0 * es, (size_t)E * es, (size_t)ec * es, N,
+                                  cudaMemcpyHostToDevice, s_in);
+        else
+            e = cudaMemcpyAsync(u_c, uh + (size_t)e0 * N * es, (size_t)ec * N * es, cudaMemcpyHostToDevice, s_in);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(ev_in, s_in);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(s, ev_in, 0);
+        if (e != cudaSuccess)
+            return fail(e);
+        st = lc_contract(kh, v, D_dev, u_c, o_c, ec, N, F, stream);
+        if (st != LC_OK) {
+            cleanup();
+            return st;
+        }
+        e = cudaEventRecord(ev_comp, s);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(s_out, ev_comp, 0);
+        if (e == cudaSuccess) {
+            if (node)  // F*N rows of ec values
+                e = cudaMemcpy2DAsync(oh + (size_t)e0 * es, (size_t)E * es, o_c, (size_t)ec * es, (size_t)ec * es,
+                                      (size_t)F * N, cudaMemcpyDeviceToHost, s_out);
+            else  // F rows of ec*N values
+                e = cudaMemcpy2DAsync(oh + (size_t)e0 * N * es, (size_t)E * N * es, o_c, (size_t)ec * N * es,
+                                      (size_t)ec * N * es, F, cudaMemcpyDeviceToHost, s_out);
+        }
+        if (e != cudaSuccess)
+            return fail(e);
+    }
+    // the caller's stream resumes after the last copy out
+    e = cudaEventRecord(ev_done, cs[1]);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(s, ev_done, 0);
+    if (e != cudaSuccess)
+        return fail(e);
+    cleanup();
     return LC_OK;
 }
 
