@@ -154,3 +154,23 @@ def test_store_groups_and_slots(lc, prec):
                 assert np.array_equal(got, ref), (E, N, F, rows, ob)
                 ran += 1
         assert ran >= 3, (E, N, F, ran)
+
+
+@pytest.mark.parametrize("E,N,F,layout,prec,kbw", [
+    (1000, 165, 1, "node", "bf16", 16),   # 11 K-blocks handed over one by one
+    (1000, 165, 2, "node", "bf16", 32),   # two column blocks, a ragged last K-block
+    (777, 120, 2, "elem", "bf16", 16),    # 8 K-blocks, element-major staging
+    (333, 100, 1, "node", "bf16x3", 16),  # stacked terms, 7 K-blocks
+    (500, 64, 4, "elem", "bf16x3", 16),   # unstacked (MMA N = 256), products outermost over 4 K-blocks
+    (500, 64, 4, "node", "bf16x3", 64),
+])
+def test_large_n_k_blocks_bit_exact(lc, E, N, F, layout, prec, kbw):
+    """Integer-valued inputs at large N: every K-block handover, both MMA orders, exact."""
+    kernel = lc.Kernel()
+    D, u = synth.integer_operands(E, N, F, seed=N + F)
+    uu = synth.to_node_major(u) if layout == "node" else u
+    v = lc.Variant(engine="tcgen05", layout=layout, precision=prec, tile_e=128, elems_per_thread=kbw, split_i=0,
+                   unroll=2, prefetch_smem=1, stages=1)
+    assert lc.variant_validate(kernel, E, N, F, v) == 0
+    got = run(lc, kernel, v, D, uu, layout)
+    assert np.array_equal(got, oracle.contract(D, uu, layout)), (E, N, F, layout, prec, kbw)
