@@ -48,6 +48,8 @@ WORKLOADS = {
                          "CUDA graph"),
 }
 
+L2_BYTES = 129 * 1000 * 1000  # GB300 L2
+
 # FP32 SIMT descriptors tried for the grouped launch: (elems_per_thread, split_i, unroll,
 # prefetch_smem, stages, ctas_per_sm)
 GROUPED_CANDIDATES = [(8, 4, 4, 1, 2, 2), (4, 8, 4, 1, 2, 2), (8, 8, 1, 1, 1, 1), (8, 4, 4, 1, 1, 3),
@@ -56,7 +58,14 @@ GROUPED_CANDIDATES = [(8, 4, 4, 1, 2, 2), (4, 8, 4, 1, 2, 2), (8, 8, 1, 1, 1, 1)
 # DRAM bytes per launch from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum),
 # keyed by (workload, layout, precision, engine); valid only while the kernel sources hash
 # to `src`.  `variant` records the descriptor the capture ran.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # full size (E = 2^21), profiles/tc_contract_bf16x3_elem_N35_F3.md: 293.70 MB read +
+    # 818.55 MB written (the remaining 62 MB of output was still in L2 when the kernel ended)
+    ("fp32_three", "elem", "bf16x3", "tcgen05"): {
+        "bytes": 293698048 + 818553088, "src": "be85d7c90436d2f7",
+        "variant": {"tile_e": 128, "elems_per_thread": 64, "split_i": 0, "unroll": 4, "stages": 1,
+                    "store_rows": 128}},
+}
 
 
 def csrc_hash() -> str:
@@ -283,6 +292,7 @@ def main():
     v, n_tuned = choose_variant(lc, kernel, wl, args.layout, args.variant, Dd, ud, out, stream)
     vd = lc.variant_dict(v)
     flops = 2.0 * E * N * N * F
+    step_bytes = (8 if wl["precision"] == "fp64" else 4) * (E * N * (1 + F) + F * N * N)
 
     def step():
         lc.check(lc.lc_contract(kernel, v, Dd.data_ptr(), ud.data_ptr(), out.data_ptr(), E, N, F,
@@ -404,8 +414,8 @@ def main():
                        "precision": wl["precision"], "variant": vd,
                        "variant_choice": f"autotuned over {n_tuned} candidates" if n_tuned else args.variant,
                        "parallelism": f"replicas x{world}",
-                       "l2": ("inputs+outputs larger than L2 (no flush needed)" if not use_graph else
-                              "inputs+outputs fit in L2 (1.3 MB); L2-resident by design of this small case"),
+                       "l2": ("inputs+outputs larger than L2 (no flush needed)" if step_bytes > L2_BYTES else
+                              f"inputs+outputs ({step_bytes / 1e6:.1f} MB) fit in L2: L2-resident small case"),
                        "timing": (f"one CUDA graph of {args.steps} back-to-back steps, device time / steps"
                                   if use_graph else "CUDA events around every step on the launching stream"),
                        "bytes_per_step": (8 if wl["precision"] == "fp64" else 4) * (E * N * (1 + F) + F * N * N)},
