@@ -181,9 +181,8 @@ def roofline_for(v, wl, peaks, sms, t_launch_s, workload_key):
                 "frac": ach / peaks["hbm_gbs"], "traffic": traffic, "peak_source": peaks["source"],
                 "tensor_frac": (tflops / t_launch_s / 1e12) / peaks["bf16_tflops"]}
     else:
-        # FP32: 128 FMA lanes per SM; FP64: 4 per SM (one per sub-partition; the nominal
-        # 1.25 TFLOP/s, i.e. 2 per SM, is exceeded by the measured 1.5 TFLOP/s of this kernel)
-        lanes = 128 if es == 4 else 4
+        # FP32: 128 FMA lanes per SM; FP64: 2 per SM (the part's nominal 1.25 TFLOP/s FP64)
+        lanes = 128 if es == 4 else 2
         alu_peak = sms * lanes * 2 * peaks["sm_max_mhz"] * 1e6
     t_alu = flops / alu_peak if alu_peak else 0.0
     if t_alu > t_hbm:
@@ -326,12 +325,13 @@ def main():
         e_b.record(stream)
     torch.cuda.synchronize()
     use_graph = e_a.elapsed_time(e_b) / 8 < 0.1
-    graph = flush_graph = None
+    graph = flush_graph = resident_graph = None
+    resident_ms = None
     if use_graph:
         # every step preceded by a write of a scratch buffer larger than L2; the flushes
         # alone are timed in a second graph and subtracted
         scratch = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
-        graph, flush_graph = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+        graph, flush_graph, resident_graph = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=stream):
             for _ in range(args.steps):
                 scratch.zero_()
@@ -339,8 +339,13 @@ def main():
         with torch.cuda.graph(flush_graph, stream=stream):
             for _ in range(args.steps):
                 scratch.zero_()
-        graph.replay()
-        flush_graph.replay()
+        with torch.cuda.graph(resident_graph, stream=stream):  # the steps alone, L2 warm
+            for _ in range(args.steps):
+                step()
+        with torch.cuda.stream(stream):  # a graph replays on the current stream
+            graph.replay()
+            flush_graph.replay()
+            resident_graph.replay()
         torch.cuda.synchronize()
 
     clocks = ClockSampler(local_rank)
@@ -351,13 +356,19 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     if use_graph:
-        starts[0].record(stream)
-        graph.replay()
-        ends[-1].record(stream)
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        flush_graph.replay()
-        f1.record(stream)
+        # the flushes dwarf the steps: seven interleaved replays of each graph, medians
+        with_steps, flushes_only, resident = [], [], []
+        for rep in range(7):
+            for g, acc in ((graph, with_steps), (flush_graph, flushes_only), (resident_graph, resident)):
+                a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(stream):  # a graph replays on the current stream
+                    a_.record(stream)
+                    g.replay()
+                    b_.record(stream)
+                if g is graph and rep == 0:
+                    starts[0], ends[-1] = a_, b_
+                b_.synchronize()
+                acc.append(a_.elapsed_time(b_))
     else:
         for k in range(args.steps):
             starts[k].record(stream)
@@ -369,7 +380,8 @@ def main():
     clk = clocks.stop()
     total_ms = starts[0].elapsed_time(ends[-1])
     if use_graph:
-        total_ms = max(total_ms - f0.elapsed_time(f1), 1e-6)
+        total_ms = max(statistics.median(with_steps) - statistics.median(flushes_only), 1e-6)
+        resident_ms = statistics.median(resident) / args.steps
         per_launch_ms = [total_ms / args.steps]
     else:
         per_launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
@@ -439,8 +451,9 @@ def main():
                        "parallelism": f"replicas x{world}",
                        "l2": ("inputs+outputs larger than L2 (no flush needed)" if step_bytes > L2_BYTES and not use_graph
                               else "L2 flushed before every step (a 258 MB scratch write; flush time subtracted)"),
-                       "timing": (f"one CUDA graph of {args.steps} (flush, step) pairs minus a graph of the "
-                                  f"{args.steps} flushes alone, / steps" if use_graph else
+                       "timing": (f"median of 7 replays of a CUDA graph of {args.steps} (flush, step) pairs minus "
+                                  f"the median of 7 replays of the {args.steps} flushes alone, / steps; the same steps "
+                                  f"back to back with L2 warm: {resident_ms * 1e3:.2f} us each" if use_graph else
                                   "CUDA events around every step on the launching stream"),
                        "bytes_per_step": (8 if wl["precision"] == "fp64" else 4) * (E * N * (1 + F) + F * N * N)},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,

@@ -875,7 +875,9 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
     if (v->engine == LC_ENGINE_WARP) {
         if (v->precision != LC_PREC_FP32 && v->precision != LC_PREC_FP64)
             return LC_ERR_INVALID_VARIANT;
-        if (N > (v->precision == LC_PREC_FP64 ? 16 : 32) || F > 4)
+        // registers hold F x N coefficients: FP32 N <= 32 (F <= 4); FP64 N <= 16 (F <= 4) or
+        // N <= 32 with one operator
+        if (N > 32 || F > 4 || (v->precision == LC_PREC_FP64 && N > 16 && F > 1))
             return LC_ERR_INVALID_VARIANT;
         const int per = 32 / N;
         if (v->tile_e <= 0 || v->tile_e % per != 0 || v->tile_e / per > 16)

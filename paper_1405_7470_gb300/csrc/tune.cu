@@ -11,7 +11,7 @@
 
 namespace lc {
 
-static std::vector<lc_variant> candidates(int N, int layout, int precision)
+static std::vector<lc_variant> candidates(int N, int F, int layout, int precision)
 {
     std::vector<lc_variant> out;
     lc_variant b;
@@ -38,7 +38,7 @@ static std::vector<lc_variant> candidates(int N, int layout, int precision)
                         v.ctas_per_sm = 2;
                         out.push_back(v);
                     }
-        if (N <= (precision == LC_PREC_FP64 ? 16 : 32)) {
+        if (N <= 32 && (precision != LC_PREC_FP64 || N <= 16 || F == 1)) {
             for (int warps : {4, 8}) {
                 lc_variant v = b;
                 v.engine = LC_ENGINE_WARP;
@@ -86,7 +86,7 @@ lc_status lc_enumerate_variants(const lc_kernel *k, int64_t E, int32_t N, int32_
 {
     if (!k || !count || cap < 0 || (cap > 0 && !out))
         return LC_ERR_INVALID_ARGUMENT;
-    std::vector<lc_variant> cand = candidates(N, layout, precision);
+    std::vector<lc_variant> cand = candidates(N, F, layout, precision);
     if (precision == LC_PREC_BF16 || precision == LC_PREC_BF16X3) {
         // when no tensor-core plan fits (large N), the FP32 SIMT variants serve the request:
         // their error is below both reduced-precision bounds
@@ -94,7 +94,7 @@ lc_status lc_enumerate_variants(const lc_kernel *k, int64_t E, int32_t N, int32_
         for (const lc_variant &v : cand)
             any = any || lc_variant_validate(k, E, N, F, &v) == LC_OK;
         if (!any)
-            cand = candidates(N, layout, LC_PREC_FP32);
+            cand = candidates(N, F, layout, LC_PREC_FP32);
     }
     int n = 0;
     for (const lc_variant &v : cand) {

@@ -68,7 +68,11 @@ static void *warp_pick(int N)
         return reinterpret_cast<void *>(&warp_contract_kernel<T, 8, 4, NODE>);
     if (N <= 16)
         return reinterpret_cast<void *>(&warp_contract_kernel<T, 16, 4, NODE>);
-    return reinterpret_cast<void *>(&warp_contract_kernel<T, 32, 4, NODE>);
+    // FP64 above 16 nodes: one operator's row in registers (the planner admits F = 1 only)
+    if constexpr (sizeof(T) == 8)
+        return reinterpret_cast<void *>(&warp_contract_kernel<T, 32, 1, NODE>);
+    else
+        return reinterpret_cast<void *>(&warp_contract_kernel<T, 32, 4, NODE>);
 }
 
 lc_status warp_launch(const WarpArgs &a, int layout, int fp64, int grid, int threads, cudaStream_t s)

@@ -133,6 +133,25 @@ def test_warp_engine_small_n(lc, layout):
         assert np.array_equal(got.astype(np.float64), oracle.contract(Di, uui, layout))
 
 
+@pytest.mark.parametrize("layout", ["elem", "node"])
+def test_warp_engine_fp64_single_operator(lc, layout):
+    """FP64 warp engine above 16 nodes (one operator's row in registers): N = 20 (the FP64
+    workload's size, one element per warp, 12 lanes idle) and N = 32."""
+    kernel = lc.Kernel("{ [e,i,j]: 0<=e<E and 0<=i,j<N }", "out[e,i] = sum(j, D[i,j]*u[e,j])")
+    for E, N in [(4096, 20), (777, 20), (130, 32)]:
+        D, u = synth.operands(E, N, 1, np.float64, seed=N + E)
+        uu = synth.to_node_major(u) if layout == "node" else u
+        for warps in (1, 8):
+            v = lc.Variant(engine="warp", layout=layout, precision="fp64", tile_e=(32 // N) * warps,
+                           elems_per_thread=1, split_i=1, unroll=1, prefetch_smem=0)
+            assert lc.variant_validate(kernel, E, N, 1, v) == 0
+            check(run(lc, kernel, v, D, uu, layout), D, uu, layout, True)
+    # two operators above 16 nodes do not fit the registers: rejected before launch
+    v = lc.Variant(engine="warp", layout=layout, precision="fp64", tile_e=8, elems_per_thread=1, split_i=1,
+                   unroll=1, prefetch_smem=0)
+    assert lc.variant_validate(lc.Kernel(), 100, 20, 2, v) != 0
+
+
 def test_tail_free_under_assumption(lc):
     kernel = lc.Kernel(assumptions="E mod 128 = 0")
     D, u = synth.operands(1024, 35, 3, np.float32, seed=9)
