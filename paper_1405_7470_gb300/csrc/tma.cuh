@@ -109,9 +109,6 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 // Wait until the source shared memory of all committed bulk stores has been read.
 __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 
-// Wait until at most one committed bulk-store group may still be reading shared memory.
-__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
-
 // Wait until at most n (0..3) committed bulk-store groups may still be reading shared memory.
 __device__ __forceinline__ void bulk_wait_read(int n)
 {
