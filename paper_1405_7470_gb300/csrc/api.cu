@@ -1484,7 +1484,10 @@ static lc_status grouped_plan_host(const Kernel &K, const lc_variant *v, const l
         if (!aligned16(G.D_dev) || !aligned16(G.u_dev) || !aligned16(G.out_dev))
             return LC_ERR_MISALIGNED;
         // tile of TE = EG * RE elements within T threads: the most active threads, then the
-        // fewest padded columns, then the largest tile (fewer, longer bulk copies per tile)
+        // fewest padded columns, then the largest tile (fewer, longer bulk copies per tile).
+        // Node-major also counts column blocks: each one reads the u tile again with plain
+        // loads (the bulk engine needs 16-byte aligned rows of u), which costs more than
+        // idle threads do.
         Resolved best;
         double best_key = 0;
         bool have = false;
@@ -1497,7 +1500,9 @@ static lc_status grouped_plan_host(const Kernel &K, const lc_variant *v, const l
                 continue;
             const double idle = (double)(T - r.g.threads) / T;
             const double pad = (double)(r.g.nchunks * (long long)r.g.CW) / ((double)G.F * G.N) - 1.0;
-            const double key = idle * 4.0 + pad - 0.05 * std::log2((double)vg.tile_e);
+            const bool nodel = v->layout == LC_LAYOUT_NODE_MAJOR;
+            const double key = idle * (nodel ? 0.25 : 4.0) + pad + (nodel ? 0.5 * (r.g.nchunks - 1) : 0.0) -
+                               0.05 * std::log2((double)vg.tile_e);
             if (!have || key < best_key) {
                 best_key = key;
                 best = r;
