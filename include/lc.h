@@ -204,7 +204,8 @@ lc_status lc_contract(const lc_kernel *k, const lc_variant *v, const void *D_dev
  * ordered by events; all of it starts after the work already queued on `stream`, and
  * `stream` resumes after the last copy out.  Asynchronous with respect to the host when
  * the host buffers are page-locked; synchronise `stream` before reading out_host.  Not
- * for use inside a stream capture.
+ * for use inside a stream capture.  Calls on one device share the two copy streams: calls
+ * from several threads stay correct, their copies take turns.
  *   D_host, u_host, out_host   host arrays with the layouts of lc_contract
  *   D_dev, u_dev, out_dev      device scratch of the same sizes (caller-owned); each chunk
  *                              packs its u and out at its element offset, so after the
