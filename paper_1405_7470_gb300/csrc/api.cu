@@ -839,10 +839,10 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
             return LC_ERR_INVALID_VARIANT;
         // Shared-memory plan, in order of preference: the most operators per CTA (fewer
         // column blocks re-reading the same u tile), then at least two output staging
-        // slots (bulk stores of one operator overlap the staging of the next), then two A
+        // slots (the bulk stores of one slot overlap the staging of the next), then two A
         // buffers (conversion of tile k+1 overlaps the MMAs of tile k), then more slots.
-        static const int combos[8][2] = {{3, 2}, {2, 2}, {4, 1}, {3, 1}, {2, 1}, {1, 2}, {1, 1}};  // {slots, abufs}
-        const int ncombos = 7;
+        static const int combos[][2] = {{3, 2}, {2, 2}, {4, 1}, {3, 1}, {2, 1}, {1, 2}, {1, 1}};  // {slots, abufs}
+        const int ncombos = (int)(sizeof combos / sizeof combos[0]);
         bool found = false;
         const int g_hi = v->split_i ? v->split_i : F, g_lo = v->split_i ? v->split_i : 1;
         for (int g = g_hi; g >= g_lo && !found; --g)

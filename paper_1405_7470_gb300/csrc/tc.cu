@@ -1,8 +1,9 @@
 // Tensor-core (tcgen05 / TMEM) kernel for the element-local contraction
 //     out[f,e,i] = sum_j D[f,i,j] * u[e,j]                (dG FEM volume, Table 1)
 // as a GEMM per tile of 128 elements: A = u tile [128 x K] (K = nodes j, padded to a
-// multiple of 16), B = D^T columns [CB x K] (c = f*N + i for the G operators of this
-// CTA's column block), accumulator [128 x CB] FP32 in tensor memory.
+// multiple of 16), B = D^T columns [CB x K] (c = f*Np + i for the G operators of this
+// CTA's column block, each padded to Np columns), accumulator [128 x CB] FP32 in tensor
+// memory.  Operands live in K-blocks of 16, 32 or 64 bf16 per row (32/64/128-byte swizzle).
 //
 // Precision paths (FP32 accumulation in both):
 //   BF16    operands rounded to bfloat16 (nearest-even), one product.
@@ -16,14 +17,18 @@
 //   producer warp  the bulk-copy engine fetches u tiles (fp32) into a ring of
 //                  `stages` shared-memory buffers;
 //   MMA warp       one lane issues the tcgen05.mma chain of tile k into TMEM
-//                  accumulator k % 2 (two accumulators), then commits to the
-//                  A-buffer-empty and accumulator-full barriers;
+//                  accumulator k % 2 (two accumulators), K-block by K-block,
+//                  committing each block of the A buffer back as it is done, then the
+//                  accumulator to the epilogue;
 //   4*Hc converters convert the fp32 tile into the bf16 A-operand terms (K-major,
-//                  hardware swizzle layout; Hc threads share a tile row's K chunks);
+//                  hardware swizzle layout; Hc threads share a tile row's K chunks),
+//                  K-block by K-block;
 //   4*He epilogue  drain the accumulator of a finished tile (tcgen05.ld; the He warps
 //                  of a TMEM lane quarter split its columns) and store it: element-
-//                  major through shared memory and one bulk store per operator,
-//                  node-major straight from registers (coalesced along e).
+//                  major through shared-memory slots and bulk stores (every operator
+//                  of the tile per slot, or one operator per slot in store groups of
+//                  lane quarters), node-major straight from registers (coalesced
+//                  along e).
 // Setup: the MMA warp allocates the accumulators; all threads split D into the
 // B-operand terms, resident for the CTA's lifetime.
 // Every mbarrier wait is bounded in time; on a timeout the kernel sets the device
