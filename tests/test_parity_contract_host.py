@@ -29,25 +29,28 @@ CASES = [
     ((1 << 18) + 77, 35, 3, "node", "bf16x3"),
     ((1 << 19) + 128, 20, 2, "elem", "fp32"),   # eight chunks, SIMT engine
     ((1 << 17) + 5, 84, 4, "node", "bf16"),
+    ((1 << 18) + 3, 20, 1, "elem", "fp64"),   # FP64 storage (8-byte elements), four chunks
+    ((1 << 18) + 3, 20, 1, "node", "fp64"),
 ]
 
 
 @pytest.mark.parametrize("E,N,F,layout,prec", CASES)
 def test_host_entry_matches_device_entry(lc, E, N, F, layout, prec):
     import torch
-    D, u = synth.operands(E, N, F, np.float32, seed=E % 1000 + N)
+    dtype = np.float64 if prec == "fp64" else np.float32
+    D, u = synth.operands(E, N, F, dtype, seed=E % 1000 + N)
     uu = np.ascontiguousarray(synth.to_node_major(u) if layout == "node" else u)
-    kernel = lc.Kernel()
+    kernel = lc.Kernel() if F > 1 else lc.Kernel("{ [e,i,j]: 0<=e<E and 0<=i,j<N }", "out[e,i] = sum(j, D[i,j]*u[e,j])")
     v = lc.variant_default(kernel, E, N, F, layout, prec)
     shape = (F, N, E) if layout == "node" else (F, E, N)
     Dd, ud = torch.from_numpy(D).cuda(), torch.from_numpy(uu).cuda()
-    want = lc.contract(kernel, v, Dd, ud, torch.empty(shape, device="cuda"))
+    want = lc.contract(kernel, v, Dd, ud, torch.empty(shape, dtype=Dd.dtype, device="cuda"))
     torch.cuda.synchronize()
     want = want.cpu().numpy()
 
     Dh, uh = torch.from_numpy(D).pin_memory(), torch.from_numpy(uu).pin_memory()
-    oh = torch.full(shape, float("nan")).pin_memory()
-    D2, u2, o2 = torch.empty_like(Dd), torch.empty_like(ud), torch.empty(shape, device="cuda")
+    oh = torch.full(shape, float("nan"), dtype=Dd.dtype).pin_memory()
+    D2, u2, o2 = torch.empty_like(Dd), torch.empty_like(ud), torch.empty(shape, dtype=Dd.dtype, device="cuda")
     stream = torch.cuda.Stream()
     lc.contract_host(kernel, v, Dh, uh, oh, D2, u2, o2, stream=stream)
     stream.synchronize()
@@ -58,7 +61,7 @@ def test_host_entry_matches_device_entry(lc, E, N, F, layout, prec):
     rows = np.unique(np.concatenate([np.arange(64), np.random.default_rng(0).integers(0, E, 500), [E - 1]]))
     ref = oracle.contract_rows(D, u, rows)
     sub = got[:, :, rows].transpose(0, 2, 1) if layout == "node" else got[:, rows, :]
-    tol = {"bf16": 1e-2, "bf16x3": 1e-6, "fp32": 1e-6}[prec]
+    tol = {"bf16": 1e-2, "bf16x3": 1e-6, "fp32": 1e-6, "fp64": 1e-13}[prec]
     assert oracle.rel_fro_error(sub, ref) <= tol
 
 
