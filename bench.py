@@ -52,8 +52,8 @@ L2_BYTES = 129 * 1000 * 1000  # GB300 L2
 
 # FP32 SIMT descriptors tried for the grouped launch: (elems_per_thread, split_i, unroll,
 # prefetch_smem, stages, ctas_per_sm)
-GROUPED_CANDIDATES = [(8, 4, 4, 1, 2, 2), (4, 8, 4, 1, 2, 2), (8, 8, 1, 1, 1, 1), (8, 4, 4, 1, 1, 3),
-                      (8, 8, 1, 1, 2, 1)]
+GROUPED_CANDIDATES = [(8, 8, 4, 1, 2, 3), (4, 8, 4, 1, 2, 3), (4, 8, 4, 1, 1, 3), (8, 4, 4, 1, 2, 2),
+                      (4, 8, 4, 1, 2, 2), (8, 8, 4, 1, 2, 1), (8, 8, 1, 1, 1, 1)]
 
 # sources that decide a tensor-core launch: the kernel, its helpers, the planner
 TC_SOURCES = ("tc.cu", "tma.cuh", "lc_internal.h", "api.cu")
