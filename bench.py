@@ -25,6 +25,7 @@ import os
 import shutil
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -110,9 +111,8 @@ class ClockSampler:
         exe = shutil.which("nvidia-smi")
         if not exe:
             return
-        os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
-        self.fh = open(self.path, "w")
+        fd, self.path = tempfile.mkstemp(prefix="lc_clocks_", suffix=".csv")
+        self.fh = os.fdopen(fd, "w")
         self.proc = subprocess.Popen([exe, f"--id={self.index}", f"--query-gpu={self.Q}",
                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                      stdout=self.fh, stderr=subprocess.DEVNULL)
@@ -129,24 +129,74 @@ class ClockSampler:
             self.proc.kill()
         self.fh.close()
         sms, maxs, reasons = [], [], set()
+        lines = open(self.path).read().splitlines()
+        os.unlink(self.path)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        with open(self.path) as fh:
-            for line in fh:
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) < 9:
-                    continue
-                try:
-                    sms.append(float(parts[1]))
-                    maxs.append(float(parts[2]))
-                except ValueError:
-                    continue
-                for n, p in zip(names, parts[5:9]):
-                    if p.lower() == "active":
-                        reasons.add(n)
+        for line in lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                maxs.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, p in zip(names, parts[5:9]):
+                if p.lower() == "active":
+                    reasons.add(n)
         if not sms:
             return None
         return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxs), "reasons": sorted(reasons),
                 "samples": len(sms)}
+
+
+def numa_report(dev_index: int, tensors) -> dict:
+    """Where the end-to-end path's pinned host buffers live: the GPU's NUMA node (sysfs, by
+    its PCI address), the nodes of the CPUs this process may run on, and the pages of each
+    buffer per node (/proc/self/numa_maps).  Values that cannot be read are null."""
+    rep = {"gpu_numa_node": None, "cpu_nodes": None, "pinned_pages_by_node": None}
+    try:
+        exe = shutil.which("nvidia-smi")
+        if exe:
+            bus = subprocess.run([exe, f"--id={dev_index}", "--query-gpu=pci.bus_id", "--format=csv,noheader"],
+                                 capture_output=True, text=True, timeout=20).stdout.strip().lower()
+            dom, rest = bus.split(":", 1)
+            path = f"/sys/bus/pci/devices/{int(dom, 16):04x}:{rest}/numa_node"
+            if os.path.exists(path):
+                rep["gpu_numa_node"] = int(open(path).read().strip())
+    except (OSError, ValueError, subprocess.SubprocessError):
+        pass
+    try:
+        nodes = set()
+        for cpu in sorted(os.sched_getaffinity(0)):
+            d = f"/sys/devices/system/cpu/cpu{cpu}"
+            for name in os.listdir(d):
+                if name.startswith("node") and name[4:].isdigit():
+                    nodes.add(int(name[4:]))
+        rep["cpu_nodes"] = sorted(nodes)
+    except OSError:
+        pass
+    try:
+        regions = []
+        for line in open("/proc/self/maps"):
+            lo, hi = line.split()[0].split("-")
+            regions.append((int(lo, 16), int(hi, 16)))
+        numa = {}
+        for line in open("/proc/self/numa_maps"):
+            parts = line.split()
+            numa[int(parts[0], 16)] = {k: int(v) for k, v in (p.split("=") for p in parts[2:] if p[:1] == "N" and "=" in p)}
+        pages = {}
+        for t in tensors:
+            ptr = t.data_ptr()
+            for lo, hi in regions:
+                if lo <= ptr < hi:
+                    for k, v in numa.get(lo, {}).items():
+                        pages[k] = pages.get(k, 0) + v
+                    break
+        rep["pinned_pages_by_node"] = pages or None
+    except (OSError, ValueError):
+        pass
+    return rep
 
 
 def choose_variant(lc, kernel, wl, layout, spec, D, u, out, stream):
@@ -438,7 +488,7 @@ def main():
         esz = 8 if wl["precision"] == "fp64" else 4
         e2e = {"value": flops * world / (es * 1e-3) / 1e9, "unit": "GFLOP/s",
                "h2d_bytes_per_step": esz * (E * N + F * N * N), "d2h_bytes_per_step": esz * F * E * N,
-               "ms_per_step": es}
+               "ms_per_step": es, "numa": numa_report(local_rank, (Dh, uh, oh))}
     if lc.device_error() != 0:
         raise RuntimeError("device error word set during the timed region")
 

@@ -28,6 +28,10 @@
  *     Element type: double for LC_PREC_FP64, float for every other precision.
  *   - All entry points are thread-safe; a kernel handle is immutable after
  *     creation (Section 2.4: transformations return new kernels).
+ *   - Per-device state (the device error word, the copy streams of lc_contract_host,
+ *     the address of lc_error_norm_noalloc's array) is looked up once per device and
+ *     kept for the life of the process: do not use the library across a
+ *     cudaDeviceReset of a device it has already run on.
  */
 #ifndef LC_H
 #define LC_H
@@ -361,6 +365,8 @@ lc_status lc_mlp_adam_step(float *params_dev, const float *grad_dev, float *m_de
  *   out_dev, ref_dev, sums_dev   as for lc_error_norm; 1 <= n <= 2^28
  * The partial sums live in a 64 KiB array in device memory that the library holds on
  * every GPU it is loaded on until the process exits; nothing is allocated per call.
+ * The grid (at most 4096 blocks of 256 threads, one per 1024 elements) grid-strides
+ * through larger inputs.
  * The array's address is looked up on the first call made on each device (with that
  * device current); make that first call before any stream capture.  All calls share the
  * array, so calls that overlap on the GPU race: serialise them.  Each call rewrites the

@@ -1474,7 +1474,6 @@ static lc_status grouped_plan_host(const Kernel &K, const lc_variant *v, const l
     P.threads = v->elems_per_thread * v->split_i >= 64 ? 256 : 512;
     const int T = P.threads;
     std::vector<double> tile_cost(ng);
-    std::vector<long long> ntiles(ng);
     P.groups.resize(ng);
     P.smem = 0;
     for (int gi = 0; gi < ng; ++gi) {
@@ -1509,8 +1508,7 @@ static lc_status grouped_plan_host(const Kernel &K, const lc_variant *v, const l
                 have = true;
             }
         }
-        const long long best_key_ok = have ? 0 : -1;
-        if (best_key_ok < 0)
+        if (!have)
             return LC_ERR_INVALID_VARIANT;
         SimtArgs a;
         memset(&a, 0, sizeof a);
@@ -1536,8 +1534,6 @@ static lc_status grouped_plan_host(const Kernel &K, const lc_variant *v, const l
         a.tail_free = 0;
         P.groups[gi] = a;
         P.smem = std::max(P.smem, best.g.smem);
-        ntiles[gi] = G.E > 0 ? best.g.ntiles * best.g.nchunks : 0;  // (tile, column block) items
-        (void)ntiles[gi];
         // estimated seconds per item: FMA pipe (FP32, padded columns) vs HBM
         const double flops = 2.0 * a.TE * (double)G.N * a.CW;
         const double bytes = 4.0 * a.TE * ((double)G.N + (a.isplit ? a.isplit : (double)a.G * G.N));

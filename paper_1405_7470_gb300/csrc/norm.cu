@@ -3,6 +3,7 @@
 // same on every call: per-block partial sums, then one block adds them in order.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 
@@ -138,14 +139,17 @@ lc_status norm_launch(const void *out, int dtype, const double *ref, long long n
 // its partial sums from a fixed array that the library places in device memory.
 //
 // The array holds one (sum of squared differences, sum of squares) pair per block of
-// the first kernel; the grid has one block per kNoallocChunk elements, so one call
-// handles at most kNoallocChunk * kNoallocMaxBlocks elements (2^28).  Every GPU that
+// the first kernel.  The grid is fixed by n alone: one block per kNoallocPerBlock
+// elements, at most kNoallocMaxBlocks blocks, which grid-stride through the rest, so
+// small inputs still spread over every SM.  One call handles at most kNoallocMaxElems
+// elements (2^28), the documented limit of this entry point.  Every GPU that
 // loads the library keeps these 64 KiB until the process exits.  All calls share the
 // array: calls whose kernels overlap on the GPU (different streams, or threads) race on
 // it and must be serialised by the caller.  Each call overwrites every slot it reads, so
 // nothing needs clearing between calls.
-static constexpr long long kNoallocChunk = 1LL << 16;
+static constexpr long long kNoallocPerBlock = 4LL * kNormThreads;
 static constexpr int kNoallocMaxBlocks = 4096;
+static constexpr long long kNoallocMaxElems = 1LL << 28;
 static __device__ __align__(256) double g_norm_scratch[2 * kNoallocMaxBlocks];
 
 static std::mutex g_scratch_mu;
@@ -185,15 +189,16 @@ lc_status lc_error_norm_noalloc(const void *out, int32_t out_dtype, const double
         return LC_ERR_INVALID_ARGUMENT;
     if (out_dtype != LC_DTYPE_F32 && out_dtype != LC_DTYPE_F64)
         return LC_ERR_INVALID_ARGUMENT;
-    if (n > lc::kNoallocChunk * lc::kNoallocMaxBlocks)
-        return LC_ERR_BUFFER_TOO_SMALL;  // more elements than the fixed partial-sum array covers
+    if (n > lc::kNoallocMaxElems)
+        return LC_ERR_BUFFER_TOO_SMALL;  // beyond the entry point's documented size limit
     if (((uintptr_t)ref & 7u) || ((uintptr_t)sums & 7u) || ((uintptr_t)out & (out_dtype == LC_DTYPE_F64 ? 7u : 3u)))
         return LC_ERR_MISALIGNED;
     double *scratch = nullptr;
     lc_status st = lc::norm_scratch(&scratch);
     if (st != LC_OK)
         return st;
-    const int blocks = (int)((n + lc::kNoallocChunk - 1) / lc::kNoallocChunk);
+    const int blocks =
+        (int)std::min<long long>(lc::kNoallocMaxBlocks, (n + lc::kNoallocPerBlock - 1) / lc::kNoallocPerBlock);
     cudaStream_t s = (cudaStream_t)stream;
     if (out_dtype == LC_DTYPE_F32)
         lc::norm_partial_kernel<float><<<blocks, lc::kNormThreads, 0, s>>>(static_cast<const float *>(out), ref, n,

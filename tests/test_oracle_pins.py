@@ -207,6 +207,47 @@ def test_bf16x3_all_nine_products_equal_exact_contraction():
     assert 1e-4 < err < 1e-2   # bf16 operand rounding shows up at about 2^-8
 
 
+def _bf16_pin_failures(fn):
+    """Check ``fn(D, u)`` (the plain BF16 path's target) against a route that shares no
+    code with the oracle: torch's nearest-even bfloat16 conversion of BOTH operands, then
+    numpy's einsum in float64.  Returns the failing check names."""
+    torch = pytest.importorskip("torch")
+    fails = []
+    for seed, scale in ((21, None), (22, 3.0)):
+        D, u = synth.operands(97, 13, 3, np.float32, seed=seed, scale_exp=scale)
+        Db = torch.from_numpy(D).to(torch.bfloat16).double().numpy()
+        ub = torch.from_numpy(u).to(torch.bfloat16).double().numpy()
+        want = np.einsum("fij,ej->fei", Db, ub)
+        got = np.asarray(fn(D, u), dtype=np.float64)
+        # products of bfloat16 values are exact in float64; two summation orders of
+        # N = 13 terms differ by at most 2 N 2^-53 sum_j |D_ij u_j|
+        den = np.einsum("fij,ej->fei", np.abs(Db), np.abs(ub))
+        if got.shape != want.shape or not np.all(np.abs(got - want) <= 2 * 13 * 2.0 ** -53 * den):
+            fails.append(f"torch_bf16_einsum_seed{seed}")
+    return fails
+
+
+def test_contract_bf16_matches_torch_rounding_and_einsum():
+    assert _bf16_pin_failures(oracle.contract_bf16) == []
+
+
+@pytest.mark.parametrize("kind", ["round_u_only", "round_D_only", "round_neither", "truncate"])
+def test_bf16_pin_catches_planted_mistakes(kind):
+    def chop(x):  # round toward zero to bfloat16 (a plausible wrong rounding mode)
+        b = np.ascontiguousarray(np.asarray(x, dtype=np.float32)).view(np.uint32) & np.uint32(0xFFFF0000)
+        return b.view(np.float32)
+
+    def fn(D, u):
+        if kind == "round_u_only":
+            return oracle.contract(D, oracle.bf16_round(u))
+        if kind == "round_D_only":
+            return oracle.contract(oracle.bf16_round(D), u)
+        if kind == "round_neither":
+            return oracle.contract(D, u)
+        return oracle.contract(chop(D), chop(u))
+    assert _bf16_pin_failures(fn), f"the bf16 pin missed the planted mistake {kind}"
+
+
 def test_integer_inputs_are_bf16_exact():
     D, u = synth.integer_operands(64, 33, 2, seed=8)
     ref = oracle.contract(D, u)
