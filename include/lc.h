@@ -136,6 +136,9 @@ struct lc_variant {
                                  one operator at a time and store it), or 128 (all epilogue
                                  warps stage every operator of the block, then store);
                                  0 = the planner's choice */
+    int32_t max_ctas;         /* upper bound on the persistent grid (0 = none): the CTAs then
+                                 walk more tiles each, and the rest of the GPU stays free for
+                                 concurrent work; at least the number of column blocks */
 };
 
 /*

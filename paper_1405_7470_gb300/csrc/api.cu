@@ -646,6 +646,18 @@ static bool simt_warp_shape(SimtGeom &g, int C, int N, int es, size_t fixed, siz
     return best_waste >= 0;
 }
 
+// Apply the descriptor's grid bound (max_ctas > 0) to a grid of whole column-block sets:
+// false if the bound is below one set or the grid does not fit an int.
+static bool cap_grid(long long &grid, int nblocks, int max_ctas)
+{
+    if (max_ctas > 0) {
+        if (max_ctas < nblocks)
+            return false;
+        grid = std::min<long long>(grid, (long long)max_ctas / nblocks * nblocks);
+    }
+    return grid <= 0x7fffffffLL;
+}
+
 struct Resolved {
     int engine, layout, precision;
     SimtGeom g;
@@ -672,7 +684,7 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         return LC_ERR_INVALID_VARIANT;
     if (v->tail_free != 0 && v->tail_free != 1)
         return LC_ERR_INVALID_VARIANT;
-    if (v->ctas_per_sm < 0 || v->ctas_per_sm > 32)
+    if (v->ctas_per_sm < 0 || v->ctas_per_sm > 32 || v->max_ctas < 0)
         return LC_ERR_INVALID_VARIANT;
     r.engine = v->engine;
     r.layout = v->layout;
@@ -756,7 +768,7 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         if (v->ctas_per_sm > 0)
             grid = std::min<long long>(grid, (long long)v->ctas_per_sm * sms);
         grid = std::max<long long>(grid / g.nchunks * g.nchunks, g.nchunks);  // whole column-block sets
-        if (grid > 0x7fffffffLL)
+        if (!cap_grid(grid, g.nchunks, v->max_ctas))
             return LC_ERR_INVALID_VARIANT;
         g.grid = (int)grid;
         return LC_OK;
@@ -867,7 +879,7 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         long long work = t.ntiles * t.nblocks;
         long long grid = std::min<long long>(work, (long long)sms);
         grid = std::max<long long>(grid / t.nblocks * t.nblocks, t.nblocks);
-        if (grid > 0x7fffffffLL)
+        if (!cap_grid(grid, t.nblocks, v->max_ctas))
             return LC_ERR_INVALID_VARIANT;
         r.tc_grid = (int)grid;
         return LC_OK;
@@ -893,9 +905,10 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         long long grid = g.ntiles;
         if (v->ctas_per_sm > 0)
             grid = std::min<long long>(grid, (long long)v->ctas_per_sm * sms);
-        if (grid > 0x7fffffffLL)
+        grid = std::max<long long>(grid, 1);
+        if (!cap_grid(grid, 1, v->max_ctas))
             return LC_ERR_INVALID_VARIANT;
-        g.grid = (int)std::max<long long>(grid, 1);
+        g.grid = (int)grid;
         g.smem = 0;
         return LC_OK;
     }
@@ -1051,8 +1064,9 @@ lc_status lc_kernel_print(const lc_kernel *kh, const lc_variant *v, char *buf, s
             appendf(s, "  no guard: assumption %s mod %d = 0\n", E, v->tile_e);
         else
             appendf(s, "  guard: %s_inner + %d*%s_outer < %s on the last tile only\n", e, v->tile_e, e, E);
-        appendf(s, "tags: %s_outer -> g.0 (persistent, %d CTAs/SM), ilp(%s_inner) = %d, ilp(%s) = %d, unr(%s) = %d\n",
-                e, v->ctas_per_sm, e, v->elems_per_thread, K.i_iname.c_str(), v->split_i,
+        appendf(s, "tags: %s_outer -> g.0 (persistent, %d CTAs/SM, at most %d CTAs; 0 = no bound), ilp(%s_inner) = %d, "
+                   "ilp(%s) = %d, unr(%s) = %d\n",
+                e, v->ctas_per_sm, v->max_ctas, e, v->elems_per_thread, K.i_iname.c_str(), v->split_i,
                 K.j_iname.c_str(), v->unroll);
         appendf(s, "add_prefetch(%s): %s, stages: %d, output buffers: %d\n", K.u_name.c_str(),
                 v->prefetch_smem ? "shared memory" : "none (global loads)", v->stages, v->out_buffers);
@@ -1557,7 +1571,10 @@ static lc_status grouped_plan_host(const Kernel &K, const lc_variant *v, const l
         }
     }
     const int per_sm = v->ctas_per_sm > 0 ? v->ctas_per_sm : 2;
-    P.grid = (int)std::max<long long>(1, std::min<long long>((long long)sms * per_sm, total_items));
+    long long cap = (long long)sms * per_sm;
+    if (v->max_ctas > 0)
+        cap = std::min<long long>(cap, v->max_ctas);
+    P.grid = (int)std::max<long long>(1, std::min<long long>(cap, total_items));
     const double budget = total / P.grid;
     // CTAs per big unit (worth >= 1 CTA), the rest for the small units
     std::vector<int> alloc(units.size(), 0);

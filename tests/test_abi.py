@@ -172,3 +172,22 @@ def test_variant_plan_reports_the_resolved_launch(lib):
     v.unroll = 9
     with pytest.raises(lc.LcError):
         lc.variant_plan(k, 1 << 21, 35, 3, v)
+
+
+def test_max_ctas_bounds_the_grid(lib):
+    """The descriptor's grid bound: honoured by the plan in whole column-block sets; a bound
+    below one set of column blocks, or a negative one, is rejected before any launch."""
+    kernel = lc.Kernel()
+    for prec, N, F in (("bf16x3", 84, 4), ("fp32", 35, 3), ("bf16", 165, 3)):
+        v = lc.variant_default(kernel, 1 << 16, N, F, "elem", prec)
+        p = lc.variant_plan(kernel, 1 << 16, N, F, v)
+        nb = p["column_blocks"]
+        v.max_ctas = 2 * nb + 1
+        assert lc.variant_plan(kernel, 1 << 16, N, F, v)["grid"] == (2 * nb + 1) // nb * nb
+        v.max_ctas = 10 ** 6
+        assert lc.variant_plan(kernel, 1 << 16, N, F, v)["grid"] == p["grid"]
+        if nb > 1:
+            v.max_ctas = nb - 1
+            assert lc.variant_validate(kernel, 1 << 16, N, F, v) == 3  # LC_ERR_INVALID_VARIANT
+        v.max_ctas = -1
+        assert lc.variant_validate(kernel, 1 << 16, N, F, v) == 3

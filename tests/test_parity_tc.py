@@ -174,3 +174,33 @@ def test_large_n_k_blocks_bit_exact(lc, E, N, F, layout, prec, kbw):
     assert lc.variant_validate(kernel, E, N, F, v) == 0
     got = run(lc, kernel, v, D, uu, layout)
     assert np.array_equal(got, oracle.contract(D, uu, layout)), (E, N, F, layout, prec, kbw)
+
+
+@pytest.mark.parametrize("layout", ["elem", "node"])
+def test_full_size_fp32_three_tensor_sampled(lc, layout):
+    """E=2^21, N=35, F=3 on the tensor cores (BF16X3, the default descriptor and the bench's
+    launch configuration), sampled rows against the oracle: per-output FP32-accumulation
+    bound against the exact split products, and the relative error within 1e-6."""
+    import torch
+    E, N, F = 1 << 21, 35, 3
+    D, u = synth.fp32_three()
+    kernel = lc.Kernel()
+    uu = synth.to_node_major(u) if layout == "node" else u
+    v = lc.variant_default(kernel, E, N, F, layout, "bf16x3")
+    assert lc.variant_dict(v)["engine"] == "tcgen05"
+    rows = np.unique(np.concatenate([np.arange(300), np.random.default_rng(3).integers(0, E, 4000),
+                                     np.arange(E - 300, E)]))
+    out = lc.contract(kernel, v, to_dev(D), to_dev(uu))
+    torch.cuda.synchronize()
+    assert lc.device_error() == 0
+    idx = torch.from_numpy(rows).cuda()
+    got = out.index_select(2 if layout == "node" else 1, idx).cpu().numpy().astype(np.float64)
+    if layout == "node":
+        got = got.transpose(0, 2, 1)
+    us = u[rows]
+    target = oracle.contract_bf16x3(D, us)
+    Ds, uss = oracle.bf16_split3(D), oracle.bf16_split3(us)
+    bound = accum_bound(np.abs(Ds[0]) + np.abs(Ds[1]) + np.abs(Ds[2]), np.abs(uss[0]) + np.abs(uss[1]) + np.abs(uss[2]),
+                        "elem", "bf16x3")
+    assert np.all(np.abs(got - target) <= bound)
+    assert oracle.rel_fro_error(got, oracle.contract_rows(D, u, rows)) <= 1e-6
