@@ -361,6 +361,43 @@ lc_status lc_mlp_adam_step(float *params_dev, const float *grad_dev, float *m_de
                            int32_t step, float lr, float beta1, float beta2, float eps, void *stream);
 
 /*
+ * The learned pick (Section 1: the controlling program chooses the transformations per
+ * target and workload).  The cost model reads LC_FEATURES features of a (problem,
+ * descriptor) pair: problem size and requested path, the descriptor's fields, and the
+ * launch plan lc_variant_plan resolves it to (grid, tiles per CTA, column blocks, shared
+ * memory, threads, tensor-core instructions per CTA, ...); every feature is O(1).
+ */
+#define LC_FEATURES 32
+
+/*
+ * x[0..LC_FEATURES) = the features of descriptor v for the problem (E, N, F) stored in
+ * `layout` and requested at `precision` (the path asked for; v->precision is the one it
+ * runs).  Host only; uses the current device's SM count and shared memory when there is
+ * one (else a 148-SM, 227 KB part).  Errors: those of lc_variant_plan.
+ */
+lc_status lc_variant_features(const lc_kernel *k, int64_t E, int32_t N, int32_t F, int32_t layout,
+                              int32_t precision, const lc_variant *v, float *x);
+
+/* Workspace bytes lc_pick_variant needs (room for the features and predictions of up to
+ * 256 candidates). */
+lc_status lc_pick_workspace_size(size_t *bytes);
+
+/*
+ * Pick a descriptor with a trained cost model: enumerate the candidates
+ * (lc_enumerate_variants), build their features (lc_variant_features), predict their log
+ * run time with lc_mlp_forward on `stream` (din = LC_FEATURES), and return the candidate
+ * with the smallest prediction (the first one on ties) in *picked, its prediction in
+ * *predicted (may be NULL).  Synchronises `stream`.
+ *   params_dev     the network's parameters (lc_mlp_param_count(LC_FEATURES) floats)
+ *   workspace_dev  lc_pick_workspace_size bytes, 16-byte aligned (features, predictions)
+ * Errors: LC_ERR_INVALID_ARGUMENT, LC_ERR_BUFFER_TOO_SMALL, LC_ERR_MISALIGNED,
+ * LC_ERR_UNSUPPORTED (no candidate for this problem), LC_ERR_CUDA.
+ */
+lc_status lc_pick_variant(const lc_kernel *k, int64_t E, int32_t N, int32_t F, int32_t layout, int32_t precision,
+                          const float *params_dev, void *workspace_dev, size_t workspace_bytes,
+                          lc_variant *picked, float *predicted, void *stream);
+
+/*
  * lc_error_norm without a workspace, for callers that cannot allocate device memory
  * (cudaMalloc synchronises the device, which latency-bound or real-time callers forbid,
  * and some host frameworks give their plugins no allocator).  This call has no

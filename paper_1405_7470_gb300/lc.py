@@ -96,7 +96,12 @@ SIGNATURES = {
     "lc_mlp_loss_grad": ([_P, _P, _P, _I64, _I32, _P, _P, _SZ, _P], ctypes.c_int),
     "lc_mlp_adam_step": ([_P, _P, _P, _P, _I64, _I32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                           ctypes.c_float, _P], ctypes.c_int),
+    "lc_variant_features": ([_P, _I64, _I32, _I32, _I32, _I32, _VP, _P], ctypes.c_int),
+    "lc_pick_workspace_size": ([ctypes.POINTER(_SZ)], ctypes.c_int),
+    "lc_pick_variant": ([_P, _I64, _I32, _I32, _I32, _I32, _P, _P, _SZ, _VP, ctypes.POINTER(ctypes.c_float), _P],
+                        ctypes.c_int),
 }
+FEATURES = 32  # LC_FEATURES
 
 _lib = None
 _lock = threading.Lock()
@@ -371,3 +376,29 @@ def mlp_loss_grad(params, X, t, workspace=None, stream=None):
 def mlp_adam_step(params, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
     check(load().lc_mlp_adam_step(params.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(), params.numel(),
                                   step, lr, beta1, beta2, eps, _stream_ptr(stream)), "lc_mlp_adam_step")
+
+
+def variant_features(kernel: Kernel, E: int, N: int, F: int, layout, precision, v: lc_variant):
+    """The cost model's LC_FEATURES inputs for descriptor v on a problem (lc_variant_features)."""
+    import numpy as np
+    x = np.zeros(FEATURES, dtype=np.float32)
+    check(load().lc_variant_features(kernel.handle, E, N, F, LAYOUT[layout] if isinstance(layout, str) else layout,
+                                     PRECISION[precision] if isinstance(precision, str) else precision,
+                                     ctypes.byref(v), x.ctypes.data_as(ctypes.c_void_p)), "lc_variant_features")
+    return x
+
+
+def pick_variant(kernel: Kernel, E: int, N: int, F: int, layout, precision, params, workspace=None, stream=None):
+    """(descriptor, predicted log ms) picked by the trained network `params` (lc_pick_variant)."""
+    import torch
+    lib = load()
+    need = ctypes.c_size_t(0)
+    check(lib.lc_pick_workspace_size(ctypes.byref(need)), "lc_pick_workspace_size")
+    if workspace is None or workspace.numel() * workspace.element_size() < need.value:
+        workspace = torch.empty(need.value // 4 + 4, dtype=torch.float32, device=params.device)
+    v = lc_variant()
+    pred = ctypes.c_float(0.0)
+    check(lib.lc_pick_variant(kernel.handle, E, N, F, LAYOUT[layout], PRECISION[precision], params.data_ptr(),
+                              workspace.data_ptr(), need.value, ctypes.byref(v), ctypes.byref(pred),
+                              _stream_ptr(stream)), "lc_pick_variant")
+    return v, pred.value

@@ -124,15 +124,16 @@ PATHS = ("fp32", "bf16", "bf16x3")
 LAYOUTS = ("elem", "node")
 
 
-def picker_shapes(seed: int = 0, count: int = 600):
+def picker_shapes(seed: int = 0, count: int = 600, e_lo: float = 12.0, e_hi: float = 23.0):
     """Random shapes for the learned variant picker.
 
-    Returns a list of dicts {E, N, F, path, layout}; the first 500 train the
-    model and the last 100 are held out.
+    Returns a list of dicts {E, N, F, path, layout} with N ~ U{4..165},
+    E = floor(2^U(e_lo, e_hi)), F ~ U{1..4}; for the full experiment the first 500
+    train the model and the last 100 are held out.
     """
     rng = np.random.default_rng(seed)
     N = rng.integers(4, 166, size=count)
-    E = np.floor(2.0 ** rng.uniform(12.0, 23.0, size=count)).astype(np.int64)
+    E = np.floor(2.0 ** rng.uniform(e_lo, e_hi, size=count)).astype(np.int64)
     F = rng.integers(1, 5, size=count)
     p = rng.integers(0, len(PATHS), size=count)
     lay = rng.integers(0, len(LAYOUTS), size=count)

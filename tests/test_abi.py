@@ -191,3 +191,20 @@ def test_max_ctas_bounds_the_grid(lib):
             assert lc.variant_validate(kernel, 1 << 16, N, F, v) == 3  # LC_ERR_INVALID_VARIANT
         v.max_ctas = -1
         assert lc.variant_validate(kernel, 1 << 16, N, F, v) == 3
+
+
+def test_variant_features_and_pick_arguments(lib):
+    """The cost model's features come from the library (host only): LC_FEATURES finite values
+    with consistent one-hot groups; lc_pick_variant rejects bad arguments before any work."""
+    import numpy as np
+    kernel = lc.Kernel()
+    for path, layout in (("bf16x3", "elem"), ("fp32", "node"), ("bf16", "node")):
+        for v in lc.enumerate_variants(kernel, 100000, 35, 3, layout, path):
+            x = lc.variant_features(kernel, 100000, 35, 3, layout, path, v)
+            assert x.shape == (lc.FEATURES,) and np.all(np.isfinite(x))
+            assert x[4:7].sum() == 1 and x[7:9].sum() == 1 and x[12:15].sum() == 1
+    need = ctypes.c_size_t(0)
+    assert lib.lc_pick_workspace_size(ctypes.byref(need)) == 0 and need.value >= 256 * 33 * 4
+    v = lc.lc_variant()
+    assert lib.lc_pick_variant(kernel.handle, 1000, 35, 3, 0, 3, None, None, 0, ctypes.byref(v), None, None) == 1
+    assert lib.lc_pick_variant(kernel.handle, 1000, 35, 3, 0, 3, 16, 16, 8, ctypes.byref(v), None, None) == 6

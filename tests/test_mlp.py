@@ -18,8 +18,14 @@ def test_features_are_deterministic_and_bounded():
     assert x.shape == (picker.DIN,) and x.dtype == np.float32
     assert np.array_equal(x, picker.features(sh, v))
     assert np.all(np.abs(x) <= 2.0)
+    from paper_1405_7470_gb300 import lc
     for s in synth.picker_shapes(0, 50):
-        assert np.all(np.isfinite(picker.features(s, v)))
+        for c in lc.enumerate_variants(picker.kernel_for(s["F"]), s["E"], s["N"], s["F"], s["layout"], s["path"]):
+            x = picker.features(s, c)
+            assert np.all(np.isfinite(x)) and np.all(np.abs(np.delete(x, 27)) <= 4.0)  # 27: column blocks / 8
+    # a descriptor that is not valid for the problem has no features
+    with pytest.raises(lc.LcError):
+        picker.features(dict(E=1000, N=300, F=3, path="bf16x3", layout="elem"), v)
 
 
 def test_he_uniform_init_is_seeded():

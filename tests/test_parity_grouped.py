@@ -44,6 +44,7 @@ def test_grouped_matches_oracle(lc, layout, graph):
         for rep in range(2):  # replay twice: the result must not depend on the previous run
             for _, _, out in groups:
                 out.fill_(float("nan"))
+            torch.cuda.synchronize()  # the fills run on torch's stream, the plan on `stream`
             plan.run(stream)
             stream.synchronize()
             assert lc.device_error() == 0
@@ -93,6 +94,7 @@ def _check_groups_sampled(lc, kernel, v, sizes, data, layout, graph, reps=2):
     for rep in range(reps):
         for _, _, out in groups:
             out.fill_(float("nan"))
+        torch.cuda.synchronize()  # the fills run on torch's stream, the plan on `stream`
         plan.run(stream)
         stream.synchronize()
         assert lc.device_error() == 0
