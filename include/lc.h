@@ -139,6 +139,15 @@ struct lc_variant {
     int32_t max_ctas;         /* upper bound on the persistent grid (0 = none): the CTAs then
                                  walk more tiles each, and the rest of the GPU stays free for
                                  concurrent work; at least the number of column blocks */
+    int32_t slot_ops;         /* tensor-core engine, element-major, store_rows 128: operators per
+                                 staging slot: 1 (one operator's whole tile per slot, stored as
+                                 soon as it is staged) or 0 (the planner's choice: every
+                                 operator of the block per slot); must be 0 otherwise */
+    int32_t mma_order;        /* tensor-core engine, BF16X3: 0 = the planner's choice, 1 = the
+                                 large hi*hi products in their own accumulator columns (two D
+                                 terms stacked along the MMA's N), 2 = one accumulator, the
+                                 small products first over all of K and hi*hi last; must be 0
+                                 for other paths */
 };
 
 /*

@@ -17,7 +17,12 @@ What it computes (all in float64, no reordering of any sum):
   ``contract_bf16x3``     paths: bf16-rounded operands (or the kept split products)
                           multiplied exactly, summed in float64.
 * ``mlp_forward`` / ``mlp_loss_grad`` / ``adam_step``  the cost model's network.
+* ``contract_geo``        out[d,e,i] = sum_f r[e,d,f] sum_j D[f,i,j] u[e,j]: the volume
+                          derivative with per-element geometric factors.
 * ``rel_fro_error``       ||out - ref||_F / ||ref||_F in float64.
+* ``elementwise.evaluate`` one elementwise assignment over a rectangular loop domain,
+                          every operation one IEEE float32 operation (module
+                          ``oracle.elementwise``).
 
 Parity pins: every function here is pinned by tests in ``tests/test_oracle_pins.py``
 against brute force, closed forms, a library routine, or finite differences.
@@ -69,6 +74,8 @@ def _load():
             lib.oracle_contract.argtypes = [P, P, P, i64, i32, i32, i32, i32]
             lib.oracle_contract.restype = None
             lib.oracle_num_threads.restype = ctypes.c_int
+            lib.oracle_contract_geo.argtypes = [P, P, P, P, i64, i32, i32, i32, i32, i32]
+            lib.oracle_contract_geo.restype = None
             lib.oracle_bf16_round.argtypes = [P, P, i64]
             lib.oracle_bf16_split3.argtypes = [P, P, P, P, i64]
             lib.oracle_mlp_param_count.argtypes = [i32, i32]
@@ -127,6 +134,41 @@ def contract_rows(D, u, rows, layout: str = "elem", threads: int = 0) -> np.ndar
     u = np.asarray(u)
     sub = u[rows] if layout == "elem" else u[:, rows].T
     return contract(D, sub, "elem", threads)
+
+
+def contract_geo(D, u, r, layout: str = "elem", threads: int = 0) -> np.ndarray:
+    """out[d,e,i] = sum_f r[e,d,f] * sum_j D[f,i,j] u[e,j] in float64 (volume derivative
+    with per-element geometric factors).
+
+    D: (F, N, N). u: (E, N) or (N, E) per layout. r: (E, Dd, F) element-major or
+    (Dd, F, E) node-major. Returns (Dd, E, N) or (Dd, N, E).
+    """
+    lib = _load()
+    D, u, r = _f64(D), _f64(u), _f64(r)
+    F, N, N2 = D.shape
+    assert N == N2
+    node = layout == "node"
+    if node:
+        Dd, F2, E = r.shape
+        assert u.shape == (N, E)
+        out = np.empty((Dd, N, E), dtype=np.float64)
+    else:
+        E, Dd, F2 = r.shape
+        assert u.shape == (E, N)
+        out = np.empty((Dd, E, N), dtype=np.float64)
+    assert F2 == F
+    if E > 0 and N > 0 and F > 0 and Dd > 0:
+        lib.oracle_contract_geo(_ptr(D), _ptr(u), _ptr(r), _ptr(out), E, N, F, Dd, int(node), int(threads))
+    return out
+
+
+def contract_geo_rows(D, u, r, rows, layout: str = "elem", threads: int = 0) -> np.ndarray:
+    """contract_geo for the elements ``rows`` only, as (Dd, len(rows), N)."""
+    rows = np.asarray(rows, dtype=np.int64)
+    u, r = np.asarray(u), np.asarray(r)
+    if layout == "node":
+        return contract_geo(D, u[:, rows].T, np.ascontiguousarray(r[:, :, rows].transpose(2, 0, 1)), "elem", threads)
+    return contract_geo(D, u[rows], r[rows], "elem", threads)
 
 
 def bf16_round(x) -> np.ndarray:

@@ -77,6 +77,47 @@ void oracle_contract(const double *D, const double *u, double *out,
     (void)nthreads;
 }
 
+/* The volume derivative with per-element geometric factors (the dG FEM volume
+ * workload of Table 1 with the chain rule applied inside the kernel):
+ *
+ *   out[d,e,i] = sum_f r[e,d,f] * ( sum_j D[f,i,j] * u[e,j] )
+ *
+ * over { [d,f,e,i,j] : 0<=d<Dd and 0<=f<F and 0<=e<E and 0<=i,j<N }: the inner sum
+ * is the contraction above (the reference-coordinate derivative along f), the outer
+ * one maps it to physical coordinate d with the element's factors r[e,d,:].
+ * Layouts: element-major r [E][Dd][F], out [Dd][E][N];
+ *          node-major    r [Dd][F][E], out [Dd][N][E]  (u as for the contraction). */
+void oracle_contract_geo(const double *D, const double *u, const double *r, double *out,
+                         int64_t E, int32_t N, int32_t F, int32_t Dd, int32_t node_major,
+                         int32_t nthreads)
+{
+#ifdef _OPENMP
+    int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(static) num_threads(nt)
+#endif
+    for (int64_t e = 0; e < E; ++e) {
+        for (int32_t d = 0; d < Dd; ++d) {
+            for (int32_t i = 0; i < N; ++i) {
+                double acc = 0.0;
+                for (int32_t f = 0; f < F; ++f) {
+                    double part = 0.0;
+                    for (int32_t j = 0; j < N; ++j) {
+                        double x = node_major ? u[(int64_t)j * E + e] : u[e * N + j];
+                        part += D[((int64_t)f * N + i) * N + j] * x;
+                    }
+                    double g = node_major ? r[((int64_t)d * F + f) * E + e] : r[(e * Dd + d) * F + f];
+                    acc += g * part;
+                }
+                if (node_major)
+                    out[((int64_t)d * N + i) * E + e] = acc;
+                else
+                    out[((int64_t)d * E + e) * N + i] = acc;
+            }
+        }
+    }
+    (void)nthreads;
+}
+
 /* Round one binary32 value to bfloat16, nearest-even, returned as a float.
  * The bfloat16 value is the upper half of a binary32 word; the lower 16 bits
  * decide the rounding: above half -> up, below -> down, exactly half -> to

@@ -699,7 +699,8 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
     if (need_device && (sms <= 0 || smem_cap == 0))
         return LC_ERR_NO_DEVICE;
 
-    if (v->engine != LC_ENGINE_TCGEN05 && (v->out_buffers != 0 || v->store_rows != 0))
+    if (v->engine != LC_ENGINE_TCGEN05 &&
+        (v->out_buffers != 0 || v->store_rows != 0 || v->slot_ops != 0 || v->mma_order != 0))
         return LC_ERR_INVALID_VARIANT;
     if (v->engine == LC_ENGINE_SIMT) {
         if (v->precision != LC_PREC_FP32 && v->precision != LC_PREC_FP64)
@@ -790,6 +791,10 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
             return LC_ERR_INVALID_VARIANT;
         const bool node = v->layout == LC_LAYOUT_NODE_MAJOR;
         const int NT = v->precision == LC_PREC_BF16X3 ? 3 : 1;
+        if (!(v->slot_ops == 0 || v->slot_ops == 1) || (v->slot_ops == 1 && (node || v->store_rows != 128)))
+            return LC_ERR_INVALID_VARIANT;  // one operator per whole-tile slot: element-major, 128-row stores
+        if (v->mma_order < 0 || v->mma_order > 2 || (v->mma_order != 0 && NT != 3))
+            return LC_ERR_INVALID_VARIANT;
         TcArgs &t = r.tc;
         memset(&t, 0, sizeof t);
         t.N = N;
@@ -813,14 +818,18 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         // small N (few, large stores), else 32-row pieces of one operator at a time (the
         // stores stream, and the staging slots stay small)
         t.store_quarters = v->store_rows ? v->store_rows / 32 : (N <= 48 ? 4 : 1);
+        t.slot_ops = v->slot_ops;
         auto plan = [&](int G, TcArgs &q) -> bool {
             q.G = G;
             // operator padding: 16 columns (16-column epilogue chunks), or 8 where that lets
             // the BF16X3 terms stack (2 CBp <= 256) or the block fit (CBp <= 256) at all
             auto cbp = [&](int np) { return (G * np + 15) / 16 * 16; };
             const int np16 = (N + 15) / 16 * 16, np8 = (N + 7) / 8 * 8;
-            if (NT == 3 && 2 * cbp(np16) > 256 && 2 * cbp(np8) <= 256)
+            const bool want_stack = NT == 3 && v->mma_order != 2;
+            if (want_stack && 2 * cbp(np16) > 256 && 2 * cbp(np8) <= 256)
                 q.Np = np8;
+            else if (NT == 3 && !want_stack && cbp(np8) < cbp(np16))
+                q.Np = np8;  // one accumulator region: the narrowest padding (smaller B, fewer columns)
             else
                 q.Np = cbp(np16) <= 256 ? np16 : np8;
             q.chunk = q.Np % 16 == 0 ? 16 : 8;
@@ -828,7 +837,9 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
             q.CBp = cbp(q.Np);
             if (q.CBp > 256)
                 return false;
-            q.stack = NT == 3 && 2 * q.CBp <= 256;
+            q.stack = want_stack && 2 * q.CBp <= 256;
+            if (v->mma_order == 1 && !q.stack)
+                return false;  // the stacked order needs 2 x MMA N <= 256
             q.tmem_cols = 32;
             while (q.tmem_cols < (q.stack ? 2 : 1) * q.CBp)
                 q.tmem_cols *= 2;
@@ -839,7 +850,7 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
             off += (size_t)q.stages * 128 * N * 4;
             q.off_out = (unsigned)off;
             if (!node)  // staging slots: every operator of the block (4 quarters per store), else one
-                off += (size_t)q.obufs * (q.store_quarters == 4 ? G : 1) * 128 * N * 4;
+                off += (size_t)q.obufs * (q.store_quarters == 4 && q.slot_ops != 1 ? G : 1) * 128 * N * 4;
             off = (off + 15) / 16 * 16;
             q.off_bar = (unsigned)off;
             off += 1024;  // 10 mbarriers, TMEM address, abort flag; 2 x 2 x 16 A-block mbarriers

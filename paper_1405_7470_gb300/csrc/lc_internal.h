@@ -96,6 +96,7 @@ struct TcArgs {
     int abufs;      // A-operand buffers (1 or 2)
     int obufs;      // element-major output staging slots of one operator-tile (1 to 4)
     int store_quarters;  // element-major: TMEM lane quarters (32 rows each) per bulk store: 1, 2 or 4
+    int slot_ops;   // element-major, 4 quarters per store: 1 = one operator per staging slot, else all G
     long long ntiles;
     int bulk_u, bulk_store;
     unsigned int *err;

@@ -596,7 +596,7 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
         };
         int k = 0;
         bool ok = true;
-        if (SQ == 4) {
+        if (SQ == 4 && (NODE || a.slot_ops != 1)) {
             // ---- node-major, or element-major with whole-tile slots
             for (long long t = my_first; t < a.ntiles; t += my_step, ++k) {
                 const int b = k & 1;
@@ -647,7 +647,8 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
             if (!NODE && tid == 0)
                 bulk_wait0();
         } else {
-            // ---- element-major, one operator per slot, store groups of SQ quarters
+            // ---- element-major, one operator per slot, store groups of SQ quarters (with SQ = 4
+            //      all epilogue warps form one group and each slot holds one operator's tile)
             const int gq = q / SQ, qin = q % SQ;  // store group, quarter within it
             const int gthreads = 32 * He * SQ;
             const bool leader = part == 0 && lane == 0 && qin == 0;  // issues and waits on the group's stores

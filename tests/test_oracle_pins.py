@@ -303,3 +303,88 @@ def test_adam_constant_gradient_closed_form():
         oracle.adam_step(p, g, m, v, t, lr=lr, eps=eps)
     want = -5 * lr * g / (np.abs(g) + eps)
     assert np.allclose(p, want, rtol=1e-9, atol=1e-15)
+
+
+# ------------------------------------------------- geometric-factor volume derivative
+
+def _geo_pin_failures(fn):
+    """Pins of out[d,e,i] = sum_f r[e,d,f] sum_j D[f,i,j] u[e,j] against ``fn(D, u, r, layout)``."""
+    fails = []
+    with open(os.path.join(GOLDEN, "contract_geo_hand.json")) as fh:
+        g = json.load(fh)
+    if not np.array_equal(fn(np.array(g["D"], float), np.array(g["u"], float), np.array(g["r"], float), "elem"),
+                          np.array(g["out"], float)):
+        fails.append("hand")
+    rng = np.random.default_rng(31)
+    E, N, F, Dd = 23, 7, 3, 2
+    D = rng.uniform(-1, 1, size=(F, N, N))
+    u = rng.standard_normal((E, N))
+    r = rng.standard_normal((E, Dd, F))
+    if not np.allclose(fn(D, u, r, "elem"), np.einsum("edf,fij,ej->dei", r, D, u), rtol=1e-13, atol=1e-13):
+        fails.append("einsum")
+    # r = identity per element (Dd = F): the plain contraction, exactly
+    I = np.broadcast_to(np.eye(F), (E, F, F)).copy()
+    if not np.array_equal(fn(D, u, I, "elem"), oracle.contract(D, u)):
+        fails.append("identity_factors")
+    # r[e,d,f] = c_f for d = 0 and 0 otherwise: one weighted sum of the contractions
+    c = rng.standard_normal(F)
+    rc = np.zeros((E, Dd, F))
+    rc[:, 0, :] = c
+    want = np.einsum("f,fei->ei", c, oracle.contract(D, u))
+    got = fn(D, u, rc, "elem")
+    if not (np.allclose(got[0], want, rtol=1e-13, atol=1e-13) and np.all(got[1] == 0)):
+        fails.append("weighted_sum")
+    # linear in r
+    r2 = rng.standard_normal((E, Dd, F))
+    if not np.allclose(fn(D, u, 2 * r - 0.5 * r2, "elem"), 2 * fn(D, u, r, "elem") - 0.5 * fn(D, u, r2, "elem"),
+                       rtol=1e-12, atol=1e-12):
+        fails.append("linear_r")
+    # integer-valued inputs: exact
+    Di, ui, ri = rng.integers(-4, 5, (F, N, N)), rng.integers(-4, 5, (E, N)), rng.integers(-3, 4, (E, Dd, F))
+    if not np.array_equal(fn(Di.astype(float), ui.astype(float), ri.astype(float), "elem"),
+                          np.einsum("edf,fij,ej->dei", ri, Di, ui).astype(float)):
+        fails.append("integer_exact")
+    # node-major layout: the transposes
+    got_n = fn(D, np.ascontiguousarray(u.T), np.ascontiguousarray(r.transpose(1, 2, 0)), "node")
+    if not np.array_equal(got_n, np.ascontiguousarray(fn(D, u, r, "elem").transpose(0, 2, 1))):
+        fails.append("node_major")
+    return fails
+
+
+def test_contract_geo_passes_every_pin():
+    assert _geo_pin_failures(oracle.contract_geo) == []
+
+
+@pytest.mark.parametrize("kind", ["transpose_r", "drop_last_f", "transpose_D", "none"])
+def test_geo_pins_catch_planted_mistakes(kind):
+    def fn(D, u, r, layout):
+        if layout == "node":
+            u, r = u.T, r.transpose(2, 0, 1)
+        F, N, _ = D.shape
+        E, Dd, _ = r.shape
+        out = np.zeros((Dd, E, N))
+        for d in range(Dd):
+            for e in range(E):
+                for i in range(N):
+                    acc = 0.0
+                    for f in range(F - 1 if kind == "drop_last_f" else F):
+                        part = sum((D[f, j, i] if kind == "transpose_D" else D[f, i, j]) * u[e, j] for j in range(N))
+                        g = r[e, f, d] if (kind == "transpose_r" and f < Dd and d < F) else r[e, d, f]
+                        acc += g * part
+                    out[d, e, i] = acc
+        return out.transpose(0, 2, 1).copy() if layout == "node" else out
+    fails = _geo_pin_failures(fn)
+    if kind == "none":
+        assert fails == []
+    else:
+        assert fails, f"no pin caught the planted mistake {kind}"
+
+
+def test_contract_geo_rows_matches_full():
+    D, u = synth.operands(90, 6, 3, np.float32, seed=8)
+    r = np.random.default_rng(2).standard_normal((90, 3, 3)).astype(np.float32)
+    rows = np.array([0, 89, 41])
+    full = oracle.contract_geo(D, u, r)
+    assert np.array_equal(oracle.contract_geo_rows(D, u, r, rows), full[:, rows, :])
+    rn = np.ascontiguousarray(r.transpose(1, 2, 0))
+    assert np.array_equal(oracle.contract_geo_rows(D, synth.to_node_major(u), rn, rows, "node"), full[:, rows, :])
