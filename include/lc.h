@@ -139,15 +139,16 @@ struct lc_variant {
     int32_t max_ctas;         /* upper bound on the persistent grid (0 = none): the CTAs then
                                  walk more tiles each, and the rest of the GPU stays free for
                                  concurrent work; at least the number of column blocks */
-    int32_t slot_ops;         /* tensor-core engine, element-major, store_rows 128: operators per
-                                 staging slot: 1 (one operator's whole tile per slot, stored as
-                                 soon as it is staged) or 0 (the planner's choice: every
-                                 operator of the block per slot); must be 0 otherwise */
     int32_t mma_order;        /* tensor-core engine, BF16X3: 0 = the planner's choice, 1 = the
                                  large hi*hi products in their own accumulator columns (two D
                                  terms stacked along the MMA's N), 2 = one accumulator, the
                                  small products first over all of K and hi*hi last; must be 0
                                  for other paths */
+    int32_t a_operand;        /* tensor-core engine: where the converted u tile (the MMA's A
+                                 operand) lives: 0 = the planner's choice, 1 = shared memory,
+                                 2 = tensor memory beside the accumulators (written by the
+                                 conversion warps with tcgen05.st; frees shared memory and its
+                                 bandwidth, needs the columns: one accumulator region) */
 };
 
 /*
@@ -191,6 +192,8 @@ typedef struct lc_plan {
     int32_t out_slots;       /* element-major output staging slots */
     int32_t store_rows;      /* element-major tile rows per bulk store */
     int32_t mma_per_tile;    /* tcgen05.mma instructions per tile and column block */
+    int32_t a_in_tmem;       /* 1: the A terms live in tensor memory */
+    int32_t tmem_cols;       /* tensor-memory columns allocated per CTA */
 } lc_plan;
 
 lc_status lc_variant_plan(const lc_kernel *k, int64_t E, int32_t N, int32_t F, const lc_variant *v,

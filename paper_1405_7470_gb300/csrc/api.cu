@@ -515,6 +515,89 @@ static bool parse_instruction(const char *text, Kernel &K, std::string &why)
     return true;
 }
 
+// Parse the volume derivative with per-element geometric factors,
+//   "out[d,e,i] = sum((f,j), G[e,d,f]*D[f,i,j]*u[e,j])"
+// (the three factors in any order): the reference derivatives sum_j D[f,i,j] u[e,j] mapped
+// to physical coordinate d by the element's factors G[e,d,:]; d and f share the bound F.
+static bool parse_geo_instruction(const char *text, Kernel &K, std::string &why)
+{
+    std::vector<Tok> toks;
+    if (!tokenize(text, toks)) {
+        why = "instruction: bad character";
+        return false;
+    }
+    Cursor c(toks);
+    Access lhs, fac[3];
+    std::string sum, r1, r2;
+    if (!parse_access(c, lhs) || !c.op("=") || !c.id(sum) || sum != "sum" || !c.op("(") || !c.op("(") ||
+        !c.id(r1) || !c.op(",") || !c.id(r2) || !c.op(")") || !c.op(",")) {
+        why = "instruction: expected 'out[d,e,i] = sum((f,j), ...)'";
+        return false;
+    }
+    if (!parse_access(c, fac[0]) || !c.op("*") || !parse_access(c, fac[1]) || !c.op("*") ||
+        !parse_access(c, fac[2]) || !c.op(")") || !c.end()) {
+        why = "instruction: expected a product of three array accesses";
+        return false;
+    }
+    if (lhs.idx.size() != 3) {
+        why = "instruction: output must be out[d,e,i]";
+        return false;
+    }
+    const std::string d = lhs.idx[0], e = lhs.idx[1], i = lhs.idx[2];
+    Access *G = nullptr, *D = nullptr, *U = nullptr;
+    for (Access &x : fac) {
+        if (x.idx.size() == 2)
+            U = &x;
+        else if (x.idx.size() == 3 && x.idx[0] == e)
+            G = &x;
+        else if (x.idx.size() == 3)
+            D = &x;
+    }
+    if (!G || !D || !U) {
+        why = "instruction: factors must be G[e,d,f], D[f,i,j] and u[e,j]";
+        return false;
+    }
+    std::string f = G->idx[2], j = U->idx[1];
+    if (G->idx != std::vector<std::string>{e, d, f} || D->idx != std::vector<std::string>{f, i, j} ||
+        U->idx != std::vector<std::string>{e, j} ||
+        std::set<std::string>{r1, r2} != std::set<std::string>{f, j}) {
+        why = "instruction: index structure is not out[d,e,i] = sum((f,j), G[e,d,f]*D[f,i,j]*u[e,j])";
+        return false;
+    }
+    std::set<std::string> su = {d, f, e, i, j};
+    if (su.size() != 5 || su != std::set<std::string>(K.inames.begin(), K.inames.end())) {
+        why = "instruction: inames differ from the domain's";
+        return false;
+    }
+    std::set<std::string> names = {lhs.name, G->name, D->name, U->name};
+    if (names.size() != 4) {
+        why = "instruction: arrays must be distinct";
+        return false;
+    }
+    auto bound = [&](const std::string &n) {
+        return K.bounds[std::find(K.inames.begin(), K.inames.end(), n) - K.inames.begin()];
+    };
+    if (bound(d) != bound(f) || bound(i) != bound(j) ||
+        std::set<std::string>{bound(f), bound(e), bound(i)}.size() != 3) {
+        why = "instruction: d and f must share F, i and j must share N, and F, E, N must differ";
+        return false;
+    }
+    K.kind = KIND_GEO;
+    K.out_name = lhs.name;
+    K.g_name = G->name;
+    K.d_name = D->name;
+    K.u_name = U->name;
+    K.d_iname = d;
+    K.f_iname = f;
+    K.e_iname = e;
+    K.i_iname = i;
+    K.j_iname = j;
+    K.F_param = bound(f);
+    K.E_param = bound(e);
+    K.N_param = bound(i);
+    return true;
+}
+
 static bool parse_assumptions(const char *text, Kernel &K, std::string &why)
 {
     if (!text)
@@ -700,7 +783,7 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         return LC_ERR_NO_DEVICE;
 
     if (v->engine != LC_ENGINE_TCGEN05 &&
-        (v->out_buffers != 0 || v->store_rows != 0 || v->slot_ops != 0 || v->mma_order != 0))
+        (v->out_buffers != 0 || v->store_rows != 0 || v->mma_order != 0 || v->a_operand != 0))
         return LC_ERR_INVALID_VARIANT;
     if (v->engine == LC_ENGINE_SIMT) {
         if (v->precision != LC_PREC_FP32 && v->precision != LC_PREC_FP64)
@@ -774,6 +857,14 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         g.grid = (int)grid;
         return LC_OK;
     }
+    const bool geo = K.kind == KIND_GEO;
+    if (geo) {
+        // every operator in one column block (the epilogue mixes all F partial sums of a node);
+        // kernel instances exist for F = 2 and 3; whole-tile staging slots
+        if (v->engine != LC_ENGINE_TCGEN05 || F < 2 || F > 3 || !(v->split_i == 0 || v->split_i == F) ||
+            !(v->store_rows == 0 || v->store_rows == 128))
+            return LC_ERR_INVALID_VARIANT;
+    }
     if (v->engine == LC_ENGINE_TCGEN05) {
         if (v->precision != LC_PREC_BF16 && v->precision != LC_PREC_BF16X3)
             return LC_ERR_INVALID_VARIANT;
@@ -791,9 +882,9 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
             return LC_ERR_INVALID_VARIANT;
         const bool node = v->layout == LC_LAYOUT_NODE_MAJOR;
         const int NT = v->precision == LC_PREC_BF16X3 ? 3 : 1;
-        if (!(v->slot_ops == 0 || v->slot_ops == 1) || (v->slot_ops == 1 && (node || v->store_rows != 128)))
-            return LC_ERR_INVALID_VARIANT;  // one operator per whole-tile slot: element-major, 128-row stores
         if (v->mma_order < 0 || v->mma_order > 2 || (v->mma_order != 0 && NT != 3))
+            return LC_ERR_INVALID_VARIANT;
+        if (v->a_operand < 0 || v->a_operand > 2)
             return LC_ERR_INVALID_VARIANT;
         TcArgs &t = r.tc;
         memset(&t, 0, sizeof t);
@@ -817,22 +908,23 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         // rows per element-major bulk store: whole tiles of every operator of the block for
         // small N (few, large stores), else 32-row pieces of one operator at a time (the
         // stores stream, and the staging slots stay small)
-        t.store_quarters = v->store_rows ? v->store_rows / 32 : (N <= 48 ? 4 : 1);
-        t.slot_ops = v->slot_ops;
-        auto plan = [&](int G, TcArgs &q) -> bool {
+        t.store_quarters = geo ? 4 : (v->store_rows ? v->store_rows / 32 : (N <= 48 ? 4 : 1));
+        // a_tm: A terms in tensor memory (one accumulator region each: BF16, or BF16X3 with the
+        // hi*hi products last), else in shared memory
+        auto plan = [&](int G, TcArgs &q, bool a_tm) -> bool {
             q.G = G;
             // operator padding: 16 columns (16-column epilogue chunks), or 8 where that lets
             // the BF16X3 terms stack (2 CBp <= 256) or the block fit (CBp <= 256) at all
             auto cbp = [&](int np) { return (G * np + 15) / 16 * 16; };
             const int np16 = (N + 15) / 16 * 16, np8 = (N + 7) / 8 * 8;
-            const bool want_stack = NT == 3 && v->mma_order != 2;
+            const bool want_stack = NT == 3 && v->mma_order != 2 && !a_tm;
             if (want_stack && 2 * cbp(np16) > 256 && 2 * cbp(np8) <= 256)
                 q.Np = np8;
-            else if (NT == 3 && !want_stack && cbp(np8) < cbp(np16))
+            else if ((NT == 3 || a_tm) && !want_stack && cbp(np8) < cbp(np16))
                 q.Np = np8;  // one accumulator region: the narrowest padding (smaller B, fewer columns)
             else
                 q.Np = cbp(np16) <= 256 ? np16 : np8;
-            q.chunk = q.Np % 16 == 0 ? 16 : 8;
+            q.chunk = q.Np % 16 == 0 && !geo ? 16 : 8;
             q.CB = G * q.Np;
             q.CBp = cbp(q.Np);
             if (q.CBp > 256)
@@ -843,14 +935,22 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
             q.tmem_cols = 32;
             while (q.tmem_cols < (q.stack ? 2 : 1) * q.CBp)
                 q.tmem_cols *= 2;
+            q.a_tmem = a_tm;
+            q.a_cols = a_tm ? NT * ((N + 15) / 16 * 16) / 2 : 0;
+            const int need = 2 * q.tmem_cols + q.abufs * q.a_cols;
+            if (need > 512)
+                return false;
+            q.tmem_alloc = 32;
+            while (q.tmem_alloc < need)
+                q.tmem_alloc *= 2;
             size_t off = 0;
-            off += (size_t)NT * q.nkb * q.CBp * W;          // B terms
-            off += (size_t)q.abufs * NT * q.nkb * 128 * W;  // A terms
+            off += (size_t)NT * q.nkb * q.CBp * W;                       // B terms
+            off += a_tm ? 0 : (size_t)q.abufs * NT * q.nkb * 128 * W;  // A terms
             q.off_stage = (unsigned)off;
             off += (size_t)q.stages * 128 * N * 4;
             q.off_out = (unsigned)off;
             if (!node)  // staging slots: every operator of the block (4 quarters per store), else one
-                off += (size_t)q.obufs * (q.store_quarters == 4 && q.slot_ops != 1 ? G : 1) * 128 * N * 4;
+                off += (size_t)q.obufs * (q.store_quarters == 4 ? G : 1) * 128 * N * 4;
             off = (off + 15) / 16 * 16;
             q.off_bar = (unsigned)off;
             off += 1024;  // 10 mbarriers, TMEM address, abort flag; 2 x 2 x 16 A-block mbarriers
@@ -867,19 +967,26 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         static const int combos[][2] = {{3, 2}, {2, 2}, {4, 1}, {3, 1}, {2, 1}, {1, 2}, {1, 1}};  // {slots, abufs}
         const int ncombos = (int)(sizeof combos / sizeof combos[0]);
         bool found = false;
-        const int g_hi = v->split_i ? v->split_i : F, g_lo = v->split_i ? v->split_i : 1;
+        const int g_hi = v->split_i ? v->split_i : F, g_lo = geo ? F : (v->split_i ? v->split_i : 1);
+        // the most operators per CTA first; for each, A in tensor memory (when asked, or by
+        // default), then in shared memory
         for (int g = g_hi; g >= g_lo && !found; --g)
-            for (int c = 0; c < ncombos && !found; ++c) {
-                TcArgs q = t;
-                q.obufs = node ? 1 : combos[c][0];
-                q.abufs = combos[c][1];
-                if (!node && v->out_buffers && q.obufs != v->out_buffers)
+            for (int pass = 0; pass < 2 && !found; ++pass) {
+                const bool a_tm = pass == 0;
+                if ((a_tm && v->a_operand == 1) || (!a_tm && v->a_operand == 2) || (a_tm && v->mma_order == 1))
                     continue;
-                if (plan(g, q)) {
-                    t = q;
-                    found = true;
+                for (int c = 0; c < ncombos && !found; ++c) {
+                    TcArgs q = t;
+                    q.obufs = node ? 1 : combos[c][0];
+                    q.abufs = combos[c][1];
+                    if (!node && v->out_buffers && q.obufs != v->out_buffers)
+                        continue;
+                    if (plan(g, q, a_tm)) {
+                        t = q;
+                        found = true;
+                    }
                 }
-            }
+        }
         if (!found)
             return LC_ERR_INVALID_VARIANT;
         const int G = t.G;
@@ -963,8 +1070,16 @@ lc_status lc_kernel_create(const char *domain, const char *instructions, const c
         return LC_ERR_INVALID_ARGUMENT;
     Kernel K;
     std::string why;
-    if (!parse_domain(domain, K, why) || !parse_instruction(instructions, K, why) ||
-        !parse_assumptions(assumptions, K, why))
+    if (!parse_domain(domain, K, why))
+        return LC_ERR_UNSUPPORTED;
+    // the instruction forms, in turn: the contraction, the volume derivative with geometric factors
+    const Kernel base = K;
+    bool parsed = parse_instruction(instructions, K, why);
+    if (!parsed) {
+        K = base;
+        parsed = parse_geo_instruction(instructions, K, why);
+    }
+    if (!parsed || !parse_assumptions(assumptions, K, why))
         return LC_ERR_UNSUPPORTED;
     K.domain_text = domain;
     K.insn_text = instructions;
@@ -1135,6 +1250,8 @@ lc_status lc_variant_plan(const lc_kernel *kh, int64_t E, int32_t N, int32_t F, 
         q.out_slots = r.layout == LC_LAYOUT_ELEM_MAJOR ? t.obufs : 0;
         q.store_rows = r.layout == LC_LAYOUT_ELEM_MAJOR ? 32 * t.store_quarters : 0;
         q.mma_per_tile = (nt == 1 ? 1 : (t.stack ? 5 : 6)) * (q.k_mma / 16);
+        q.a_in_tmem = t.a_tmem;
+        q.tmem_cols = t.tmem_alloc;
     } else {
         q.grid = r.g.grid;
         q.threads = r.g.threads;
@@ -1234,6 +1351,8 @@ lc_status lc_contract(const lc_kernel *kh, const lc_variant *v, const void *D, c
 {
     if (!kh || !v)
         return LC_ERR_INVALID_ARGUMENT;
+    if (kh->k.kind != KIND_CONTRACT)
+        return LC_ERR_UNSUPPORTED;
     // an empty batch may come with null u / out (zero-size allocations)
     if (!D || (E > 0 && (!u || !out)))
         return LC_ERR_INVALID_ARGUMENT;
@@ -1310,6 +1429,45 @@ lc_status lc_contract(const lc_kernel *kh, const lc_variant *v, const void *D, c
         return warp_launch(a, r.layout, r.precision == LC_PREC_FP64, r.g.grid, r.g.threads, s);
     }
     return LC_ERR_INVALID_VARIANT;
+}
+
+lc_status lc_contract_geo(const lc_kernel *kh, const lc_variant *v, const void *D, const void *u, const void *r,
+                          void *out, int64_t E, int32_t N, int32_t F, void *stream)
+{
+    if (!kh || !v)
+        return LC_ERR_INVALID_ARGUMENT;
+    if (kh->k.kind != KIND_GEO)
+        return LC_ERR_UNSUPPORTED;
+    if (!D || (E > 0 && (!u || !out || !r)))
+        return LC_ERR_INVALID_ARGUMENT;
+    if (!aligned16(D) || !aligned16(u) || !aligned16(out) || !aligned16(r))
+        return LC_ERR_MISALIGNED;
+    Resolved rs;
+    lc_status st = resolve(kh->k, E, N, F, v, rs, true);
+    if (st != LC_OK)
+        return st;
+    {
+        // out must not overlap its inputs
+        const uintptr_t o0 = (uintptr_t)out, o1 = o0 + (size_t)F * E * N * 4;
+        const uintptr_t in[3][2] = {{(uintptr_t)u, (uintptr_t)u + (size_t)E * N * 4},
+                                    {(uintptr_t)D, (uintptr_t)D + (size_t)F * N * N * 4},
+                                    {(uintptr_t)r, (uintptr_t)r + (size_t)E * F * F * 4}};
+        for (auto &x : in)
+            if (o0 < x[1] && x[0] < o1)
+                return LC_ERR_INVALID_ARGUMENT;
+    }
+    int major = 0, minor = 0;
+    if (current_cc(&major, &minor) != 0 || major != 10 || minor != 3)
+        return LC_ERR_NO_DEVICE;
+    if (E == 0)
+        return LC_OK;
+    TcArgs a = rs.tc;
+    a.D = static_cast<const float *>(D);
+    a.u = static_cast<const float *>(u);
+    a.out = static_cast<float *>(out);
+    a.r = static_cast<const float *>(r);
+    a.err = error_word();
+    return tc_geo_launch(a, rs.layout, rs.precision == LC_PREC_BF16X3 ? 3 : 1, rs.tc_grid, (cudaStream_t)stream);
 }
 
 namespace lc {

@@ -18,7 +18,12 @@ struct Assumption {
     long long k;
 };
 
+// What the instruction computes (each kind has its own entry point).
+enum KernelKind { KIND_CONTRACT = 0, KIND_GEO = 1, KIND_ELEMENTWISE = 2 };
+
 struct Kernel {
+    int kind = KIND_CONTRACT;
+    std::string g_name, d_iname;      // KIND_GEO: geometric-factor array G[e,d,f], physical-derivative iname
     std::vector<std::string> inames;  // as written in the domain
     std::vector<std::string> bounds;  // parameter bounding each iname
     std::string out_name, d_name, u_name;
@@ -80,6 +85,7 @@ struct TcArgs {
     const float *D;
     const float *u;
     float *out;
+    const float *r;  // volume derivative: per-element geometric factors (null for the contraction)
     long long E;
     int N, F;
     int G;          // operators per column block
@@ -90,13 +96,15 @@ struct TcArgs {
     int Kp, KB, nkb;  // K padded to the block width, K-block width (16/32/64 -> 32/64/128-byte swizzle), blocks
     int stack;      // BF16X3 with two B terms stacked along N (2 * CBp <= 256): 5 MMAs per K step, not 6
     int tmem_cols;  // columns per accumulator (power of two >= CBp, or >= 2 * CBp when stacked)
+    int a_tmem;     // 1: the A terms live in tensor memory after the two accumulators
+    int a_cols;     // tensor-memory columns per A buffer (NT terms x K/2 packed bf16 pairs)
+    int tmem_alloc; // tensor-memory columns allocated (power of two >= 32)
     int stages;     // u stage buffers (1 or 2)
     int threads_per_row;       // epilogue threads per tile row
     int conv_threads_per_row;  // conversion threads per tile row (CTA = 128 * (both) + 64 threads)
     int abufs;      // A-operand buffers (1 or 2)
     int obufs;      // element-major output staging slots of one operator-tile (1 to 4)
     int store_quarters;  // element-major: TMEM lane quarters (32 rows each) per bulk store: 1, 2 or 4
-    int slot_ops;   // element-major, 4 quarters per store: 1 = one operator per staging slot, else all G
     long long ntiles;
     int bulk_u, bulk_store;
     unsigned int *err;
@@ -104,6 +112,7 @@ struct TcArgs {
 };
 
 lc_status tc_launch(const TcArgs &a, int layout, int nterms, int grid, cudaStream_t s);
+lc_status tc_geo_launch(const TcArgs &a, int layout, int nterms, int grid, cudaStream_t s);
 
 // Grouped launch: per-group SIMT arguments, contiguous tile ranges, ranges per CTA.
 struct GroupSeg {

@@ -44,7 +44,7 @@ class lc_variant(ctypes.Structure):
         (n, ctypes.c_int32) for n in (
             "engine", "layout", "precision", "tile_e", "elems_per_thread", "split_i", "unroll",
             "prefetch_smem", "tail_free", "stages", "ctas_per_sm", "out_buffers", "store_rows", "max_ctas",
-            "slot_ops", "mma_order")
+            "mma_order", "a_operand")
     ]
 
 
@@ -53,7 +53,7 @@ class lc_plan(ctypes.Structure):
                 ("smem_bytes", ctypes.c_int32), ("tiles", ctypes.c_int64)] + [
         (n, ctypes.c_int32) for n in (
             "column_blocks", "ops_per_block", "k_mma", "k_block", "cols_per_op", "mma_n", "stacked", "a_buffers",
-            "out_slots", "store_rows", "mma_per_tile")
+            "out_slots", "store_rows", "mma_per_tile", "a_in_tmem", "tmem_cols")
     ]
 
 
@@ -171,7 +171,7 @@ class Kernel:
 
 def Variant(engine="simt", layout="elem", precision="fp32", tile_e=64, elems_per_thread=4, split_i=8,
             unroll=4, prefetch_smem=1, tail_free=0, stages=1, ctas_per_sm=0, out_buffers=0,
-            store_rows=0, max_ctas=0, slot_ops=0, mma_order=0) -> lc_variant:
+            store_rows=0, max_ctas=0, mma_order=0, a_operand=0) -> lc_variant:
     v = lc_variant()
     v.struct_size = ctypes.sizeof(lc_variant)
     v.engine = ENGINE[engine] if isinstance(engine, str) else engine
@@ -180,7 +180,7 @@ def Variant(engine="simt", layout="elem", precision="fp32", tile_e=64, elems_per
     v.tile_e, v.elems_per_thread, v.split_i, v.unroll = tile_e, elems_per_thread, split_i, unroll
     v.prefetch_smem, v.tail_free, v.stages, v.ctas_per_sm = prefetch_smem, tail_free, stages, ctas_per_sm
     v.out_buffers, v.store_rows, v.max_ctas = out_buffers, store_rows, max_ctas
-    v.slot_ops, v.mma_order = slot_ops, mma_order
+    v.mma_order, v.a_operand = mma_order, a_operand
     return v
 
 
@@ -189,8 +189,8 @@ def variant_dict(v: lc_variant) -> dict:
     return dict(engine=inv(ENGINE, v.engine), layout=inv(LAYOUT, v.layout), precision=inv(PRECISION, v.precision),
                 tile_e=v.tile_e, elems_per_thread=v.elems_per_thread, split_i=v.split_i, unroll=v.unroll,
                 prefetch_smem=v.prefetch_smem, tail_free=v.tail_free, stages=v.stages, ctas_per_sm=v.ctas_per_sm,
-                out_buffers=v.out_buffers, store_rows=v.store_rows, max_ctas=v.max_ctas, slot_ops=v.slot_ops,
-                mma_order=v.mma_order)
+                out_buffers=v.out_buffers, store_rows=v.store_rows, max_ctas=v.max_ctas, mma_order=v.mma_order,
+                a_operand=v.a_operand)
 
 
 def variant_default(kernel: Kernel, E: int, N: int, F: int, layout="elem", precision="fp32") -> lc_variant:

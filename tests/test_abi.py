@@ -156,14 +156,24 @@ def test_variant_plan_reports_the_resolved_launch(lib):
     the argument checks (host only; without a GPU a 148-SM part is assumed)."""
     k = lc.Kernel()
     v = lc.Variant(engine="tcgen05", layout="elem", precision="bf16x3", tile_e=128, elems_per_thread=64,
-                   split_i=0, unroll=4, prefetch_smem=1, stages=1, store_rows=128)
+                   split_i=0, unroll=4, prefetch_smem=1, stages=1, store_rows=128, mma_order=1)
     p = lc.variant_plan(k, 1 << 21, 35, 3, v)
     assert p["tiles"] == (1 << 21) // 128 and p["column_blocks"] == 1 and p["ops_per_block"] == 3
     assert p["k_mma"] == 48 and p["k_block"] == 64
     # N = 35 pads to 40 columns per operator so that the D terms stack: 5 MMAs per K step
     assert p["cols_per_op"] == 40 and p["mma_n"] == 128 and p["stacked"] == 1 and p["mma_per_tile"] == 15
     assert p["threads"] == 128 * (4 + 2) + 64 and p["store_rows"] == 128
-    assert 0 < p["smem_bytes"] <= 232448
+    assert 0 < p["smem_bytes"] <= 232448 and p["a_in_tmem"] == 0 and p["tmem_cols"] == 512
+    # the A terms in tensor memory: one accumulator region (hi*hi last, 6 MMAs per K step), two
+    # accumulators of 128 columns and two A buffers of 3 x 24 columns; no A in shared memory
+    v.mma_order, v.a_operand, v.stages = 0, 2, 2
+    q = lc.variant_plan(k, 1 << 21, 35, 3, v)
+    assert q["a_in_tmem"] == 1 and q["stacked"] == 0 and q["mma_per_tile"] == 18 and q["a_buffers"] == 2
+    assert q["cols_per_op"] == 40 and q["mma_n"] == 128 and q["tmem_cols"] == 512
+    assert q["smem_bytes"] < p["smem_bytes"]
+    v.mma_order = 1  # the stacked order cannot keep A in tensor memory
+    assert lib.lc_variant_validate(k.handle, 1 << 21, 35, 3, ctypes.byref(v)) == 3
+    v.mma_order, v.a_operand, v.stages = 1, 0, 1
     s = lc.variant_plan(k, 1 << 21, 35, 3, lc.variant_default(k, 1 << 21, 35, 3, "elem", "fp32"))
     assert s["mma_per_tile"] == 0 and s["grid"] > 0 and s["tiles"] > 0
     bad = lc.lc_plan()
