@@ -214,6 +214,92 @@ lc_status lc_contract(const lc_kernel *k, const lc_variant *v, const void *D_dev
                       const void *u_dev, void *out_dev, int64_t E, int32_t N, int32_t F,
                       void *stream);
 
+/* ------------------------------------------------------------------------- */
+/* General front end: elementwise instructions (Section 2.1, 2.4).            */
+/* ------------------------------------------------------------------------- */
+/*
+ * A kernel whose domain has one or two inames, e.g. "{ [i]: 0<=i<n }" or
+ * "{ [i,j]: 0<=i<n and 0<=j<m }", and whose instruction is one assignment
+ *     out[i] = expr        or        out[i,j] = expr
+ * with expr built from +, -, *, / (usual precedence, left to right), unary minus,
+ * parentheses, decimal literals, scalar parameters (names without an index) and array
+ * accesses indexed by the domain's inames in domain order (a subset of them: "c[j]" inside
+ * [i,j] is broadcast along i).  The saxpy of Table 1 is "z[i] = a*x[i] + y[i]".
+ *
+ * lc_elementwise generates a CUDA kernel for the instruction (once per instruction,
+ * unroll factor and edge handling; compiled for this GPU at run time with NVRTC and cached
+ * for the life of the process) and launches it.  The transformations of Section 2.4 are
+ * the descriptor's fields: split_iname of the innermost iname into tiles (256 x 4 x unroll
+ * elements for one iname; 256 columns x 4 x unroll rows for two), bulk tiles with no guard
+ * and 16-byte vectors (elems_per_thread 4; 1 = scalar code throughout), separate edge code
+ * for tiles cut by one bound and corner code for tiles cut by both, chosen per tile at run
+ * time; tail_free = 1 drops the edge code when an assumption "n mod tile = 0" holds (one
+ * iname only).  Every operation is one IEEE binary32 operation rounded to nearest, never
+ * contracted into a fused multiply-add: the result is the plain loop's, bit for bit.
+ * Descriptor: engine SIMT, precision FP32, element-major layout, unroll 1/2/4/8,
+ * elems_per_thread 1 or 4, ctas_per_sm (0 = 4), max_ctas, tail_free; every other field 0
+ * (stages 1); tile_e 0 or the tile above.  lc_variant_default gives unroll 4, vectors,
+ * 4 CTAs per SM; lc_variant_validate and lc_variant_plan take the extents of the first and
+ * second iname as E and N (N ignored for one iname) and F = 1.
+ */
+
+/* Argument counts of a kernel: arrays (elementwise: the output, then the inputs in order
+ * of first appearance; contraction: out, D, u; volume derivative: out, D, u, G), scalar
+ * parameters (in order of first appearance) and domain inames. */
+lc_status lc_kernel_signature(const lc_kernel *k, int32_t *n_arrays, int32_t *n_params, int32_t *n_dims);
+
+/* The name of argument `index` of kind `what` (0 array, 1 scalar parameter, 2 the bound
+ * of iname `index`), NUL-terminated in buf[cap].  Errors: LC_ERR_INVALID_ARGUMENT (no such
+ * argument), LC_ERR_BUFFER_TOO_SMALL (truncated). */
+lc_status lc_kernel_arg_name(const lc_kernel *k, int32_t what, int32_t index, char *buf, size_t cap);
+
+/* The CUDA source lc_elementwise would compile for (v, extents), NUL-terminated in
+ * buf[cap]; *needed = its length + 1.  Nothing is compiled or launched. */
+lc_status lc_elementwise_source(const lc_kernel *k, const lc_variant *v, const int64_t *extents, char *buf,
+                                size_t cap, size_t *needed);
+
+/*
+ * Enqueue the elementwise instruction over the domain on `stream`.
+ *   extents     one per iname, in domain order (>= 0)
+ *   arrays_dev  one device pointer per array in signature order (arrays_dev[0] = the
+ *               output); float, dense row-major over the inames each array is indexed by;
+ *               4-byte aligned, 16-byte aligned for the vector code (elems_per_thread 4 and,
+ *               with two inames, the inner extent a multiple of 4); the output must not
+ *               overlap an input
+ *   params      one value per scalar parameter, in signature order (rounded to binary32)
+ * The first call for a new instruction compiles it (NVRTC; synchronous, tens of
+ * milliseconds): make it before any stream capture.
+ * Errors: LC_ERR_INVALID_ARGUMENT, LC_ERR_INVALID_VARIANT, LC_ERR_ASSUMPTION,
+ * LC_ERR_MISALIGNED, LC_ERR_NO_DEVICE, LC_ERR_UNSUPPORTED (not an elementwise kernel, or
+ * no run-time compiler on this machine), LC_ERR_CUDA.
+ */
+lc_status lc_elementwise(const lc_kernel *k, const lc_variant *v, const int64_t *extents, void *const *arrays_dev,
+                         const double *params, void *stream);
+
+/*
+ * The volume derivative with per-element geometric factors: the dG FEM volume workload of
+ * Table 1 with the chain rule applied inside the kernel,
+ *
+ *     out[d, e, i] = sum_f r[e, d, f] * sum_j D[f, i, j] * u[e, j]      d, f < F
+ *
+ * stated to lc_kernel_create as the domain { [d,f,e,i,j] : 0<=d<F and 0<=f<F and 0<=e<E and
+ * 0<=i,j<N } and the instruction "out[d,e,i] = sum((f,j), G[e,d,f]*D[f,i,j]*u[e,j])" (the
+ * three factors in any order).  The F reference derivatives of a node stay in tensor memory;
+ * the epilogue mixes them with the element's F x F factors (FP32) before the one store, so
+ * the output is written once instead of twice, and the F partial results never reach memory.
+ * Tensor-core engine only (LC_PREC_BF16, or LC_PREC_BF16X3 for FP32-level accuracy), F = 2
+ * or 3, every operator in one column block (split_i 0 or F), element-major store_rows 0 or
+ * 128.
+ *   D_dev    [F][N][N] float       u_dev  layout per v->layout
+ *   r_dev    element-major [E][F][F] (r[(e*F + d)*F + f]); node-major [F][F][E]
+ *   out_dev  element-major [F][E][N], node-major [F][N][E] (d in place of f); must not
+ *            overlap the inputs
+ * Errors: as lc_contract; LC_ERR_UNSUPPORTED when the kernel is not of this form (and
+ * lc_contract returns it for kernels of this form).
+ */
+lc_status lc_contract_geo(const lc_kernel *k, const lc_variant *v, const void *D_dev, const void *u_dev,
+                          const void *r_dev, void *out_dev, int64_t E, int32_t N, int32_t F, void *stream);
+
 /*
  * The contraction on host arrays: copies D and u from host to the caller's device
  * buffers, contracts, and copies out back to the host.  Large batches are cut into up to

@@ -18,9 +18,7 @@
 
 #include "lc_internal.h"
 
-struct lc_kernel {
-    lc::Kernel k;
-};
+
 
 namespace lc {
 
@@ -106,9 +104,10 @@ int current_cc(int *major, int *minor)
 // ------------------------------------------------------------------ tokenizer
 
 struct Tok {
-    enum Kind { ID, INT, OP, END } kind;
+    enum Kind { ID, INT, NUM, OP, END } kind;
     std::string s;
     long long v = 0;
+    double d = 0.0;  // NUM: a literal with a fraction or an exponent
 };
 
 static bool tokenize(const char *text, std::vector<Tok> &out)
@@ -128,17 +127,37 @@ static bool tokenize(const char *text, std::vector<Tok> &out)
             out.push_back({Tok::ID, std::string(b, p)});
             continue;
         }
-        if (isdigit(c)) {
-            long long v = 0;
-            while (isdigit((unsigned char)*p)) {
-                if (v > (1LL << 50))
-                    return false;
-                v = v * 10 + (*p - '0');
+        if (isdigit(c) || (c == '.' && isdigit((unsigned char)p[1]))) {
+            // an integer, or a decimal literal with a fraction and/or an exponent
+            const char *b = p;
+            bool real = false;
+            while (isdigit((unsigned char)*p))
                 ++p;
+            if (*p == '.') {
+                real = true;
+                ++p;
+                while (isdigit((unsigned char)*p))
+                    ++p;
             }
-            Tok t{Tok::INT, ""};
-            t.v = v;
-            out.push_back(t);
+            if ((*p == 'e' || *p == 'E') &&
+                (isdigit((unsigned char)p[1]) || ((p[1] == '-' || p[1] == '+') && isdigit((unsigned char)p[2])))) {
+                real = true;
+                p += 2;
+                while (isdigit((unsigned char)*p))
+                    ++p;
+            }
+            const std::string lit(b, p);
+            if (real) {
+                Tok t{Tok::NUM, lit};
+                t.d = strtod(lit.c_str(), nullptr);
+                out.push_back(t);
+            } else {
+                if (lit.size() > 15)
+                    return false;
+                Tok t{Tok::INT, lit};
+                t.v = strtoll(lit.c_str(), nullptr, 10);
+                out.push_back(t);
+            }
             continue;
         }
         if ((p[0] == '<' || p[0] == '>' || p[0] == '=') && p[1] == '=') {
@@ -146,7 +165,7 @@ static bool tokenize(const char *text, std::vector<Tok> &out)
             p += 2;
             continue;
         }
-        if (strchr("{}[]():,<>=*-+", c)) {
+        if (strchr("{}[]():,<>=*-+/", c)) {
             out.push_back({Tok::OP, std::string(1, (char)c)});
             ++p;
             continue;
@@ -598,6 +617,188 @@ static bool parse_geo_instruction(const char *text, Kernel &K, std::string &why)
     return true;
 }
 
+// Elementwise instruction "lhs[i0, i1] = expr" over a domain of one or two inames: expr is
+// built from +, -, *, / (left-associative, * and / binding tighter), unary minus,
+// parentheses, decimal literals, scalar parameters (unindexed names) and array accesses
+// indexed by inames in domain order (a subset of them: broadcast along the others).
+struct EwParser {
+    Cursor &c;
+    Kernel &K;
+    std::string why;
+    EwParser(Cursor &cc, Kernel &kk) : c(cc), K(kk) {}
+    int add(EwNode n)
+    {
+        K.ew.nodes.push_back(n);
+        return (int)K.ew.nodes.size() - 1;
+    }
+    int primary()
+    {
+        if (c.op("(")) {
+            int e = expr();
+            if (e < 0 || !c.op(")"))
+                return -1;
+            return e;
+        }
+        if (c.op("-")) {
+            int a = primary();
+            if (a < 0)
+                return -1;
+            EwNode n{EW_NEG};
+            n.a = a;
+            return add(n);
+        }
+        const Tok &t = c.peek();
+        if (t.kind == Tok::INT || t.kind == Tok::NUM) {
+            EwNode n{EW_CONST};
+            n.val = t.kind == Tok::INT ? (double)t.v : t.d;
+            ++c.i;
+            return add(n);
+        }
+        std::string name;
+        if (!c.id(name)) {
+            why = "instruction: expected an operand";
+            return -1;
+        }
+        if (std::find(K.inames.begin(), K.inames.end(), name) != K.inames.end()) {
+            why = "instruction: inames are indices, not values";
+            return -1;
+        }
+        if (!c.op("[")) {  // a scalar parameter
+            auto it = std::find(K.ew.params.begin(), K.ew.params.end(), name);
+            EwNode n{EW_PARAM};
+            n.arg = (int)(it - K.ew.params.begin());
+            if (it == K.ew.params.end())
+                K.ew.params.push_back(name);
+            return add(n);
+        }
+        std::vector<int> dims;
+        std::string ix;
+        while (c.id(ix)) {
+            auto it = std::find(K.inames.begin(), K.inames.end(), ix);
+            if (it == K.inames.end()) {
+                why = "instruction: index is not an iname";
+                return -1;
+            }
+            dims.push_back((int)(it - K.inames.begin()));
+            if (!c.op(","))
+                break;
+        }
+        if (!c.op("]") || dims.empty()) {
+            why = "instruction: bad array access";
+            return -1;
+        }
+        for (size_t q = 1; q < dims.size(); ++q)
+            if (dims[q] <= dims[q - 1]) {
+                why = "instruction: indices must follow the domain order";
+                return -1;
+            }
+        int k = -1;
+        for (size_t q = 0; q < K.ew.arrays.size(); ++q)
+            if (K.ew.arrays[q].name == name)
+                k = (int)q;
+        if (k == 0) {
+            why = "instruction: the output cannot be read";
+            return -1;
+        }
+        if (k > 0 && K.ew.arrays[k].dims != dims) {
+            why = "instruction: one array, two index lists";
+            return -1;
+        }
+        if (k < 0) {
+            K.ew.arrays.push_back({name, dims});
+            k = (int)K.ew.arrays.size() - 1;
+        }
+        EwNode n{EW_LOAD};
+        n.arg = k;
+        return add(n);
+    }
+    int term()
+    {
+        int a = primary();
+        while (a >= 0 && (c.peek().kind == Tok::OP && (c.peek().s == "*" || c.peek().s == "/"))) {
+            const bool mul = c.peek().s == "*";
+            ++c.i;
+            int b = primary();
+            if (b < 0)
+                return -1;
+            EwNode n{mul ? EW_MUL : EW_DIV};
+            n.a = a;
+            n.b = b;
+            a = add(n);
+        }
+        return a;
+    }
+    int expr()
+    {
+        int a = term();
+        while (a >= 0 && (c.peek().kind == Tok::OP && (c.peek().s == "+" || c.peek().s == "-"))) {
+            const bool plus = c.peek().s == "+";
+            ++c.i;
+            int b = term();
+            if (b < 0)
+                return -1;
+            EwNode n{plus ? EW_ADD : EW_SUB};
+            n.a = a;
+            n.b = b;
+            a = add(n);
+        }
+        return a;
+    }
+};
+
+static bool parse_elementwise(const char *text, Kernel &K, std::string &why)
+{
+    if (K.inames.empty() || K.inames.size() > 2) {
+        why = "instruction: elementwise domains have one or two inames";
+        return false;
+    }
+    std::vector<Tok> toks;
+    if (!tokenize(text, toks)) {
+        why = "instruction: bad character";
+        return false;
+    }
+    Cursor c(toks);
+    Access lhs;
+    if (!parse_access(c, lhs) || !c.op("=") || lhs.idx != K.inames) {
+        why = "instruction: the output must be indexed by every iname, in domain order";
+        return false;
+    }
+    K.ew = Elementwise();
+    std::vector<int> all;
+    for (size_t d = 0; d < K.inames.size(); ++d)
+        all.push_back((int)d);
+    K.ew.arrays.push_back({lhs.name, all});
+    EwParser P(c, K);
+    K.ew.root = P.expr();
+    if (K.ew.root < 0 || !c.end()) {
+        why = P.why.empty() ? "instruction: trailing text" : P.why;
+        return false;
+    }
+    if (K.ew.nodes.size() > 256 || K.ew.arrays.size() > 17 || K.ew.params.size() > 16) {
+        why = "instruction: expression too large";
+        return false;
+    }
+    std::set<std::string> bnd(K.bounds.begin(), K.bounds.end());
+    if (bnd.size() != K.bounds.size()) {
+        why = "instruction: each iname needs its own bound";
+        return false;
+    }
+    for (const auto &p : K.ew.params) {
+        if (bnd.count(p) || std::find(K.inames.begin(), K.inames.end(), p) != K.inames.end()) {
+            why = "instruction: a parameter shadows a bound or an iname";
+            return false;
+        }
+        for (const auto &a : K.ew.arrays)
+            if (a.name == p) {
+                why = "instruction: one name used as an array and as a scalar";
+                return false;
+            }
+    }
+    K.kind = KIND_ELEMENTWISE;
+    K.out_name = lhs.name;
+    return true;
+}
+
 static bool parse_assumptions(const char *text, Kernel &K, std::string &why)
 {
     if (!text)
@@ -613,6 +814,8 @@ static bool parse_assumptions(const char *text, Kernel &K, std::string &why)
     std::set<std::string> params = {K.E_param, K.N_param};
     if (!K.F_param.empty())
         params.insert(K.F_param);
+    if (K.kind == KIND_ELEMENTWISE)
+        params = std::set<std::string>(K.bounds.begin(), K.bounds.end());
     for (;;) {
         Assumption a;
         if (!c.id(a.param) || !params.count(a.param)) {
@@ -1079,6 +1282,10 @@ lc_status lc_kernel_create(const char *domain, const char *instructions, const c
         K = base;
         parsed = parse_geo_instruction(instructions, K, why);
     }
+    if (!parsed) {
+        K = base;
+        parsed = parse_elementwise(instructions, K, why);
+    }
     if (!parsed || !parse_assumptions(assumptions, K, why))
         return LC_ERR_UNSUPPORTED;
     K.domain_text = domain;
@@ -1117,12 +1324,80 @@ lc_status lc_kernel_print(const lc_kernel *kh, const lc_variant *v, char *buf, s
     const char *E = K.E_param.c_str(), *N = K.N_param.c_str();
     std::string s;
     const char *rule = "------------------------------------------------------\n";
+    const bool geo = K.kind == KIND_GEO;
+    if (K.kind == KIND_ELEMENTWISE) {
+        const bool two = K.inames.size() == 2;
+        s += rule;
+        s += "KERNEL: elementwise\n";
+        s += rule;
+        s += "ARGUMENTS:\n";
+        for (size_t k = 0; k < K.ew.arrays.size(); ++k) {
+            const EwArray &A = K.ew.arrays[k];
+            std::string shape, tags;
+            for (size_t q = 0; q < A.dims.size(); ++q) {
+                shape += (q ? ", " : "") + K.bounds[A.dims[q]];
+                tags += q ? ", stride:1" : (A.dims.size() == 2 ? "stride:" + K.bounds[A.dims[1]] : "stride:1");
+            }
+            appendf(s, "%s: GlobalArg, type: float32, shape: (%s), dim_tags: (%s)%s\n", A.name.c_str(), shape.c_str(),
+                    tags.c_str(), k == 0 ? ", output" : "");
+        }
+        for (const auto &p : K.ew.params)
+            appendf(s, "%s: ValueArg, type: float32\n", p.c_str());
+        for (const auto &b : K.bounds)
+            appendf(s, "%s: ValueArg, type: int64\n", b.c_str());
+        s += rule;
+        s += "DOMAINS:\n";
+        std::string names, cons, params;
+        for (size_t k = 0; k < K.inames.size(); ++k) {
+            names += (k ? ", " : "") + K.inames[k];
+            params += (k ? ", " : "") + K.bounds[k];
+            cons += (k ? " and " : "") + std::string("0 <= ") + K.inames[k] + " < " + K.bounds[k];
+        }
+        appendf(s, "[%s] -> { [%s] : %s }\n", params.c_str(), names.c_str(), cons.c_str());
+        if (!K.assumptions.empty()) {
+            s += rule;
+            appendf(s, "ASSUMPTIONS: %s\n", K.assumptions_text.c_str());
+        }
+        s += rule;
+        s += "INSTRUCTIONS:\n";
+        appendf(s, "[%s] %s\n", names.c_str(), K.insn_text.c_str());
+        if (v && v->struct_size == sizeof(lc_variant)) {
+            s += rule;
+            s += "TRANSFORMATIONS:\n";
+            const std::string &in = K.inames.back();
+            const int tile = two ? 256 : 1024 * v->unroll;
+            appendf(s, "split_iname(%s, %d): bulk tiles without guards, %s\n", in.c_str(), tile,
+                    v->tail_free ? "no edge code (assumed divisible)" : "edge tile with a guard");
+            if (two)
+                appendf(s, "split_iname(%s, %d): edge code per bound and corner code for both\n", K.inames[0].c_str(),
+                        4 * v->unroll);
+            appendf(s, "tags: vec(%s) = %d, unr = %d, %d CTAs/SM\n", in.c_str(), v->elems_per_thread, v->unroll,
+                    v->ctas_per_sm);
+        }
+        s += rule;
+        if (needed)
+            *needed = s.size() + 1;
+        if (!buf || cap == 0)
+            return LC_ERR_BUFFER_TOO_SMALL;
+        size_t n = std::min(cap - 1, s.size());
+        memcpy(buf, s.data(), n);
+        buf[n] = 0;
+        return n < s.size() ? LC_ERR_BUFFER_TOO_SMALL : LC_OK;
+    }
     s += rule;
-    s += "KERNEL: element_local_contraction\n";
+    s += geo ? "KERNEL: volume_derivative_with_geometric_factors\n" : "KERNEL: element_local_contraction\n";
     s += rule;
     s += "ARGUMENTS:\n";
     appendf(s, "%s: GlobalArg, type: %s, shape: (%s, %s, %s), dim_tags: (stride:%s*%s, stride:%s, stride:1)\n",
             K.d_name.c_str(), ty, F, N, N, N, N, N);
+    if (geo) {
+        if (node)
+            appendf(s, "%s: GlobalArg, type: %s, shape: (%s, %s, %s), dim_tags: (stride:1, stride:%s*%s, stride:%s)\n",
+                    K.g_name.c_str(), ty, E, F, F, F, E, E);
+        else
+            appendf(s, "%s: GlobalArg, type: %s, shape: (%s, %s, %s), dim_tags: (stride:%s*%s, stride:%s, stride:1)\n",
+                    K.g_name.c_str(), ty, E, F, F, F, F, F);
+    }
     if (multi)
         appendf(s, "%s: ValueArg, type: int32\n", F);
     appendf(s, "%s: ValueArg, type: int64\n%s: ValueArg, type: int32\n", E, N);
@@ -1164,7 +1439,13 @@ lc_status lc_kernel_print(const lc_kernel *kh, const lc_variant *v, char *buf, s
     }
     s += rule;
     s += "INSTRUCTIONS:\n";
-    if (multi)
+    if (geo)
+        appendf(s, "[%s, %s, %s] %s[%s, %s, %s] <- sum((%s, %s), %s[%s, %s, %s]*%s[%s, %s, %s]*%s[%s, %s])\n",
+                K.d_iname.c_str(), K.e_iname.c_str(), K.i_iname.c_str(), K.out_name.c_str(), K.d_iname.c_str(),
+                K.e_iname.c_str(), K.i_iname.c_str(), K.f_iname.c_str(), K.j_iname.c_str(), K.g_name.c_str(),
+                K.e_iname.c_str(), K.d_iname.c_str(), K.f_iname.c_str(), K.d_name.c_str(), K.f_iname.c_str(),
+                K.i_iname.c_str(), K.j_iname.c_str(), K.u_name.c_str(), K.e_iname.c_str(), K.j_iname.c_str());
+    else if (multi)
         appendf(s, "[%s, %s, %s] %s[%s, %s, %s] <- sum(%s, %s[%s, %s, %s]*%s[%s, %s])\n",
                 K.f_iname.c_str(), K.e_iname.c_str(), K.i_iname.c_str(), K.out_name.c_str(),
                 K.f_iname.c_str(), K.e_iname.c_str(), K.i_iname.c_str(), K.j_iname.c_str(),
@@ -1214,6 +1495,13 @@ lc_status lc_variant_validate(const lc_kernel *kh, int64_t E, int32_t N, int32_t
 {
     if (!kh)
         return LC_ERR_INVALID_ARGUMENT;
+    if (kh->k.kind == KIND_ELEMENTWISE) {
+        // the extents of the first and second iname come as E and N; F must be 1
+        const int64_t ext[2] = {E, N};
+        int grid = 0;
+        long long nt = 0;
+        return F != 1 ? LC_ERR_INVALID_ARGUMENT : ew_validate(kh->k, v, ext, false, &grid, &nt);
+    }
     Resolved r;
     return resolve(kh->k, E, N, F, v, r, false);
 }
@@ -1223,6 +1511,27 @@ lc_status lc_variant_plan(const lc_kernel *kh, int64_t E, int32_t N, int32_t F, 
 {
     if (!kh || !p || p->struct_size != sizeof(lc_plan))
         return LC_ERR_INVALID_ARGUMENT;
+    if (kh->k.kind == KIND_ELEMENTWISE) {
+        const int64_t ext[2] = {E, N};
+        int grid = 0;
+        long long nt = 0;
+        if (F != 1)
+            return LC_ERR_INVALID_ARGUMENT;
+        lc_status st = ew_validate(kh->k, v, ext, true, &grid, &nt);
+        if (st == LC_ERR_NO_DEVICE)
+            st = ew_validate(kh->k, v, ext, false, &grid, &nt);
+        if (st != LC_OK)
+            return st;
+        lc_plan q;
+        memset(&q, 0, sizeof q);
+        q.struct_size = sizeof(lc_plan);
+        q.grid = grid;
+        q.threads = 256;
+        q.tiles = nt;
+        q.column_blocks = 1;
+        *p = q;
+        return LC_OK;
+    }
     Resolved r;
     lc_status st = resolve(kh->k, E, N, F, v, r, true);
     if (st == LC_ERR_NO_DEVICE)
@@ -1272,6 +1581,19 @@ lc_status lc_variant_default(const lc_kernel *kh, int64_t E, int32_t N, int32_t 
     lc_variant d;
     memset(&d, 0, sizeof d);
     d.struct_size = sizeof(lc_variant);
+    if (kh->k.kind == KIND_ELEMENTWISE) {
+        // 16-byte vectors, four per thread and tile, four CTAs per SM; FP32
+        if (precision != LC_PREC_FP32 || layout != LC_LAYOUT_ELEM_MAJOR)
+            return LC_ERR_UNSUPPORTED;
+        d.engine = LC_ENGINE_SIMT;
+        d.precision = LC_PREC_FP32;
+        d.unroll = 4;
+        d.elems_per_thread = 4;
+        d.stages = 1;
+        d.ctas_per_sm = 4;
+        *v = d;
+        return LC_OK;
+    }
     d.layout = layout;
     d.precision = precision;
     d.unroll = 4;

@@ -21,9 +21,30 @@ struct Assumption {
 // What the instruction computes (each kind has its own entry point).
 enum KernelKind { KIND_CONTRACT = 0, KIND_GEO = 1, KIND_ELEMENTWISE = 2 };
 
+// Elementwise instruction: an expression tree over array loads, scalar parameters and
+// constants.  arrays[0] is the output; the inputs follow in order of first appearance.
+enum EwOp { EW_LOAD, EW_PARAM, EW_CONST, EW_ADD, EW_SUB, EW_MUL, EW_DIV, EW_NEG };
+struct EwNode {
+    int op;
+    int a = -1, b = -1;  // operands (node indices)
+    int arg = -1;        // EW_LOAD: array index; EW_PARAM: parameter index
+    double val = 0.0;    // EW_CONST
+};
+struct EwArray {
+    std::string name;
+    std::vector<int> dims;  // domain positions of its indices, ascending
+};
+struct Elementwise {
+    std::vector<EwNode> nodes;
+    int root = -1;
+    std::vector<EwArray> arrays;
+    std::vector<std::string> params;
+};
+
 struct Kernel {
     int kind = KIND_CONTRACT;
     std::string g_name, d_iname;      // KIND_GEO: geometric-factor array G[e,d,f], physical-derivative iname
+    Elementwise ew;                   // KIND_ELEMENTWISE
     std::vector<std::string> inames;  // as written in the domain
     std::vector<std::string> bounds;  // parameter bounding each iname
     std::string out_name, d_name, u_name;
@@ -112,6 +133,11 @@ struct TcArgs {
 };
 
 lc_status tc_launch(const TcArgs &a, int layout, int nterms, int grid, cudaStream_t s);
+
+// Elementwise kernels: check a descriptor against extents (one per iname) without launching;
+// reports the grid and the number of tiles.
+lc_status ew_validate(const Kernel &K, const lc_variant *v, const int64_t *extents, bool need_device, int *grid,
+                      long long *ntiles);
 lc_status tc_geo_launch(const TcArgs &a, int layout, int nterms, int grid, cudaStream_t s);
 
 // Grouped launch: per-group SIMT arguments, contiguous tile ranges, ranges per CTA.
@@ -146,3 +172,9 @@ lc_status simt_launch_f64_node(const SimtArgs &a, const SimtGeom &g, int unroll,
 lc_status warp_launch(const WarpArgs &a, int layout, int fp64, int grid, int threads, cudaStream_t s);
 
 }  // namespace lc
+
+// The opaque handle of the C ABI: an immutable parsed kernel.
+struct lc_kernel {
+    lc::Kernel k;
+};
+

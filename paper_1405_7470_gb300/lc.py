@@ -75,6 +75,11 @@ SIGNATURES = {
     "lc_variant_validate": ([_P, _I64, _I32, _I32, _VP], ctypes.c_int),
     "lc_variant_plan": ([_P, _I64, _I32, _I32, _VP, ctypes.POINTER(lc_plan)], ctypes.c_int),
     "lc_contract": ([_P, _VP, _P, _P, _P, _I64, _I32, _I32, _P], ctypes.c_int),
+    "lc_contract_geo": ([_P, _VP, _P, _P, _P, _P, _I64, _I32, _I32, _P], ctypes.c_int),
+    "lc_kernel_signature": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)], ctypes.c_int),
+    "lc_kernel_arg_name": ([_P, _I32, _I32, ctypes.c_char_p, _SZ], ctypes.c_int),
+    "lc_elementwise_source": ([_P, _VP, _P, ctypes.c_char_p, _SZ, ctypes.POINTER(_SZ)], ctypes.c_int),
+    "lc_elementwise": ([_P, _VP, _P, _P, _P, _P], ctypes.c_int),
     "lc_contract_host": ([_P, _VP, _P, _P, _P, _I64, _I32, _I32, _P, _P, _P, _P], ctypes.c_int),
     "lc_device_error": ([ctypes.c_int], ctypes.c_int),
     "lc_selftest_wait_timeout": ([_I64, _P], ctypes.c_int),
@@ -234,6 +239,28 @@ def contract(kernel: Kernel, v: lc_variant, D, u, out=None, stream=None):
             raise ValueError("D, u and out must be contiguous CUDA tensors")
     st = lc_contract(kernel, v, D.data_ptr(), u.data_ptr(), out.data_ptr(), E, N, F, _stream_ptr(stream))
     check(st, "lc_contract")
+    return out
+
+
+GEO_DOMAIN = "{ [d,f,e,i,j]: 0<=d<F and 0<=f<F and 0<=e<E and 0<=i,j<N }"
+GEO_INSTRUCTION = "out[d,e,i] = sum((f,j), G[e,d,f]*D[f,i,j]*u[e,j])"
+
+
+def contract_geo(kernel: Kernel, v: lc_variant, D, u, r, out=None, stream=None):
+    """Volume derivative with per-element geometric factors (lc_contract_geo) on torch CUDA
+    tensors: D (F, N, N), u (E, N) or (N, E), r (E, F, F) element-major or (F, F, E)
+    node-major; returns out (F, E, N) or (F, N, E)."""
+    import torch
+    F, N, _ = D.shape
+    node = v.layout == LAYOUT["node"]
+    E = u.shape[1] if node else u.shape[0]
+    if out is None:
+        out = torch.empty((F, N, E) if node else (F, E, N), dtype=u.dtype, device=u.device)
+    for t in (D, u, r, out):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("D, u, r and out must be contiguous CUDA tensors")
+    check(load().lc_contract_geo(kernel.handle, ctypes.byref(v), D.data_ptr(), u.data_ptr(), r.data_ptr(),
+                                 out.data_ptr(), E, N, F, _stream_ptr(stream)), "lc_contract_geo")
     return out
 
 
@@ -405,3 +432,46 @@ def pick_variant(kernel: Kernel, E: int, N: int, F: int, layout, precision, para
                               workspace.data_ptr(), need.value, ctypes.byref(v), ctypes.byref(pred),
                               _stream_ptr(stream)), "lc_pick_variant")
     return v, pred.value
+
+
+def kernel_args(kernel: Kernel) -> dict:
+    """Argument names in call order: {"arrays": [...], "params": [...], "dims": [...]}."""
+    lib = load()
+    na, npar, nd = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    check(lib.lc_kernel_signature(kernel.handle, ctypes.byref(na), ctypes.byref(npar), ctypes.byref(nd)),
+          "lc_kernel_signature")
+    buf = ctypes.create_string_buffer(256)
+
+    def names(what, n):
+        out = []
+        for q in range(n):
+            check(lib.lc_kernel_arg_name(kernel.handle, what, q, buf, 256), "lc_kernel_arg_name")
+            out.append(buf.value.decode())
+        return out
+    return dict(arrays=names(0, na.value), params=names(1, npar.value), dims=names(2, nd.value))
+
+
+def elementwise_source(kernel: Kernel, v: lc_variant, extents) -> str:
+    """The CUDA source lc_elementwise compiles for this descriptor and these extents."""
+    lib = load()
+    ext = (ctypes.c_int64 * 2)(*(list(extents) + [1])[:2])
+    need = ctypes.c_size_t(0)
+    lib.lc_elementwise_source(kernel.handle, ctypes.byref(v), ext, None, 0, ctypes.byref(need))
+    buf = ctypes.create_string_buffer(need.value)
+    check(lib.lc_elementwise_source(kernel.handle, ctypes.byref(v), ext, buf, need.value, ctypes.byref(need)),
+          "lc_elementwise_source")
+    return buf.value.decode()
+
+
+def elementwise(kernel: Kernel, v: lc_variant, arrays, params=(), extents=None, stream=None):
+    """Run an elementwise kernel (lc_elementwise). arrays: torch CUDA float32 tensors in
+    signature order (arrays[0] is the output); params: scalars in order; extents: one per
+    iname (default: the output's shape). Returns arrays[0]."""
+    lib = load()
+    ext = list(extents) if extents is not None else list(arrays[0].shape)
+    e_arr = (ctypes.c_int64 * max(1, len(ext)))(*ext)
+    ptrs = (ctypes.c_void_p * len(arrays))(*[a.data_ptr() for a in arrays])
+    par = (ctypes.c_double * max(1, len(params)))(*params)
+    check(lib.lc_elementwise(kernel.handle, ctypes.byref(v), e_arr, ptrs, par, _stream_ptr(stream)),
+          "lc_elementwise")
+    return arrays[0]

@@ -218,3 +218,40 @@ def test_variant_features_and_pick_arguments(lib):
     v = lc.lc_variant()
     assert lib.lc_pick_variant(kernel.handle, 1000, 35, 3, 0, 3, None, None, 0, ctypes.byref(v), None, None) == 1
     assert lib.lc_pick_variant(kernel.handle, 1000, 35, 3, 0, 3, 16, 16, 8, ctypes.byref(v), None, None) == 6
+
+
+GEO_DOM = "{ [d,f,e,i,j]: 0<=d<F and 0<=f<F and 0<=e<E and 0<=i,j<N }"
+
+
+@pytest.mark.parametrize("insn,ok", [
+    ("out[d,e,i] = sum((f,j), G[e,d,f]*D[f,i,j]*u[e,j])", True),
+    ("y[d,e,i] = sum((j,f), u[e,j]*Dr[f,i,j]*rx[e,d,f])", True),
+    ("out[d,e,i] = sum((f,j), G[e,f,d]*D[f,i,j]*u[e,j])", False),   # transposed factors
+    ("out[d,e,i] = sum((f,j), G[e,d,f]*D[f,j,i]*u[e,j])", False),   # transposed operator
+    ("out[d,e,i] = sum((f,j), G[e,d,f]*D[f,i,j]*G[e,j])", False),   # repeated array
+    ("out[d,e,i] = sum(j, D[d,i,j]*u[e,j])", False),                # not this domain's inames
+])
+def test_parse_geometric_factor_form(lib, insn, ok):
+    assert (_create(lib, GEO_DOM, insn) == 0) == ok
+    # d and f must share one bound
+    assert _create(lib, "{ [d,f,e,i,j]: 0<=d<P and 0<=f<F and 0<=e<E and 0<=i,j<N }",
+                   "out[d,e,i] = sum((f,j), G[e,d,f]*D[f,i,j]*u[e,j])") == 2
+
+
+def test_geometric_factor_kernel_rules(lib):
+    """The two instruction forms have their own entry points; the fused epilogue needs every
+    operator in one column block of the tensor-core engine, F = 2 or 3."""
+    kg = lc.Kernel(lc.GEO_DOMAIN, lc.GEO_INSTRUCTION)
+    kc = lc.Kernel()
+    v = lc.variant_default(kg, 1 << 20, 35, 3, "elem", "bf16x3")
+    assert lc.variant_dict(v)["engine"] == "tcgen05" and lc.variant_plan(kg, 1 << 20, 35, 3, v)["column_blocks"] == 1
+    assert lc.load().lc_contract(kg.handle, ctypes.byref(v), 16, 16, 16, 0, 35, 3, None) == 2
+    assert lib.lc_contract_geo(kc.handle, ctypes.byref(v), 16, 16, 16, 16, 0, 35, 3, None) == 2
+    for bad in (dict(split_i=1), dict(engine="simt", precision="fp32", tile_e=64, elems_per_thread=4, split_i=8)):
+        d = lc.variant_dict(v)
+        d.update(bad)
+        assert lc.variant_validate(kg, 1 << 20, 35, 3, lc.Variant(**d)) == 3, bad
+    assert lc.variant_validate(kg, 1 << 20, 35, 4, v) == 3  # F = 4: no kernel instance
+    text = kg.print(v)
+    assert "out[d, e, i] <- sum((f, j), G[e, d, f]*D[f, i, j]*u[e, j])" in text
+    assert "G: GlobalArg" in text
