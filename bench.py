@@ -49,6 +49,28 @@ WORKLOADS = {
                          "CUDA graph"),
 }
 
+WORKLOADS.update({
+    "geo": dict(E=1 << 21, N=35, F=3, precision="bf16x3",
+                desc="volume derivative with per-element geometric factors E=2^21 N=35 F=3 "
+                     "(out[d,e,i] = sum_f r[e,d,f] sum_j D[f,i,j] u[e,j])"),
+    "saxpy": dict(E=1 << 28, N=1, F=1, precision="fp32",
+                  desc="saxpy z[i] = a*x[i] + y[i], n=2^28 floats, through the elementwise front end"),
+})
+
+# the configurations measured beside the headline line (one subprocess each, after it)
+PER_CONFIG = [
+    ("fp64_single", ["--workload", "fp64_single"]),
+    ("fp32_three/fp32", ["--workload", "fp32_three", "--precision", "fp32"]),
+    ("fp32_three/bf16", ["--workload", "fp32_three", "--precision", "bf16"]),
+    ("fp32_three/bf16x3/node", ["--workload", "fp32_three", "--layout", "node"]),
+    ("precision/fp32", ["--workload", "precision", "--precision", "fp32"]),
+    ("precision/bf16", ["--workload", "precision", "--precision", "bf16"]),
+    ("precision/bf16x3", ["--workload", "precision", "--precision", "bf16x3"]),
+    ("grouped", ["--workload", "grouped"]),
+    ("geo/bf16x3", ["--workload", "geo"]),
+    ("saxpy", ["--workload", "saxpy"]),
+]
+
 L2_BYTES = 129 * 1000 * 1000  # GB300 L2
 
 # FP32 SIMT descriptors tried for the grouped launch: (elems_per_thread, split_i, unroll,
@@ -251,11 +273,14 @@ def roofline_for(v, wl, peaks, sms, t_launch_s, workload_key):
             "frac": ach / peaks["hbm_gbs"], "traffic": traffic, "peak_source": peaks["source"]}
 
 
-def run_oracle_baseline(wl, D, u, layout, budget_s=12.0):
-    """Time the CPU FP64 oracle on the same workload (whole batch, repeated up to ~budget_s)."""
+def run_oracle_baseline(wl, D, u, layout, budget_s=12.0, error_only=False):
+    """Time the CPU FP64 oracle on the same workload (whole batch, repeated up to ~budget_s).
+    error_only: one untimed run for the reference output only."""
     import oracle
     D64 = D.astype(np.float64)
     u64 = u.astype(np.float64)
+    if error_only:
+        return oracle.contract(D64, u64, layout), None
     flops = 2.0 * wl["E"] * wl["N"] ** 2 * wl["F"]
     reps, t_total, ref = 0, 0.0, None
     while True:
@@ -291,6 +316,10 @@ def main():
                     help="'auto' (autotuned before timing), 'default', or JSON descriptor fields")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-per-config", action="store_true",
+                    help="skip the other configurations measured after the default line")
+    ap.add_argument("--error-only", action="store_true",
+                    help="compute the error against the oracle but do not time the oracle")
     ap.add_argument("--E", type=int, default=0, help="override the workload's element count (profiling)")
     ap.add_argument("--precision", default="", choices=["", "fp32", "fp64", "bf16", "bf16x3"],
                     help="arithmetic path; default: bf16x3 (three-term split on the tensor cores, error "
@@ -304,7 +333,7 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     wl = dict(WORKLOADS[args.workload])
     wl["storage"] = "fp64" if wl["precision"] == "fp64" else "fp32"
-    if not args.precision and wl["storage"] == "fp32" and args.workload != "grouped":
+    if not args.precision and wl["storage"] == "fp32" and args.workload not in ("grouped", "saxpy", "geo"):
         args.precision = "bf16x3"
     if args.precision:
         if (args.precision == "fp64") != (wl["storage"] == "fp64"):
@@ -322,6 +351,10 @@ def main():
         if args.precision not in ("", "fp32", "bf16x3"):
             ap.error("the grouped launch runs the FP32 SIMT engine")
         return run_grouped(args, wl, world, rank, local_rank)
+    if args.workload == "geo":
+        return run_geo(args, wl, world, rank, local_rank)
+    if args.workload == "saxpy":
+        return run_saxpy(args, wl, world, rank, local_rank)
 
     import torch
     import torch.distributed as dist
@@ -452,7 +485,7 @@ def main():
     rel_err = None
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        ref, cpu = run_oracle_baseline(wl, D, u_in, args.layout)
+        ref, cpu = run_oracle_baseline(wl, D, u_in, args.layout, error_only=args.error_only)
         refd = torch.from_numpy(ref).cuda()
         rel_err = lc.error_norm(out, refd)
         del refd, ref
@@ -492,6 +525,12 @@ def main():
     if lc.device_error() != 0:
         raise RuntimeError("device error word set during the timed region")
 
+    per_config = None
+    if (rank == 0 and world == 1 and not args.no_per_config and args.workload == "fp32_three" and
+            args.layout == "elem" and args.variant == "auto" and not args.E):
+        torch.cuda.synchronize()
+        per_config = run_per_config(args, rank)
+
     if rank == 0:
         roof = roofline_for(vd, wl, peaks, sms, launch_s, args.workload)
         line = {
@@ -516,6 +555,8 @@ def main():
             "hbm_gbs_achieved": ((8 if wl["precision"] == "fp64" else 4) * (E * N * (1 + F) + F * N * N))
             / (ms_per_step * 1e-3) / 1e9,
         }
+        if per_config is not None:
+            line["per_config"] = per_config
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -633,6 +674,7 @@ def run_grouped(args, wl, world, rank, local_rank):
             got = o[:, :, rows].transpose(0, 2, 1) if node else o[:, rows, :]
             errs.append(oracle.rel_fro_error(got, ref))
         rel_err = max(errs)
+    if rank == 0 and not args.no_cpu_baseline and not args.error_only:
         per = 1 << 14
         t0 = time.perf_counter()
         sflops = 0.0
@@ -699,6 +741,228 @@ def run_grouped(args, wl, world, rank, local_rank):
         dist.destroy_process_group()
 
 
+def _timed_steps(torch, stream, step, steps):
+    """CUDA events around every step on `stream`; returns (total ms, per-step ms list)."""
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for k in range(steps):
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    return starts[0].elapsed_time(ends[-1]), [a.elapsed_time(b) for a, b in zip(starts, ends)]
+
+
+def run_geo(args, wl, world, rank, local_rank):
+    """Volume derivative with per-element geometric factors (lc_contract_geo): one launch per
+    step on the tensor cores (BF16X3 by default, FP32-level error)."""
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    import synth
+    from paper_1405_7470_gb300 import lc
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    lc.load()
+    sms = lc.device_info()["sm_count"]
+    peaks = load_peaks()
+    E, N, F = wl["E"], wl["N"], wl["F"]
+    D, u = synth.fp32_three(E=E)
+    r = np.random.default_rng(9).uniform(-2, 2, size=(E, F, F)).astype(np.float32)
+    node = args.layout == "node"
+    u_in = synth.to_node_major(u) if node else u
+    r_in = np.ascontiguousarray(r.transpose(1, 2, 0)) if node else r
+    kernel = lc.Kernel(lc.GEO_DOMAIN, lc.GEO_INSTRUCTION)
+    stream = torch.cuda.Stream()
+    Dd, ud, rd = (torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in (D, u_in, r_in))
+    out = torch.empty((F, N, E) if node else (F, E, N), device="cuda")
+    cands = [v for v in lc.enumerate_variants(kernel, E, N, F, args.layout, wl["precision"])]
+    best = None
+    with torch.cuda.stream(stream):
+        for v in cands:
+            lc.contract_geo(kernel, v, Dd, ud, rd, out, stream=stream)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(3):
+                lc.contract_geo(kernel, v, Dd, ud, rd, out, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            t = a.elapsed_time(b) / 3
+            if best is None or t < best[0]:
+                best = (t, v)
+    v = best[1]
+    flops = 2.0 * E * N * N * F + 2.0 * E * N * F * F
+    nbytes = 4.0 * (E * N + E * F * F + F * E * N + F * N * N)
+
+    def step():
+        lc.contract_geo(kernel, v, Dd, ud, rd, out, stream=stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    with torch.cuda.stream(stream):
+        total_ms, per = _timed_steps(torch, stream, step, args.steps)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = total_ms / args.steps
+    launch_s = statistics.mean(per) * 1e-3
+    rel_err = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rows = np.unique(np.concatenate([np.arange(256), np.random.default_rng(1).integers(0, E, 20000)]))
+        got = out.index_select(2 if node else 1, torch.from_numpy(rows).cuda()).cpu().numpy()
+        if node:
+            got = got.transpose(0, 2, 1)
+        rel_err = oracle.rel_fro_error(got, oracle.contract_geo_rows(D, u, r, rows))
+    if lc.device_error() != 0:
+        raise RuntimeError("device error word set during the timed region")
+    if rank == 0:
+        ach = nbytes / launch_s / 1e9
+        vd = lc.variant_dict(v)
+        line = {
+            "metric": "contraction GFLOP/s", "value": flops * world / (ms * 1e-3) / 1e9, "unit": "GFLOP/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x3 split (f32 accumulate)" if wl["precision"] == "bf16x3" else "bf16 (f32 accumulate)",
+            "data": "synthetic",
+            "config": {"workload": wl["desc"], "E": E, "N": N, "F": F, "layout": args.layout,
+                       "precision": wl["precision"], "variant": vd,
+                       "variant_choice": f"fastest of {len(cands)} candidates (3 launches each)",
+                       "bytes_per_step": nbytes, "l2": "inputs+outputs larger than L2 (no flush needed)",
+                       "unfused_bytes_per_step": 4.0 * (E * N + 2 * F * E * N + E * F * F + F * E * N)},
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": peaks["source"]},
+            "cpu_baseline": None, "e2e": None, "gpu_launches": args.steps, "clocks": clk,
+            "rel_error_vs_oracle": rel_err, "hbm_gbs_achieved": nbytes / (ms * 1e-3) / 1e9,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_saxpy(args, wl, world, rank, local_rank):
+    """saxpy (Table 1's streaming workload) through the elementwise front end: z = a x + y over
+    n floats, one generated kernel launch per step; GB/s against the measured HBM copy rate."""
+    import torch
+    import torch.distributed as dist
+
+    import oracle.elementwise as ew
+    from paper_1405_7470_gb300 import lc
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    lc.load()
+    peaks = load_peaks()
+    n = wl["E"]
+    kernel = lc.Kernel("{ [i]: 0<=i<n }", "z[i] = a*x[i] + y[i]")
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    x = torch.randn(n, device="cuda", generator=g)
+    y = torch.randn(n, device="cuda", generator=g)
+    z = torch.empty(n, device="cuda")
+    a = 0.7071
+    stream = torch.cuda.Stream()
+    best = None
+    for unroll in (1, 2, 4, 8):
+        for ctas in (2, 4, 8):
+            v = lc.variant_default(kernel, n, 1, 1, "elem", "fp32")
+            v.unroll, v.ctas_per_sm = unroll, ctas
+            with torch.cuda.stream(stream):
+                lc.elementwise(kernel, v, [z, x, y], [a], stream=stream)
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                for _ in range(3):
+                    lc.elementwise(kernel, v, [z, x, y], [a], stream=stream)
+                ev1.record(stream)
+            ev1.synchronize()
+            t = ev0.elapsed_time(ev1) / 3
+            if best is None or t < best[0]:
+                best = (t, v)
+    v = best[1]
+    nbytes = 12.0 * n
+
+    def step():
+        lc.elementwise(kernel, v, [z, x, y], [a], stream=stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    with torch.cuda.stream(stream):
+        total_ms, per = _timed_steps(torch, stream, step, args.steps)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = total_ms / args.steps
+    launch_s = statistics.mean(per) * 1e-3
+    exact = None
+    if rank == 0:
+        idx = torch.from_numpy(np.random.default_rng(2).integers(0, n, 200000)).cuda()
+        xs, ys, zs = (t.index_select(0, idx).cpu().numpy() for t in (x, y, z))
+        want = ew.evaluate("z[i] = a*x[i] + y[i]", ["i"], [len(xs)], {"x": xs, "y": ys}, {"a": a})
+        exact = bool(np.array_equal(zs, want))
+    if lc.device_error() != 0:
+        raise RuntimeError("device error word set during the timed region")
+    if rank == 0:
+        ach = nbytes / launch_s / 1e9
+        line = {
+            "metric": "saxpy GB/s", "value": nbytes * world / (ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl["desc"], "n": n, "variant": lc.variant_dict(v),
+                       "variant_choice": "fastest unroll x CTAs/SM of 12", "bytes_per_step": nbytes,
+                       "l2": "inputs+outputs larger than L2 (no flush needed)"},
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": peaks["source"]},
+            "cpu_baseline": None, "e2e": None, "gpu_launches": args.steps, "clocks": clk,
+            "bit_exact_vs_oracle_sample": exact,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_per_config(args, rank) -> dict:
+    """Each configuration of PER_CONFIG in its own process (after the headline's timed
+    region): value, roofline fraction, error against the oracle, clocks."""
+    if rank != 0:
+        return {}
+    res = {}
+    for name, extra in PER_CONFIG:
+        cmd = [sys.executable, os.path.abspath(__file__), "--steps", "10", "--warmup", "3", "--no-e2e",
+               "--no-per-config", "--error-only"] + extra
+        t0 = time.perf_counter()
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=600)
+            lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+            d = json.loads(lines[-1]) if (r.returncode == 0 and lines) else None
+        except (subprocess.SubprocessError, ValueError):
+            d = None
+        if d is None:
+            res[name] = {"error": "run failed", "wall_s": time.perf_counter() - t0}
+            continue
+        roof = d.get("roofline") or {}
+        res[name] = {"metric": d["metric"], "value": d["value"], "unit": d["unit"], "ms_per_step": d["ms_per_step"],
+                     "roofline": {k: roof.get(k) for k in ("bound", "achieved", "peak", "unit", "frac")},
+                     "rel_error_vs_oracle": d.get("rel_error_vs_oracle"),
+                     "bit_exact_vs_oracle_sample": d.get("bit_exact_vs_oracle_sample"),
+                     "variant": d["config"].get("variant"), "clocks": d.get("clocks"),
+                     "workload": d["config"]["workload"], "wall_s": time.perf_counter() - t0}
+        if "per_group_launches_ms" in d["config"]:
+            res[name]["per_group_launches_ms"] = d["config"]["per_group_launches_ms"]
+    return res
+
+
 def run_reference(args, wl):
     """CPU FP64 oracle on the host cores: each step a bounded sample of the workload."""
     import oracle
@@ -712,6 +976,8 @@ def run_reference(args, wl):
         D, u = synth.fp32_three()
     if args.workload == "grouped":
         return run_reference_grouped(args, wl)
+    if args.workload in ("geo", "saxpy"):
+        return run_reference_other(args, wl)
     Es = min(E, 1 << 18)
     sub = u[:Es]
     u_in = synth.to_node_major(sub) if args.layout == "node" else sub
@@ -735,6 +1001,45 @@ def run_reference(args, wl):
         "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": "GFLOP/s",
                          "sample": f"first {Es} of {E} elements per step, OpenMP over elements"},
         "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_other(args, wl):
+    """The oracle for the volume derivative (a 2^16-element sample per step) or for saxpy (the
+    elementwise evaluator on a 2^24-element sample per step), on the host cores."""
+    import oracle
+    import oracle.elementwise as ew
+    import synth
+    if args.workload == "geo":
+        Es, N, F = 1 << 16, wl["N"], wl["F"]
+        D, u = synth.fp32_three(E=Es)
+        r = np.random.default_rng(9).uniform(-2, 2, size=(Es, F, F)).astype(np.float32)
+        work = 2.0 * Es * N * N * F + 2.0 * Es * N * F * F
+        one = lambda: oracle.contract_geo(D, u, r)
+        metric, unit, sample = "contraction GFLOP/s", "GFLOP/s", f"{Es} elements per step"
+    else:
+        n = 1 << 24
+        rng = np.random.default_rng(0)
+        x, y = rng.standard_normal(n).astype(np.float32), rng.standard_normal(n).astype(np.float32)
+        work = 12.0 * n
+        one = lambda: ew.evaluate("z[i] = a*x[i] + y[i]", ["i"], [n], {"x": x, "y": y}, {"a": 0.7071})
+        metric, unit, sample = "saxpy GB/s", "GB/s", f"{n} floats per step, numpy on one thread"
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    dt = (time.perf_counter() - t0) / args.steps
+    value = work / dt / 1e9
+    cores = oracle.num_threads() if args.workload == "geo" else 1
+    line = {
+        "metric": metric, "value": value, "unit": unit, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.workload == "geo" else "f32", "data": "synthetic",
+        "config": {"workload": wl["desc"]}, "impl": "reference",
+        "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": unit, "sample": sample},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 

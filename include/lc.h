@@ -123,7 +123,9 @@ struct lc_variant {
                                  epilogue threads per tile row, 1 to 4 (conversion threads per
                                  row: the same, 2 for 4) */
     int32_t prefetch_smem;    /* add_prefetch of the u tile into shared memory by TMA (1) or
-                                 direct global loads into registers (0) */
+                                 direct global loads into registers (0); tensor-core engine: 1,
+                                 or 2 = each converting thread takes its values into registers
+                                 and frees the stage at once (K of one block only) */
     int32_t tail_free;        /* 1: no guard on the last e tile; only accepted when an
                                  assumption "E mod m = 0" with m a multiple of tile_e holds */
     int32_t stages;           /* u tiles in flight in shared memory (TMA ring depth), >= 1 */

@@ -1076,7 +1076,8 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         // elems_per_thread = K-block width (16, 32 or 64 bf16 = 32/64/128-byte swizzle rows),
         // K padded to a multiple of it; 1 = the widest block that divides K padded to 16
         const int kbw = v->elems_per_thread;
-        if (v->tile_e != 128 || v->prefetch_smem != 1 || !(kbw == 1 || kbw == 16 || kbw == 32 || kbw == 64) ||
+        if (v->tile_e != 128 || !(v->prefetch_smem == 1 || v->prefetch_smem == 2) ||
+            !(kbw == 1 || kbw == 16 || kbw == 32 || kbw == 64) ||
             v->unroll < 1 || v->unroll > 4)
             return LC_ERR_INVALID_VARIANT;
         if (v->stages < 1 || v->stages > 3 || v->split_i < 0 || v->split_i > F || v->ctas_per_sm > 1 ||
@@ -1105,6 +1106,7 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         if (t.nkb > 16)
             return LC_ERR_INVALID_VARIANT;  // more K-blocks than the kernel has barrier pairs for
         t.stages = v->stages;
+        t.early_release = v->prefetch_smem == 2;
         t.threads_per_row = v->unroll;
         t.conv_threads_per_row = std::min(v->unroll, 6 - v->unroll);
         const size_t W = 2 * (size_t)t.KB;
@@ -1171,11 +1173,14 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         const int ncombos = (int)(sizeof combos / sizeof combos[0]);
         bool found = false;
         const int g_hi = v->split_i ? v->split_i : F, g_lo = geo ? F : (v->split_i ? v->split_i : 1);
-        // the most operators per CTA first; for each, A in tensor memory (when asked, or by
-        // default), then in shared memory
+        // the most operators per CTA first; for each, the planner's A placement first: tensor
+        // memory for BF16 (it frees shared memory for stages and slots), shared memory for
+        // BF16X3 (the stacked order needs both accumulators' columns, and a long chain of MMAs
+        // reading A from tensor memory measured slower beside the epilogue's loads)
+        const bool tm_first = v->a_operand == 2 || (v->a_operand == 0 && NT == 1);
         for (int g = g_hi; g >= g_lo && !found; --g)
             for (int pass = 0; pass < 2 && !found; ++pass) {
-                const bool a_tm = pass == 0;
+                const bool a_tm = tm_first ? pass == 0 : pass == 1;
                 if ((a_tm && v->a_operand == 1) || (!a_tm && v->a_operand == 2) || (a_tm && v->mma_order == 1))
                     continue;
                 for (int c = 0; c < ncombos && !found; ++c) {
@@ -1626,20 +1631,25 @@ lc_status lc_variant_default(const lc_kernel *kh, int64_t E, int32_t N, int32_t 
         d.engine = LC_ENGINE_TCGEN05;
         d.tile_e = 128;
         d.split_i = 0;
-        d.unroll = 3;
+        d.unroll = 4;
         // 64-wide K-blocks first: a tcgen05.mma reading 128-byte swizzled rows costs the
-        // fewest cycles; then the narrowest blocks that cover K (least shared memory)
+        // fewest cycles; then the narrowest blocks that cover K (least shared memory).
+        // BF16X3: the A terms in shared memory first (the stacked order), one stage first (two
+        // stages leave room for one output slot only); BF16: the planner's placement, two stages.
+        const bool x3 = precision == LC_PREC_BF16X3;
         lc_status st = LC_ERR_INVALID_VARIANT;
-        for (int kbw : {64, 1})
-            for (int stg : {2, 3, 1}) {
-                if (st == LC_OK)
-                    break;
-                d.elems_per_thread = kbw;
-                d.stages = stg;
-                st = lc_variant_validate(kh, E, N, F, &d);
-                if (st != LC_OK && st != LC_ERR_INVALID_VARIANT)
-                    return st;
-            }
+        for (int aop : {x3 ? 1 : 0, 0})
+            for (int kbw : {64, 1})
+                for (int stg : {x3 ? 1 : 2, x3 ? 2 : 3, x3 ? 3 : 1}) {
+                    if (st == LC_OK)
+                        break;
+                    d.a_operand = aop;
+                    d.elems_per_thread = kbw;
+                    d.stages = stg;
+                    st = lc_variant_validate(kh, E, N, F, &d);
+                    if (st != LC_OK && st != LC_ERR_INVALID_VARIANT)
+                        return st;
+                }
         if (st == LC_OK) {
             *v = d;
             return LC_OK;

@@ -120,7 +120,8 @@ struct TcArgs {
     int a_tmem;     // 1: the A terms live in tensor memory after the two accumulators
     int a_cols;     // tensor-memory columns per A buffer (NT terms x K/2 packed bf16 pairs)
     int tmem_alloc; // tensor-memory columns allocated (power of two >= 32)
-    int stages;     // u stage buffers (1 or 2)
+    int stages;     // u stage buffers (1 to 3)
+    int early_release;  // 1: conversion threads take their chunks into registers, then free the stage
     int threads_per_row;       // epilogue threads per tile row
     int conv_threads_per_row;  // conversion threads per tile row (CTA = 128 * (both) + 64 threads)
     int abufs;      // A-operand buffers (1 or 2)

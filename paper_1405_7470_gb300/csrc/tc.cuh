@@ -466,8 +466,21 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
         }
     } else if (warp >= NW) {
         // ---------------- conversion warps: fp32 u tile -> bf16 A-operand terms, K-block by K-block
+        // A thread converts K chunks c8 (8 values of j) of its tile row: within K-block kb the
+        // chunks c8_lo + part, c8_lo + part + Hc, ...  The A terms go to shared memory (hardware
+        // swizzle) or to tensor memory (tcgen05.st into this warp's lane quarter, warp-uniform
+        // loops; rows past the tile and nodes past N are zeros).
+        // Early release (descriptor prefetch_smem = 2): when K is one block and a thread has at
+        // most 3 chunks, it loads all of them into registers first and hands the u stage back to
+        // the producer at once, so the next tile's bulk copy overlaps this tile's conversion and
+        // MMAs (it helps one-stage plans; beside a long MMA chain the extra shared-memory
+        // traffic during the MMAs can cost more than it saves).
+        constexpr int kMaxEarly = 3;
         int k = 0;
         bool ok = true;
+        const int nch8 = Kn / 8;
+        const int my_chunks = (nkb == 1 && a.early_release) ? (nch8 - part + Hc - 1) / Hc : kMaxEarly + 1;
+        const uint32_t lane_q = (uint32_t)(32 * (warp & 3)) << 16;
         for (long long t = my_first; t < a.ntiles && ok; t += my_step, ++k) {
             const int s = k % S, ab = k % NA;
             const uint32_t ns = (uint32_t)(k / S), na = (uint32_t)(k / NA);
@@ -481,116 +494,109 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
             const float *st = stage + (size_t)s * TE * N;
             unsigned char *Ab = smem + offA + (size_t)ab * bufA;
             const bool rowv = row < TEv;
-            // K chunk c8 (8 values of j) of this thread's row -> the A terms
+            constexpr int JS = NODE ? TE : 1;
+            const float *src_s = NODE ? st + row : st + row * N;
+            const float *src_g = NODE ? a.u + e0 + row : a.u + (e0 + row) * N;
+            const long long jsg = NODE ? E : 1;
+            const uint32_t abase = tmem_base + 2u * (uint32_t)a.tmem_cols + (uint32_t)(ab * a.a_cols) + lane_q;
+            // the 8 values of chunk c8 of this thread's row (zeros past the row or past N)
+            auto load_chunk = [&](int c8, float *x) {
+                if (from_stage && c8 * 8 + 8 <= N) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        x[q] = rowv ? src_s[(c8 * 8 + q) * JS] : 0.f;
+                } else if (from_stage) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        x[q] = (rowv && c8 * 8 + q < N) ? src_s[(c8 * 8 + q) * JS] : 0.f;
+                } else {
+                    // unaligned tail tile, read from global memory
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        x[q] = (rowv && c8 * 8 + q < N) ? src_g[(long long)(c8 * 8 + q) * jsg] : 0.f;
+                }
+            };
+            // chunk c8 -> the A terms
             auto put = [&](int c8, const float *x) {
                 uint4 tt4[3];
                 split8<NT>(x, tt4);
-                const int kb = (c8 * 8) / KB, ch = ((c8 * 8) % KB) / 8;
-                const uint32_t off = (uint32_t)kb * TE * W + swz_off(row, ch, W);
+                if (a.a_tmem) {
 #pragma unroll
-                for (int tt = 0; tt < NT; ++tt)
-                    *reinterpret_cast<uint4 *>(Ab + off + tt * termA) = tt4[tt];
+                    for (int tt = 0; tt < NT; ++tt)
+                        tmem_st4(abase + (uint32_t)(tt * (Kn / 2) + c8 * 4), tt4[tt]);
+                } else {
+                    const int kb = (c8 * 8) / KB, ch = ((c8 * 8) % KB) / 8;
+                    const uint32_t off = (uint32_t)kb * TE * W + swz_off(row, ch, W);
+#pragma unroll
+                    for (int tt = 0; tt < NT; ++tt)
+                        *reinterpret_cast<uint4 *>(Ab + off + tt * termA) = tt4[tt];
+                }
             };
-            const int full8 = rowv ? N / 8 : 0;  // chunks with all 8 values inside the row
-            if (a.a_tmem) {
-                // A terms into tensor memory: this warp's TMEM lane quarter is its 32 tile rows;
-                // the loops are uniform across the warp (tcgen05.st is warp-collective), rows
-                // past the tile and nodes past N are written as zeros
-                const uint32_t abase =
-                    tmem_base + 2u * (uint32_t)a.tmem_cols + (uint32_t)(ab * a.a_cols) + ((uint32_t)(32 * (warp & 3)) << 16);
-                constexpr int JS = NODE ? TE : 1;
-                const float *src_s = NODE ? st + row : st + row * N;
-                const float *src_g = NODE ? a.u + e0 + row : a.u + (e0 + row) * N;
-                const long long jsg = NODE ? E : 1;
-                for (int kb = 0; kb < nkb && ok; ++kb) {
+            // block kb written: make it visible to the tensor core and hand it to the MMA warp
+            auto block_done = [&](int kb) {
+                if (a.a_tmem) {
+                    tmem_wait_st();
+                    tc_fence_before();
+                } else {
+                    fence_async_smem();
+                }
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(&a_full[ab * kTcMaxKB + kb]);
+            };
+            bool released = false;
+            if (from_stage && my_chunks <= kMaxEarly) {
+                float xv[kMaxEarly][8];
+#pragma unroll
+                for (int m = 0; m < kMaxEarly; ++m)
+                    if (m < my_chunks)
+                        load_chunk(part + Hc * m, xv[m]);
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(&u_empty[s]);  // the stage is free for the next bulk copy
+                released = true;
+                if (!mbar_wait(&a_empty[ab * kTcMaxKB], (na & 1u) ^ 1u)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int m = 0; m < kMaxEarly; ++m)
+                    if (m < my_chunks)
+                        put(part + Hc * m, xv[m]);
+                block_done(0);
+            } else {
+                for (int kb = 0; kb < nkb; ++kb) {
                     if (!mbar_wait(&a_empty[ab * kTcMaxKB + kb], (na & 1u) ^ 1u)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
                     const int c8_lo = kb * KB / 8, c8_hi = min(Kn, (kb + 1) * KB) / 8;
-                    for (int c8 = c8_lo + part; c8 < c8_hi; c8 += Hc) {
-                        float x[8];
-                        if (from_stage && c8 * 8 + 8 <= N) {
-#pragma unroll
-                            for (int q = 0; q < 8; ++q)
-                                x[q] = rowv ? src_s[(c8 * 8 + q) * JS] : 0.f;
-                        } else if (from_stage) {
-#pragma unroll
-                            for (int q = 0; q < 8; ++q)
-                                x[q] = (rowv && c8 * 8 + q < N) ? src_s[(c8 * 8 + q) * JS] : 0.f;
-                        } else {
-#pragma unroll
-                            for (int q = 0; q < 8; ++q)
-                                x[q] = (rowv && c8 * 8 + q < N) ? src_g[(long long)(c8 * 8 + q) * jsg] : 0.f;
-                        }
-                        uint4 tt4[3];
-                        split8<NT>(x, tt4);
-#pragma unroll
-                        for (int tt = 0; tt < NT; ++tt)
-                            tmem_st4(abase + (uint32_t)(tt * (Kn / 2) + c8 * 4), tt4[tt]);
-                    }
-                    tmem_wait_st();
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0)
-                        mbar_arrive(&a_full[ab * kTcMaxKB + kb]);
-                }
-            }
-            for (int kb = 0; kb < nkb && !a.a_tmem; ++kb) {
-                if (!mbar_wait(&a_empty[ab * kTcMaxKB + kb], (na & 1u) ^ 1u)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                const int c8_lo = kb * KB / 8, c8_hi = min(Kn, (kb + 1) * KB) / 8;
-                if (from_stage) {
-                    // staged tile: compile-time stride along j; two chunks in flight
-                    constexpr int JS = NODE ? TE : 1;
-                    const float *src = NODE ? st + row : st + row * N;
-                    const int f_hi = min(full8, c8_hi);
                     int c8 = c8_lo + part;
-                    for (; c8 + Hc < f_hi; c8 += 2 * Hc) {
+                    // two chunks in flight (their loads before either conversion)
+                    for (; c8 + Hc < c8_hi; c8 += 2 * Hc) {
                         float x[8], y[8];
-                        const float *p0 = src + c8 * 8 * JS, *p1 = src + (c8 + Hc) * 8 * JS;
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            x[q] = p0[q * JS];
-                            y[q] = p1[q * JS];
-                        }
+                        load_chunk(c8, x);
+                        load_chunk(c8 + Hc, y);
                         put(c8, x);
                         put(c8 + Hc, y);
                     }
                     for (; c8 < c8_hi; c8 += Hc) {
                         float x[8];
-                        const float *p0 = src + c8 * 8 * JS;
-#pragma unroll
-                        for (int q = 0; q < 8; ++q)
-                            x[q] = (rowv && c8 * 8 + q < N) ? p0[q * JS] : 0.f;
+                        load_chunk(c8, x);
                         put(c8, x);
                     }
-                } else {
-                    // unaligned tail tile read from global memory
-                    const float *src = NODE ? a.u + e0 + row : a.u + (e0 + row) * N;
-                    const long long js = NODE ? E : 1;
-                    for (int c8 = c8_lo + part; c8 < c8_hi; c8 += Hc) {
-                        float x[8];
-#pragma unroll
-                        for (int q = 0; q < 8; ++q)
-                            x[q] = (rowv && c8 * 8 + q < N) ? src[(long long)(c8 * 8 + q) * js] : 0.f;
-                        put(c8, x);
-                    }
+                    block_done(kb);
                 }
-                fence_async_smem();
-                __syncwarp();
-                if (lane == 0)
-                    mbar_arrive(&a_full[ab * kTcMaxKB + kb]);
             }
             if (!ok)
                 break;
-            __syncwarp();
-            if (lane == 0)
-                mbar_arrive(&u_empty[s]);  // every block of this tile has been read from the stage
+            if (!released) {
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(&u_empty[s]);  // every block of this tile has been read from the stage
+            }
             if (*abort_flag)
                 break;
         }

@@ -44,23 +44,17 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                  : "memory");
 }
 
-// One potentially blocking test of an mbarrier phase.  The suspend-time hint lets the
-// hardware park the waiting thread (it wakes when the phase completes, or after the hint)
-// instead of re-issuing the test: spinning warps would otherwise crowd the shared-memory
-// instruction pipe that the working warps need.
-static constexpr uint32_t kSuspendHintNs = 20000;
-
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase)
 {
     uint32_t ok;
     asm volatile(
         "{\n"
         ".reg .pred p;\n"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         "selp.u32 %0, 1, 0, p;\n"
         "}\n"
         : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(phase), "r"(kSuspendHintNs)
+        : "r"(smem_addr(bar)), "r"(phase)
         : "memory");
     return ok != 0;
 }
@@ -74,7 +68,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase)
     for (uint32_t k = 1;; ++k) {
         if (mbar_try_wait(bar, phase))
             return true;
-        if ((k & 15u) == 0 && global_ns() - t0 > kWaitLimitNs)
+        if ((k & 255u) == 0 && global_ns() - t0 > kWaitLimitNs)
             return false;
     }
 }

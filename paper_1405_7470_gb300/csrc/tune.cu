@@ -53,7 +53,8 @@ static std::vector<lc_variant> candidates(int N, int F, int layout, int precisio
         }
     } else {
         const bool node = layout == LC_LAYOUT_NODE_MAJOR;
-        for (int st : {1, 2, 3})
+        // stage ring depth 1, 2, 3, and one stage released early (prefetch_smem = 2)
+        for (int st : {1, 2, 3, 0})
             for (int tpr : {2, 3, 4})
                 for (int g : {0, 1})
                     for (int kbw : {1, 64})
@@ -66,8 +67,8 @@ static std::vector<lc_variant> candidates(int N, int F, int layout, int precisio
                             v.elems_per_thread = kbw;
                             v.split_i = g;
                             v.unroll = tpr;
-                            v.prefetch_smem = 1;
-                            v.stages = st;
+                            v.prefetch_smem = st == 0 ? 2 : 1;
+                            v.stages = st == 0 ? 1 : st;
                             v.store_rows = node ? 0 : rows;
                             out.push_back(v);
                         }
