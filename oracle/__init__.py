@@ -19,6 +19,8 @@ What it computes (all in float64, no reordering of any sum):
 * ``mlp_forward`` / ``mlp_loss_grad`` / ``adam_step``  the cost model's network.
 * ``contract_geo``        out[d,e,i] = sum_f r[e,d,f] sum_j D[f,i,j] u[e,j]: the volume
                           derivative with per-element geometric factors.
+* ``lift``                the surface part of the dG operator: jumps of the traces at
+                          the face nodes, scaled per face, lifted by the lift matrix.
 * ``rel_fro_error``       ||out - ref||_F / ||ref||_F in float64.
 * ``elementwise.evaluate`` one elementwise assignment over a rectangular loop domain,
                           every operation one IEEE float32 operation (module
@@ -76,6 +78,8 @@ def _load():
             lib.oracle_num_threads.restype = ctypes.c_int
             lib.oracle_contract_geo.argtypes = [P, P, P, P, i64, i32, i32, i32, i32, i32]
             lib.oracle_contract_geo.restype = None
+            lib.oracle_lift.argtypes = [P, P, P, P, P, P, i64, i32, i32, i32, i32, i32]
+            lib.oracle_lift.restype = None
             lib.oracle_bf16_round.argtypes = [P, P, i64]
             lib.oracle_bf16_split3.argtypes = [P, P, P, P, i64]
             lib.oracle_mlp_param_count.argtypes = [i32, i32]
@@ -169,6 +173,28 @@ def contract_geo_rows(D, u, r, rows, layout: str = "elem", threads: int = 0) -> 
     if layout == "node":
         return contract_geo(D, u[:, rows].T, np.ascontiguousarray(r[:, :, rows].transpose(2, 0, 1)), "elem", threads)
     return contract_geo(D, u[rows], r[rows], "elem", threads)
+
+
+def lift(L, fmask, vmapP, s, u, out=None, threads: int = 0) -> np.ndarray:
+    """Surface part of the dG operator in float64:
+    out[e,i] (+)= sum_m L[i,m] * s[e, m // Nfp] * (u[e, fmask[m]] - u.flat[vmapP[e,m]]).
+
+    L: (N, M); fmask: (M,) ints; vmapP: (E, M) ints into u.ravel(); s: (E, Nf); u: (E, N).
+    With ``out`` given (E, N) the result is added to a float64 copy of it, else it is returned.
+    """
+    lib = _load()
+    L, s_, u = _f64(L), _f64(s), _f64(u)
+    fmask = np.ascontiguousarray(fmask, dtype=np.int32)
+    vmapP = np.ascontiguousarray(vmapP, dtype=np.int32)
+    E, N = u.shape
+    Nf = s_.shape[1]
+    M = L.shape[1]
+    assert L.shape[0] == N and M % Nf == 0 and fmask.shape == (M,) and vmapP.shape == (E, M)
+    res = np.zeros((E, N)) if out is None else _f64(out).copy()
+    if E > 0:
+        lib.oracle_lift(_ptr(L), _ptr(fmask), _ptr(vmapP), _ptr(s_), _ptr(u), _ptr(res), E, N, Nf, M // Nf,
+                        0 if out is None else 1, int(threads))
+    return res
 
 
 def bf16_round(x) -> np.ndarray:

@@ -118,6 +118,40 @@ void oracle_contract_geo(const double *D, const double *u, const double *r, doub
     (void)nthreads;
 }
 
+/* The surface part of the dG operator (the dG FEM surface workload of Table 1): at every
+ * face node m of element e (face f = m / Nfp, node p = m % Nfp) the jump between the
+ * interior trace u[e, fmask[f][p]] and the exterior trace, the value of u at global node
+ * vmapP[e][m] (a neighbour's matching node; the element's own node on a boundary face),
+ * scaled by the face's factor s[e][f]; the scaled jumps are lifted to the volume nodes:
+ *
+ *   out[e,i] (+)= sum_m L[i,m] * ( s[e, m / Nfp] * (u[e, fmask[m]] - u_flat[vmapP[e,m]]) )
+ *
+ * over { [e,i,m] : 0<=e<E and 0<=i<N and 0<=m<M }, M = Nf * Nfp.  Layouts: L [N][M],
+ * fmask [M] (node of the element for face node m), vmapP [E][M] (index into u as a flat
+ * array of E*N values), s [E][Nf], u and out element-major [E][N].  accumulate != 0 adds
+ * to out, else overwrites it. */
+void oracle_lift(const double *L, const int32_t *fmask, const int32_t *vmapP, const double *sc, const double *u,
+                 double *out, int64_t E, int32_t N, int32_t Nf, int32_t Nfp, int32_t accumulate, int32_t nthreads)
+{
+    const int32_t M = Nf * Nfp;
+#ifdef _OPENMP
+    int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(static) num_threads(nt)
+#endif
+    for (int64_t e = 0; e < E; ++e) {
+        for (int32_t i = 0; i < N; ++i) {
+            double acc = 0.0;
+            for (int32_t m = 0; m < M; ++m) {
+                double jump = u[e * N + fmask[m]] - u[vmapP[e * M + m]];
+                double flux = sc[e * Nf + m / Nfp] * jump;
+                acc += L[(int64_t)i * M + m] * flux;
+            }
+            out[e * N + i] = accumulate ? out[e * N + i] + acc : acc;
+        }
+    }
+    (void)nthreads;
+}
+
 /* Round one binary32 value to bfloat16, nearest-even, returned as a float.
  * The bfloat16 value is the upper half of a binary32 word; the lower 16 bits
  * decide the rounding: above half -> up, below -> down, exactly half -> to

@@ -38,6 +38,8 @@ __all__ = [
     "precision_sweep",
     "grouped_sizes",
     "grouped_operands",
+    "tet_nodes",
+    "surface_mesh",
     "picker_shapes",
     "to_node_major",
     "GROUP_NS",
@@ -118,6 +120,50 @@ def grouped_operands(sizes, F: int = 3, seed: int = 0, dtype=np.float32):
         D, u = operands(e, n, F, dtype, seed=[seed, g + 1])
         out.append((D, u))
     return out
+
+
+def tet_nodes(order: int):
+    """Nodes (a, b, c), a + b + c <= order, of a degree-`order` tetrahedron in lexicographic order,
+    and its four faces' node lists (c = 0, b = 0, a = 0, a + b + c = order), each ascending."""
+    nodes = [(a, b, c) for a in range(order + 1) for b in range(order + 1 - a) for c in range(order + 1 - a - b)]
+    faces = [[k for k, (a, b, c) in enumerate(nodes) if cond(a, b, c)]
+             for cond in (lambda a, b, c: c == 0, lambda a, b, c: b == 0, lambda a, b, c: a == 0,
+                          lambda a, b, c: a + b + c == order)]
+    return nodes, faces
+
+
+def surface_mesh(E: int, order: int = 4, width: int = 64, seed: int = 0, dtype=np.float32):
+    """Synthetic dG surface (lift) problem on E tetrahedra of degree `order` (N = 35 and 4 x 15
+    face nodes for order 4).
+
+    The elements form a periodic-free strip of columns: face 0 of element e meets face 1 of
+    e + 1 (face nodes in reverse order), face 2 meets face 3 of e + width (same order); a face
+    whose neighbour would fall outside [0, E) is a boundary face whose exterior trace is the
+    element's own node (zero jump).  Returns (L, fmask, vmapP, s, u):
+    L (N, 4 Nfp) ~ U[-1, 1); fmask (4 Nfp,) int32; vmapP (E, 4 Nfp) int32 into u.ravel();
+    s (E, 4) ~ U[0.5, 2) per-face scale; u (E, N) ~ N(0, 1); drawn in the order L, s, u.
+    """
+    nodes, faces = tet_nodes(order)
+    N, Nfp = len(nodes), len(faces[0])
+    fmask = np.array([k for f in faces for k in f], dtype=np.int32)
+    M = 4 * Nfp
+    e = np.arange(E, dtype=np.int64)[:, None]
+    p = np.arange(Nfp, dtype=np.int64)[None, :]
+    vmapP = np.empty((E, M), dtype=np.int64)
+    for f, (off, fn, rev) in enumerate(((1, 1, True), (-1, 0, True), (width, 3, False), (-width, 2, False))):
+        nb = e + off
+        q = (Nfp - 1 - p) if rev else p
+        exterior = nb * N + fmask[fn * Nfp + q]
+        interior = e * N + fmask[f * Nfp + p]
+        inside = (nb >= 0) & (nb < E)
+        vmapP[:, f * Nfp:(f + 1) * Nfp] = np.where(inside, exterior, interior)
+    if E * N >= 2 ** 31:
+        raise ValueError("vmapP holds int32 indices")
+    rng = np.random.default_rng(seed)
+    L = rng.uniform(-1.0, 1.0, size=(N, M))
+    s = rng.uniform(0.5, 2.0, size=(E, 4))
+    u = rng.standard_normal(size=(E, N))
+    return _round(L, dtype), fmask, vmapP.astype(np.int32), _round(s, dtype), _round(u, dtype)
 
 
 PATHS = ("fp32", "bf16", "bf16x3")

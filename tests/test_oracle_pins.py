@@ -388,3 +388,84 @@ def test_contract_geo_rows_matches_full():
     assert np.array_equal(oracle.contract_geo_rows(D, u, r, rows), full[:, rows, :])
     rn = np.ascontiguousarray(r.transpose(1, 2, 0))
     assert np.array_equal(oracle.contract_geo_rows(D, synth.to_node_major(u), rn, rows, "node"), full[:, rows, :])
+
+
+# ------------------------------------------------------------------- dG surface lift
+
+def _lift_pin_failures(fn):
+    """Pins of out[e,i] = sum_m L[i,m] s[e,m//Nfp] (u[e,fmask[m]] - u.flat[vmapP[e,m]]) against
+    ``fn(L, fmask, vmapP, s, u)``."""
+    fails = []
+    with open(os.path.join(GOLDEN, "lift_hand.json")) as fh:
+        g = json.load(fh)
+    got = fn(np.array(g["L"], float), np.array(g["fmask"]), np.array(g["vmapP"]), np.array(g["s"], float),
+             np.array(g["u"], float))
+    if not np.array_equal(got, np.array(g["out"], float)):
+        fails.append("hand")
+    L, fmask, vmapP, s, u = synth.surface_mesh(300, order=2, width=8, seed=3, dtype=np.float64)
+    E, N = u.shape
+    Nfp = fmask.size // 4
+    jump = u[:, fmask] - u.ravel()[vmapP]
+    want = (np.repeat(s, Nfp, axis=1) * jump) @ L.T
+    if not np.allclose(fn(L, fmask, vmapP, s, u), want, rtol=1e-13, atol=1e-13):
+        fails.append("einsum")
+    own = (np.arange(E)[:, None] * N + fmask[None, :]).astype(np.int32)  # every face a boundary face
+    if np.any(fn(L, fmask, own, s, u) != 0.0):
+        fails.append("boundary_zero")
+    v = np.random.default_rng(1).standard_normal(u.shape)
+    if not np.allclose(fn(L, fmask, vmapP, s, 2 * u - v), 2 * fn(L, fmask, vmapP, s, u) - fn(L, fmask, vmapP, s, v),
+                       rtol=1e-12, atol=1e-12):
+        fails.append("linear_u")
+    # a constant field has no jumps anywhere
+    if np.any(fn(L, fmask, vmapP, s, np.full(u.shape, 3.25)) != 0.0):
+        fails.append("constant_field")
+    Li = np.random.default_rng(2).integers(-3, 4, L.shape).astype(float)
+    si = np.random.default_rng(3).integers(1, 4, s.shape).astype(float)
+    ui = np.random.default_rng(4).integers(-8, 9, u.shape).astype(float)
+    wanti = (np.repeat(si, Nfp, axis=1) * (ui[:, fmask] - ui.ravel()[vmapP])) @ Li.T
+    if not np.array_equal(fn(Li, fmask, vmapP, si, ui), wanti):
+        fails.append("integer_exact")
+    return fails
+
+
+def test_lift_passes_every_pin():
+    assert _lift_pin_failures(oracle.lift) == []
+
+
+@pytest.mark.parametrize("kind", ["sign", "face_index", "transpose_L", "none"])
+def test_lift_pins_catch_planted_mistakes(kind):
+    def fn(L, fmask, vmapP, s, u):
+        E, N = u.shape
+        M = L.shape[1]
+        Nf = s.shape[1]
+        Nfp = M // Nf
+        uf = u.ravel()
+        out = np.zeros((E, N))
+        for e in range(E):
+            for m in range(M):
+                jump = u[e, fmask[m]] - uf[vmapP[e, m]]
+                if kind == "sign":
+                    jump = -jump
+                f = m % Nf if kind == "face_index" else m // Nfp
+                flux = s[e, f] * jump
+                for i in range(N):
+                    lim = L[m % N, (i * Nfp + m) % M] if kind == "transpose_L" else L[i, m]
+                    out[e, i] += lim * flux
+        return out
+    fails = _lift_pin_failures(fn)
+    assert (fails == []) if kind == "none" else fails, kind
+
+
+def test_surface_mesh_is_consistent():
+    """Every interior face-node pair is matched both ways; boundary faces point at the element."""
+    L, fmask, vmapP, s, u = synth.surface_mesh(500, order=4, width=16, seed=0)
+    E, N = u.shape
+    M = fmask.size
+    assert N == 35 and M == 60
+    src = (np.arange(E)[:, None] * N + fmask[None, :]).ravel()
+    dst = vmapP.ravel().astype(np.int64)
+    pairs = set(zip(src.tolist(), dst.tolist()))
+    for a, b in list(pairs)[:5000]:
+        assert (b, a) in pairs or a == b
+    nodes, faces = synth.tet_nodes(4)
+    assert all(len(f) == 15 for f in faces) and len(nodes) == 35
