@@ -53,6 +53,9 @@ WORKLOADS.update({
     "geo": dict(E=1 << 21, N=35, F=3, precision="bf16x3",
                 desc="volume derivative with per-element geometric factors E=2^21 N=35 F=3 "
                      "(out[d,e,i] = sum_f r[e,d,f] sum_j D[f,i,j] u[e,j])"),
+    "lift": dict(E=1 << 21, N=35, F=1, precision="fp32",
+                 desc="dG surface lift E=2^21 tetrahedra of degree 4 (N=35, 4 faces x 15 nodes), FP32: "
+                      "trace jumps through the face-node map, per-face scale, lift matrix"),
     "saxpy": dict(E=1 << 28, N=1, F=1, precision="fp32",
                   desc="saxpy z[i] = a*x[i] + y[i], n=2^28 floats, through the elementwise front end"),
 })
@@ -69,6 +72,7 @@ PER_CONFIG = [
     ("grouped", ["--workload", "grouped"]),
     ("geo/bf16x3", ["--workload", "geo"]),
     ("saxpy", ["--workload", "saxpy"]),
+    ("lift", ["--workload", "lift"]),
 ]
 
 L2_BYTES = 129 * 1000 * 1000  # GB300 L2
@@ -333,7 +337,7 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     wl = dict(WORKLOADS[args.workload])
     wl["storage"] = "fp64" if wl["precision"] == "fp64" else "fp32"
-    if not args.precision and wl["storage"] == "fp32" and args.workload not in ("grouped", "saxpy", "geo"):
+    if not args.precision and wl["storage"] == "fp32" and args.workload not in ("grouped", "saxpy", "geo", "lift"):
         args.precision = "bf16x3"
     if args.precision:
         if (args.precision == "fp64") != (wl["storage"] == "fp64"):
@@ -355,6 +359,8 @@ def main():
         return run_geo(args, wl, world, rank, local_rank)
     if args.workload == "saxpy":
         return run_saxpy(args, wl, world, rank, local_rank)
+    if args.workload == "lift":
+        return run_lift(args, wl, world, rank, local_rank)
 
     import torch
     import torch.distributed as dist
@@ -932,6 +938,89 @@ def run_saxpy(args, wl, world, rank, local_rank):
         dist.destroy_process_group()
 
 
+def run_lift(args, wl, world, rank, local_rank):
+    """Surface lift of the dG operator (lc_lift), FP32: one launch per step over the synthetic
+    tetrahedral mesh; GB/s (gathered traces counted once) and GFLOP/s."""
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    import synth
+    from paper_1405_7470_gb300 import lc
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    lc.load()
+    peaks = load_peaks()
+    E = wl["E"]
+    L, fmask, vmapP, s, u = synth.surface_mesh(E, order=4, width=64, seed=0)
+    N, M = u.shape[1], fmask.size
+    k = lc.Kernel(lc.LIFT_DOMAIN, lc.LIFT_INSTRUCTION)
+    Ld, fd, vd, sd, ud = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (L, fmask, vmapP, s, u))
+    out = torch.zeros((E, N), device="cuda")
+    stream = torch.cuda.Stream()
+    best = None
+    for ctas in (1, 2, 3, 4, 6, 8):
+        v = lc.variant_default(k, E, N, 1, "elem", "fp32")
+        v.ctas_per_sm = ctas
+        with torch.cuda.stream(stream):
+            lc.lift(k, v, Ld, fd, vd, sd, ud, out, stream=stream)
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(stream)
+            for _ in range(3):
+                lc.lift(k, v, Ld, fd, vd, sd, ud, out, stream=stream)
+            b_.record(stream)
+        b_.synchronize()
+        t = a_.elapsed_time(b_) / 3
+        if best is None or t < best[0]:
+            best = (t, v)
+    v = best[1]
+    flops = 2.0 * E * N * M + 3.0 * E * M
+    nbytes = 4.0 * (E * N + E * M + E * 4 + E * N + N * M + M)  # u, vmapP, s, out, L, fmask
+
+    def step():
+        lc.lift(k, v, Ld, fd, vd, sd, ud, out, stream=stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    with torch.cuda.stream(stream):
+        total_ms, per = _timed_steps(torch, stream, step, args.steps)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = total_ms / args.steps
+    launch_s = statistics.mean(per) * 1e-3
+    rel_err = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rows = np.random.default_rng(1).integers(0, E, 20000)
+        got = out.index_select(0, torch.from_numpy(rows).cuda()).cpu().numpy()
+        rel_err = oracle.rel_fro_error(got, oracle.lift(L, fmask, vmapP, s, u)[rows])
+    if lc.device_error() != 0:
+        raise RuntimeError("device error word set during the timed region")
+    if rank == 0:
+        ach = nbytes / launch_s / 1e9
+        line = {
+            "metric": "contraction GFLOP/s", "value": flops * world / (ms * 1e-3) / 1e9, "unit": "GFLOP/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl["desc"], "E": E, "N": N, "M": M, "variant": lc.variant_dict(v),
+                       "variant_choice": "fastest CTAs/SM of 6", "bytes_per_step": nbytes,
+                       "l2": "inputs+outputs larger than L2 (no flush needed)"},
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": peaks["source"]},
+            "cpu_baseline": None, "e2e": None, "gpu_launches": args.steps, "clocks": clk,
+            "rel_error_vs_oracle": rel_err, "hbm_gbs_achieved": nbytes / (ms * 1e-3) / 1e9,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def run_per_config(args, rank) -> dict:
     """Each configuration of PER_CONFIG in its own process (after the headline's timed
     region): value, roofline fraction, error against the oracle, clocks."""
@@ -976,7 +1065,7 @@ def run_reference(args, wl):
         D, u = synth.fp32_three()
     if args.workload == "grouped":
         return run_reference_grouped(args, wl)
-    if args.workload in ("geo", "saxpy"):
+    if args.workload in ("geo", "saxpy", "lift"):
         return run_reference_other(args, wl)
     Es = min(E, 1 << 18)
     sub = u[:Es]
@@ -1011,7 +1100,13 @@ def run_reference_other(args, wl):
     import oracle
     import oracle.elementwise as ew
     import synth
-    if args.workload == "geo":
+    if args.workload == "lift":
+        Es = 1 << 16
+        L, fmask, vmapP, s, u = synth.surface_mesh(Es, order=4, width=64, seed=0)
+        work = 2.0 * Es * 35 * fmask.size + 3.0 * Es * fmask.size
+        one = lambda: oracle.lift(L, fmask, vmapP, s, u)
+        metric, unit, sample = "contraction GFLOP/s", "GFLOP/s", f"{Es} elements per step"
+    elif args.workload == "geo":
         Es, N, F = 1 << 16, wl["N"], wl["F"]
         D, u = synth.fp32_three(E=Es)
         r = np.random.default_rng(9).uniform(-2, 2, size=(Es, F, F)).astype(np.float32)
@@ -1032,11 +1127,11 @@ def run_reference_other(args, wl):
         one()
     dt = (time.perf_counter() - t0) / args.steps
     value = work / dt / 1e9
-    cores = oracle.num_threads() if args.workload == "geo" else 1
+    cores = oracle.num_threads() if args.workload in ("geo", "lift") else 1
     line = {
         "metric": metric, "value": value, "unit": unit, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.workload == "geo" else "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32" if args.workload == "saxpy" else "f64", "data": "synthetic",
         "config": {"workload": wl["desc"]}, "impl": "reference",
         "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": unit, "sample": sample},
         "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

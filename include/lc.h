@@ -54,7 +54,8 @@ typedef enum lc_status {
     LC_ERR_CUDA = 7,             /* a CUDA runtime call failed; see lc_last_cuda_error */
     LC_ERR_TIMEOUT = 8,          /* a bounded device wait gave up (device error word) */
     LC_ERR_NO_DEVICE = 9,        /* no sm_103 device current */
-    LC_ERR_NOT_FOUND = 10        /* lookup failed (e.g. no timing for a candidate) */
+    LC_ERR_NOT_FOUND = 10,       /* lookup failed (e.g. no timing for a candidate) */
+    LC_ERR_INDEX = 11            /* an index array held an entry out of range (device error word) */
 } lc_status;
 
 /* Human-readable name of a status. Never NULL. */
@@ -124,8 +125,8 @@ struct lc_variant {
                                  row: the same, 2 for 4) */
     int32_t prefetch_smem;    /* add_prefetch of the u tile into shared memory by TMA (1) or
                                  direct global loads into registers (0); tensor-core engine: 1,
-                                 or 2 = each converting thread takes its values into registers
-                                 and frees the stage at once (K of one block only) */
+                                 or (BF16) 2 = each converting thread takes its values into
+                                 registers and frees the stage at once (K of one block only) */
     int32_t tail_free;        /* 1: no guard on the last e tile; only accepted when an
                                  assumption "E mod m = 0" with m a multiple of tile_e holds */
     int32_t stages;           /* u tiles in flight in shared memory (TMA ring depth), >= 1 */
@@ -291,7 +292,9 @@ lc_status lc_elementwise(const lc_kernel *k, const lc_variant *v, const int64_t 
  * the output is written once instead of twice, and the F partial results never reach memory.
  * Tensor-core engine only (LC_PREC_BF16, or LC_PREC_BF16X3 for FP32-level accuracy), F = 2
  * or 3, every operator in one column block (split_i 0 or F), element-major store_rows 0 or
- * 128.
+ * 128.  The accumulators of all F operators and a whole-tile staging slot of F outputs must
+ * fit one SM: element-major BF16X3 plans exist up to N = 48 for F = 3 and N = 64 for F = 2
+ * (lc_variant_default returns LC_ERR_UNSUPPORTED beyond).
  *   D_dev    [F][N][N] float       u_dev  layout per v->layout
  *   r_dev    element-major [E][F][F] (r[(e*F + d)*F + f]); node-major [F][F][E]
  *   out_dev  element-major [F][E][N], node-major [F][N][E] (d in place of f); must not
@@ -301,6 +304,32 @@ lc_status lc_elementwise(const lc_kernel *k, const lc_variant *v, const int64_t 
  */
 lc_status lc_contract_geo(const lc_kernel *k, const lc_variant *v, const void *D_dev, const void *u_dev,
                           const void *r_dev, void *out_dev, int64_t E, int32_t N, int32_t F, void *stream);
+
+/*
+ * The surface part of the dG operator (the dG FEM surface workload of Table 1): at each face
+ * node the jump between the interior and the exterior trace, scaled per face, lifted to the
+ * volume nodes by the lift matrix:
+ *
+ *     out[e, i] (+)= sum_{f,p} L[i, f, p] * s[e, f] * (u[e, fmask[f, p]] - u_flat[vmapP[e, f, p]])
+ *
+ * stated to lc_kernel_create as the domain { [e,i,f,p] : 0<=e<E and 0<=i<N and 0<=f<Nf and
+ * 0<=p<Nfp } and, in exactly this form (names free), the instruction
+ * "out[e,i] = sum((f,p), L[i,f,p]*s[e,f]*(u[e,fmask[f,p]] - u[vmapP[e,f,p]]))" (u read as a
+ * flat array through vmapP).  FP32 SIMT engine (the contraction over f, p is short: about 5
+ * flops per byte moved), element-major.
+ *   L_dev      [N][Nf*Nfp] float          fmask_dev  [Nf*Nfp] int32, each in [0, N)
+ *   vmapP_dev  [E][Nf*Nfp] int32, each in [0, E*N) (the element's own node on boundary faces)
+ *   s_dev      [E][Nf] float               u_dev, out_dev  [E][N] float, out not overlapping
+ *   accumulate 1: out += the lifted fluxes; 0: out = them
+ * Sizes: 1 <= N <= 128, Nf * Nfp <= 256, E * N < 2^31.  Descriptor: engine SIMT, FP32,
+ * element-major; ctas_per_sm (0 = 4) and max_ctas size the persistent grid.  An index out
+ * of range is not followed: its flux becomes NaN and lc_device_error reports LC_ERR_INDEX.
+ * Errors: LC_ERR_INVALID_ARGUMENT, LC_ERR_INVALID_VARIANT, LC_ERR_MISALIGNED (4-byte),
+ * LC_ERR_NO_DEVICE, LC_ERR_UNSUPPORTED (not a kernel of this form), LC_ERR_CUDA.
+ */
+lc_status lc_lift(const lc_kernel *k, const lc_variant *v, const float *L_dev, const int32_t *fmask_dev,
+                  const int32_t *vmapP_dev, const float *s_dev, const float *u_dev, float *out_dev, int64_t E,
+                  int32_t N, int32_t Nf, int32_t Nfp, int32_t accumulate, void *stream);
 
 /*
  * The contraction on host arrays: copies D and u from host to the caller's device
@@ -326,8 +355,8 @@ lc_status lc_contract_host(const lc_kernel *k, const lc_variant *v, const void *
 
 /*
  * Device error word: returns LC_ERR_TIMEOUT if any kernel recorded a bounded
- * wait that gave up since the last clear, else LC_OK.  Synchronises the device.
- * clear != 0 resets the word.
+ * wait that gave up since the last clear, else LC_ERR_INDEX if a kernel met an index out
+ * of range (lc_lift), else LC_OK.  Synchronises the device.  clear != 0 resets the word.
  */
 lc_status lc_device_error(int clear);
 

@@ -617,6 +617,80 @@ static bool parse_geo_instruction(const char *text, Kernel &K, std::string &why)
     return true;
 }
 
+// Surface lift of the dG operator, in exactly this form (names free, bound on first use):
+//   "out[e,i] = sum((f,p), L[i,f,p]*s[e,f]*(u[e,fmask[f,p]] - u[vmapP[e,f,p]]))"
+// over { [e,i,f,p] : ... }: the jump between the interior trace u[e, fmask[f,p]] and the
+// exterior trace u[vmapP[e,f,p]] (u read as a flat array through the map), scaled per face,
+// lifted to the volume nodes.
+static bool parse_lift_instruction(const char *text, Kernel &K, std::string &why)
+{
+    std::vector<Tok> toks;
+    if (!tokenize(text, toks)) {
+        why = "instruction: bad character";
+        return false;
+    }
+    static const char *pat[] = {"$out", "[", "$e", ",", "$i", "]", "=", "#sum", "(", "(", "$f", ",", "$p", ")", ",",
+                                "$L", "[", "$i", ",", "$f", ",", "$p", "]", "*", "$s", "[", "$e", ",", "$f", "]", "*",
+                                "(", "$u", "[", "$e", ",", "$fm", "[", "$f", ",", "$p", "]", "]", "-", "$u", "[",
+                                "$vm", "[", "$e", ",", "$f", ",", "$p", "]", "]", ")", ")"};
+    std::map<std::string, std::string> bind;
+    size_t t = 0;
+    for (const char *q : pat) {
+        if (t >= toks.size())
+            return false;
+        const Tok &tk = toks[t++];
+        if (q[0] == '$') {
+            if (tk.kind != Tok::ID)
+                return false;
+            auto it = bind.find(q);
+            if (it == bind.end())
+                bind[q] = tk.s;
+            else if (it->second != tk.s)
+                return false;
+        } else if (q[0] == '#') {
+            if (tk.kind != Tok::ID || tk.s != q + 1)
+                return false;
+        } else if (tk.kind != Tok::OP || tk.s != q) {
+            return false;
+        }
+    }
+    if (toks[t].kind != Tok::END)
+        return false;
+    const std::set<std::string> in = {bind["$e"], bind["$i"], bind["$f"], bind["$p"]};
+    if (in.size() != 4 || in != std::set<std::string>(K.inames.begin(), K.inames.end())) {
+        why = "instruction: inames differ from the domain's";
+        return false;
+    }
+    const std::set<std::string> arrays = {bind["$out"], bind["$L"], bind["$s"], bind["$u"], bind["$fm"], bind["$vm"]};
+    if (arrays.size() != 6) {
+        why = "instruction: arrays must be distinct";
+        return false;
+    }
+    auto bound = [&](const std::string &n) {
+        return K.bounds[std::find(K.inames.begin(), K.inames.end(), n) - K.inames.begin()];
+    };
+    if (std::set<std::string>{bound(bind["$e"]), bound(bind["$i"]), bound(bind["$f"]), bound(bind["$p"])}.size() != 4) {
+        why = "instruction: E, N, Nf and Nfp must be distinct parameters";
+        return false;
+    }
+    K.kind = KIND_LIFT;
+    K.out_name = bind["$out"];
+    K.d_name = bind["$L"];
+    K.s_name = bind["$s"];
+    K.u_name = bind["$u"];
+    K.fmask_name = bind["$fm"];
+    K.vmap_name = bind["$vm"];
+    K.e_iname = bind["$e"];
+    K.i_iname = bind["$i"];
+    K.f_iname = bind["$f"];
+    K.p_iname = bind["$p"];
+    K.E_param = bound(bind["$e"]);
+    K.N_param = bound(bind["$i"]);
+    K.Nf_param = bound(bind["$f"]);
+    K.Nfp_param = bound(bind["$p"]);
+    return true;
+}
+
 // Elementwise instruction "lhs[i0, i1] = expr" over a domain of one or two inames: expr is
 // built from +, -, *, / (left-associative, * and / binding tighter), unary minus,
 // parentheses, decimal literals, scalar parameters (unindexed names) and array accesses
@@ -814,7 +888,7 @@ static bool parse_assumptions(const char *text, Kernel &K, std::string &why)
     std::set<std::string> params = {K.E_param, K.N_param};
     if (!K.F_param.empty())
         params.insert(K.F_param);
-    if (K.kind == KIND_ELEMENTWISE)
+    if (K.kind == KIND_ELEMENTWISE || K.kind == KIND_LIFT)
         params = std::set<std::string>(K.bounds.begin(), K.bounds.end());
     for (;;) {
         Assumption a;
@@ -972,6 +1046,14 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         return LC_ERR_INVALID_VARIANT;
     if (v->ctas_per_sm < 0 || v->ctas_per_sm > 32 || v->max_ctas < 0)
         return LC_ERR_INVALID_VARIANT;
+    const bool geo = K.kind == KIND_GEO;
+    if (geo) {
+        // every operator in one column block (the epilogue mixes all F partial sums of a node);
+        // kernel instances exist for F = 2 and 3; whole-tile staging slots
+        if (v->engine != LC_ENGINE_TCGEN05 || F < 2 || F > 3 || !(v->split_i == 0 || v->split_i == F) ||
+            !(v->store_rows == 0 || v->store_rows == 128))
+            return LC_ERR_INVALID_VARIANT;
+    }
     r.engine = v->engine;
     r.layout = v->layout;
     r.precision = v->precision;
@@ -1060,14 +1142,6 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         g.grid = (int)grid;
         return LC_OK;
     }
-    const bool geo = K.kind == KIND_GEO;
-    if (geo) {
-        // every operator in one column block (the epilogue mixes all F partial sums of a node);
-        // kernel instances exist for F = 2 and 3; whole-tile staging slots
-        if (v->engine != LC_ENGINE_TCGEN05 || F < 2 || F > 3 || !(v->split_i == 0 || v->split_i == F) ||
-            !(v->store_rows == 0 || v->store_rows == 128))
-            return LC_ERR_INVALID_VARIANT;
-    }
     if (v->engine == LC_ENGINE_TCGEN05) {
         if (v->precision != LC_PREC_BF16 && v->precision != LC_PREC_BF16X3)
             return LC_ERR_INVALID_VARIANT;
@@ -1076,7 +1150,7 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         // elems_per_thread = K-block width (16, 32 or 64 bf16 = 32/64/128-byte swizzle rows),
         // K padded to a multiple of it; 1 = the widest block that divides K padded to 16
         const int kbw = v->elems_per_thread;
-        if (v->tile_e != 128 || !(v->prefetch_smem == 1 || v->prefetch_smem == 2) ||
+        if (v->tile_e != 128 || !(v->prefetch_smem == 1 || (v->prefetch_smem == 2 && v->precision == LC_PREC_BF16)) ||
             !(kbw == 1 || kbw == 16 || kbw == 32 || kbw == 64) ||
             v->unroll < 1 || v->unroll > 4)
             return LC_ERR_INVALID_VARIANT;
@@ -1265,6 +1339,7 @@ const char *lc_status_string(lc_status s)
     case LC_ERR_TIMEOUT: return "LC_ERR_TIMEOUT";
     case LC_ERR_NO_DEVICE: return "LC_ERR_NO_DEVICE";
     case LC_ERR_NOT_FOUND: return "LC_ERR_NOT_FOUND";
+    case LC_ERR_INDEX: return "LC_ERR_INDEX";
     }
     return "LC_ERR_UNKNOWN";
 }
@@ -1286,6 +1361,10 @@ lc_status lc_kernel_create(const char *domain, const char *instructions, const c
     if (!parsed) {
         K = base;
         parsed = parse_geo_instruction(instructions, K, why);
+    }
+    if (!parsed) {
+        K = base;
+        parsed = parse_lift_instruction(instructions, K, why);
     }
     if (!parsed) {
         K = base;
@@ -1330,6 +1409,48 @@ lc_status lc_kernel_print(const lc_kernel *kh, const lc_variant *v, char *buf, s
     std::string s;
     const char *rule = "------------------------------------------------------\n";
     const bool geo = K.kind == KIND_GEO;
+    if (K.kind == KIND_LIFT) {
+        const char *E = K.E_param.c_str(), *N = K.N_param.c_str(), *Nf = K.Nf_param.c_str(),
+                   *Nfp = K.Nfp_param.c_str();
+        s += rule;
+        s += "KERNEL: dg_surface_lift\n";
+        s += rule;
+        s += "ARGUMENTS:\n";
+        appendf(s, "%s: GlobalArg, type: float32, shape: (%s, %s, %s), dim_tags: (stride:%s*%s, stride:%s, stride:1)\n",
+                K.d_name.c_str(), N, Nf, Nfp, Nf, Nfp, Nfp);
+        appendf(s, "%s: GlobalArg, type: int32, shape: (%s, %s), dim_tags: (stride:%s, stride:1)\n",
+                K.fmask_name.c_str(), Nf, Nfp, Nfp);
+        appendf(s, "%s: GlobalArg, type: int32, shape: (%s, %s, %s), dim_tags: (stride:%s*%s, stride:%s, stride:1)\n",
+                K.vmap_name.c_str(), E, Nf, Nfp, Nf, Nfp, Nfp);
+        appendf(s, "%s: GlobalArg, type: float32, shape: (%s, %s), dim_tags: (stride:%s, stride:1)\n",
+                K.s_name.c_str(), E, Nf, Nf);
+        appendf(s, "%s: GlobalArg, type: float32, shape: (%s, %s), dim_tags: (stride:%s, stride:1)\n",
+                K.u_name.c_str(), E, N, N);
+        appendf(s, "%s: GlobalArg, type: float32, shape: (%s, %s), dim_tags: (stride:%s, stride:1), output\n",
+                K.out_name.c_str(), E, N, N);
+        s += rule;
+        s += "DOMAINS:\n";
+        appendf(s, "[%s, %s, %s, %s] -> { [%s, %s, %s, %s] : 0 <= %s < %s and 0 <= %s < %s and 0 <= %s < %s and "
+                   "0 <= %s < %s }\n",
+                E, N, Nf, Nfp, K.e_iname.c_str(), K.i_iname.c_str(), K.f_iname.c_str(), K.p_iname.c_str(),
+                K.e_iname.c_str(), E, K.i_iname.c_str(), N, K.f_iname.c_str(), Nf, K.p_iname.c_str(), Nfp);
+        if (!K.assumptions.empty()) {
+            s += rule;
+            appendf(s, "ASSUMPTIONS: %s\n", K.assumptions_text.c_str());
+        }
+        s += rule;
+        s += "INSTRUCTIONS:\n";
+        appendf(s, "[%s, %s] %s\n", K.e_iname.c_str(), K.i_iname.c_str(), K.insn_text.c_str());
+        s += rule;
+        if (needed)
+            *needed = s.size() + 1;
+        if (!buf || cap == 0)
+            return LC_ERR_BUFFER_TOO_SMALL;
+        size_t n = std::min(cap - 1, s.size());
+        memcpy(buf, s.data(), n);
+        buf[n] = 0;
+        return n < s.size() ? LC_ERR_BUFFER_TOO_SMALL : LC_OK;
+    }
     if (K.kind == KIND_ELEMENTWISE) {
         const bool two = K.inames.size() == 2;
         s += rule;
@@ -1500,6 +1621,17 @@ lc_status lc_variant_validate(const lc_kernel *kh, int64_t E, int32_t N, int32_t
 {
     if (!kh)
         return LC_ERR_INVALID_ARGUMENT;
+    if (kh->k.kind == KIND_LIFT) {
+        // E and N as for lc_lift; the descriptor: FP32 SIMT, element-major, grid fields
+        if (!v || v->struct_size != sizeof(lc_variant))
+            return LC_ERR_INVALID_ARGUMENT;
+        if (E < 0 || N < 1 || N > 128)
+            return LC_ERR_INVALID_ARGUMENT;
+        return (v->engine == LC_ENGINE_SIMT && v->precision == LC_PREC_FP32 && v->layout == LC_LAYOUT_ELEM_MAJOR &&
+                v->ctas_per_sm >= 0 && v->ctas_per_sm <= 8 && v->max_ctas >= 0)
+                   ? LC_OK
+                   : LC_ERR_INVALID_VARIANT;
+    }
     if (kh->k.kind == KIND_ELEMENTWISE) {
         // the extents of the first and second iname come as E and N; F must be 1
         const int64_t ext[2] = {E, N};
@@ -1586,6 +1718,20 @@ lc_status lc_variant_default(const lc_kernel *kh, int64_t E, int32_t N, int32_t 
     lc_variant d;
     memset(&d, 0, sizeof d);
     d.struct_size = sizeof(lc_variant);
+    if (kh->k.kind == KIND_LIFT) {
+        if (precision != LC_PREC_FP32 || layout != LC_LAYOUT_ELEM_MAJOR)
+            return LC_ERR_UNSUPPORTED;
+        d.engine = LC_ENGINE_SIMT;
+        d.precision = LC_PREC_FP32;
+        d.tile_e = 64;
+        d.elems_per_thread = 4;
+        d.split_i = 4;
+        d.unroll = 4;
+        d.stages = 1;
+        d.ctas_per_sm = 4;
+        *v = d;
+        return LC_OK;
+    }
     if (kh->k.kind == KIND_ELEMENTWISE) {
         // 16-byte vectors, four per thread and tile, four CTAs per SM; FP32
         if (precision != LC_PREC_FP32 || layout != LC_LAYOUT_ELEM_MAJOR)
@@ -1656,6 +1802,8 @@ lc_status lc_variant_default(const lc_kernel *kh, int64_t E, int32_t N, int32_t 
         }
         if (st != LC_ERR_INVALID_VARIANT)
             return st;
+        if (kh->k.kind == KIND_GEO)
+            return LC_ERR_UNSUPPORTED;  // the volume derivative runs on the tensor cores only
         // no tensor-core plan fits (large N): FP32 SIMT, whose error is below both
         // reduced-precision bounds
         return lc_variant_default(kh, E, N, F, layout, LC_PREC_FP32, v);
@@ -2193,7 +2341,7 @@ lc_status lc_device_error(int clear)
         if (e != cudaSuccess)
             return cuda_fail(e);
     }
-    return h ? LC_ERR_TIMEOUT : LC_OK;
+    return (h & 1u) ? LC_ERR_TIMEOUT : (h & 2u) ? LC_ERR_INDEX : LC_OK;
 }
 
 lc_status lc_grouped_workspace_size(const lc_kernel *kh, const lc_variant *v, const lc_group *groups,

@@ -372,7 +372,7 @@ lc_status lc_kernel_signature(const lc_kernel *kh, int32_t *n_arrays, int32_t *n
         *n_arrays = (int32_t)K.ew.arrays.size();
         *n_params = (int32_t)K.ew.params.size();
     } else {
-        *n_arrays = K.kind == KIND_GEO ? 4 : 3;
+        *n_arrays = K.kind == KIND_GEO ? 4 : K.kind == KIND_LIFT ? 6 : 3;
         *n_params = 0;
     }
     *n_dims = (int32_t)K.inames.size();
@@ -400,6 +400,8 @@ lc_status lc_kernel_arg_name(const lc_kernel *kh, int32_t what, int32_t index, c
         std::vector<std::string> arrs = {K.out_name, K.d_name, K.u_name};
         if (K.kind == KIND_GEO)
             arrs.push_back(K.g_name);
+        if (K.kind == KIND_LIFT)
+            arrs = {K.out_name, K.d_name, K.fmask_name, K.vmap_name, K.s_name, K.u_name};
         if (what != 0 || index >= (int)arrs.size())
             return LC_ERR_INVALID_ARGUMENT;
         name = arrs[index];

@@ -19,7 +19,7 @@ struct Assumption {
 };
 
 // What the instruction computes (each kind has its own entry point).
-enum KernelKind { KIND_CONTRACT = 0, KIND_GEO = 1, KIND_ELEMENTWISE = 2 };
+enum KernelKind { KIND_CONTRACT = 0, KIND_GEO = 1, KIND_ELEMENTWISE = 2, KIND_LIFT = 3 };
 
 // Elementwise instruction: an expression tree over array loads, scalar parameters and
 // constants.  arrays[0] is the output; the inputs follow in order of first appearance.
@@ -45,6 +45,7 @@ struct Kernel {
     int kind = KIND_CONTRACT;
     std::string g_name, d_iname;      // KIND_GEO: geometric-factor array G[e,d,f], physical-derivative iname
     Elementwise ew;                   // KIND_ELEMENTWISE
+    std::string s_name, fmask_name, vmap_name, p_iname, Nf_param, Nfp_param;  // KIND_LIFT
     std::vector<std::string> inames;  // as written in the domain
     std::vector<std::string> bounds;  // parameter bounding each iname
     std::string out_name, d_name, u_name;
@@ -134,6 +135,23 @@ struct TcArgs {
 };
 
 lc_status tc_launch(const TcArgs &a, int layout, int nterms, int grid, cudaStream_t s);
+
+// Surface lift of the dG operator (lift.cu).
+struct LiftArgs {
+    const float *L;        // [N][M] lift matrix
+    const int *fmask;      // [M] element node of face node m
+    const int *vmapP;      // [E][M] exterior trace: index into u as a flat array
+    const float *s;        // [E][Nf] per-face scale
+    const float *u;        // [E][N]
+    float *out;            // [E][N]
+    long long E;
+    int N, Nf, Nfp, M;
+    int accumulate;
+    unsigned int *err;     // device error word: bit 1 set on an index out of range
+};
+lc_status lift_launch(const LiftArgs &a, int grid, cudaStream_t s);
+size_t lift_smem_bytes(int N, int M);
+int lift_threads(int N);
 
 // Elementwise kernels: check a descriptor against extents (one per iname) without launching;
 // reports the grid and the number of tiles.

@@ -479,7 +479,9 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
         int k = 0;
         bool ok = true;
         const int nch8 = Kn / 8;
-        const int my_chunks = (nkb == 1 && a.early_release) ? (nch8 - part + Hc - 1) / Hc : kMaxEarly + 1;
+        // (BF16 only: holding 3 x 8 values across the three-term split would spill registers)
+        const int my_chunks =
+            (NT == 1 && nkb == 1 && a.early_release) ? (nch8 - part + Hc - 1) / Hc : kMaxEarly + 1;
         const uint32_t lane_q = (uint32_t)(32 * (warp & 3)) << 16;
         for (long long t = my_first; t < a.ntiles && ok; t += my_step, ++k) {
             const int s = k % S, ab = k % NA;
@@ -545,7 +547,7 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
                     mbar_arrive(&a_full[ab * kTcMaxKB + kb]);
             };
             bool released = false;
-            if (from_stage && my_chunks <= kMaxEarly) {
+            if (NT == 1 && from_stage && my_chunks <= kMaxEarly) {
                 float xv[kMaxEarly][8];
 #pragma unroll
                 for (int m = 0; m < kMaxEarly; ++m)

@@ -22,7 +22,7 @@ LC_OK = 0
 STATUS = {
     0: "LC_OK", 1: "LC_ERR_INVALID_ARGUMENT", 2: "LC_ERR_UNSUPPORTED", 3: "LC_ERR_INVALID_VARIANT",
     4: "LC_ERR_ASSUMPTION", 5: "LC_ERR_MISALIGNED", 6: "LC_ERR_BUFFER_TOO_SMALL", 7: "LC_ERR_CUDA",
-    8: "LC_ERR_TIMEOUT", 9: "LC_ERR_NO_DEVICE", 10: "LC_ERR_NOT_FOUND",
+    8: "LC_ERR_TIMEOUT", 9: "LC_ERR_NO_DEVICE", 10: "LC_ERR_NOT_FOUND", 11: "LC_ERR_INDEX",
 }
 ENGINE = {"simt": 0, "tcgen05": 1, "warp": 2}
 LAYOUT = {"elem": 0, "node": 1}
@@ -76,6 +76,7 @@ SIGNATURES = {
     "lc_variant_plan": ([_P, _I64, _I32, _I32, _VP, ctypes.POINTER(lc_plan)], ctypes.c_int),
     "lc_contract": ([_P, _VP, _P, _P, _P, _I64, _I32, _I32, _P], ctypes.c_int),
     "lc_contract_geo": ([_P, _VP, _P, _P, _P, _P, _I64, _I32, _I32, _P], ctypes.c_int),
+    "lc_lift": ([_P, _VP, _P, _P, _P, _P, _P, _P, _I64, _I32, _I32, _I32, _I32, _P], ctypes.c_int),
     "lc_kernel_signature": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)], ctypes.c_int),
     "lc_kernel_arg_name": ([_P, _I32, _I32, ctypes.c_char_p, _SZ], ctypes.c_int),
     "lc_elementwise_source": ([_P, _VP, _P, ctypes.c_char_p, _SZ, ctypes.POINTER(_SZ)], ctypes.c_int),
@@ -261,6 +262,29 @@ def contract_geo(kernel: Kernel, v: lc_variant, D, u, r, out=None, stream=None):
             raise ValueError("D, u, r and out must be contiguous CUDA tensors")
     check(load().lc_contract_geo(kernel.handle, ctypes.byref(v), D.data_ptr(), u.data_ptr(), r.data_ptr(),
                                  out.data_ptr(), E, N, F, _stream_ptr(stream)), "lc_contract_geo")
+    return out
+
+
+LIFT_DOMAIN = "{ [e,i,f,p]: 0<=e<E and 0<=i<N and 0<=f<Nf and 0<=p<Nfp }"
+LIFT_INSTRUCTION = "out[e,i] = sum((f,p), L[i,f,p]*s[e,f]*(u[e,fmask[f,p]] - u[vmapP[e,f,p]]))"
+
+
+def lift(kernel: Kernel, v: lc_variant, L, fmask, vmapP, s, u, out=None, accumulate=False, stream=None):
+    """Surface lift of the dG operator (lc_lift) on torch CUDA tensors: L (N, Nf*Nfp) float,
+    fmask (Nf*Nfp,) int32, vmapP (E, Nf*Nfp) int32, s (E, Nf) float, u (E, N) float; returns
+    out (E, N) (added to when accumulate)."""
+    import torch
+    E, N = u.shape
+    Nf = s.shape[1]
+    M = L.shape[1]
+    if out is None:
+        out = torch.zeros((E, N), dtype=torch.float32, device=u.device)
+    for t in (L, fmask, vmapP, s, u, out):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("every array must be a contiguous CUDA tensor")
+    check(load().lc_lift(kernel.handle, ctypes.byref(v), L.data_ptr(), fmask.data_ptr(), vmapP.data_ptr(),
+                         s.data_ptr(), u.data_ptr(), out.data_ptr(), E, N, Nf, M // Nf, 1 if accumulate else 0,
+                         _stream_ptr(stream)), "lc_lift")
     return out
 
 

@@ -52,7 +52,8 @@ def run(lc, kernel, v, D, u, r, layout):
 def test_integer_inputs_bit_exact(lc, layout, prec):
     kernel = lc.Kernel(lc.GEO_DOMAIN, lc.GEO_INSTRUCTION)
     ran = 0
-    for E, N, F in ((3000 + 77, 35, 3), (2000 + 5, 20, 2), (1500 + 1, 56, 3), (700, 4, 3), (1, 10, 2)):
+    for E, N, F in ((3000 + 77, 35, 3), (2000 + 5, 20, 2), (1500 + 1, 48, 3), (1200 + 3, 64, 2), (700, 4, 3),
+                    (1, 10, 2)):
         D, u = synth.integer_operands(E, N, F, seed=E + N)
         uu = synth.to_node_major(u) if layout == "node" else u
         r = factors(E, F, layout, seed=N, integer=True)
@@ -74,7 +75,7 @@ def test_integer_inputs_bit_exact(lc, layout, prec):
 @pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
 def test_random_inputs_within_bounds(lc, layout, prec):
     kernel = lc.Kernel(lc.GEO_DOMAIN, lc.GEO_INSTRUCTION)
-    for si, (E, N, F) in enumerate(((5000 + 3, 35, 3), (1000, 56, 3), (777, 84, 2))):
+    for si, (E, N, F) in enumerate(((5000 + 3, 35, 3), (1000, 48, 3), (777, 64, 2))):
         D, u = synth.operands(E, N, F, np.float32, seed=300 + si, scale_exp=2.0 if si else None)
         uu = synth.to_node_major(u) if layout == "node" else u
         r = factors(E, F, layout, seed=si)
