@@ -149,9 +149,9 @@ struct lc_variant {
                                  for other paths */
     int32_t a_operand;        /* tensor-core engine: where the converted u tile (the MMA's A
                                  operand) lives: 0 = the planner's choice, 1 = shared memory,
-                                 2 = tensor memory beside the accumulators (written by the
-                                 conversion warps with tcgen05.st; frees shared memory and its
-                                 bandwidth, needs the columns: one accumulator region) */
+                                 2 = (BF16) tensor memory beside the accumulators, written by
+                                 the conversion warps with tcgen05.st: frees shared memory and
+                                 its bandwidth */
 };
 
 /*

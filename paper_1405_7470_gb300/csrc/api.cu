@@ -1162,8 +1162,8 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         const int NT = v->precision == LC_PREC_BF16X3 ? 3 : 1;
         if (v->mma_order < 0 || v->mma_order > 2 || (v->mma_order != 0 && NT != 3))
             return LC_ERR_INVALID_VARIANT;
-        if (v->a_operand < 0 || v->a_operand > 2)
-            return LC_ERR_INVALID_VARIANT;
+        if (v->a_operand < 0 || v->a_operand > 2 || (v->a_operand == 2 && NT != 1))
+            return LC_ERR_INVALID_VARIANT;  // A terms in tensor memory: BF16 only
         TcArgs &t = r.tc;
         memset(&t, 0, sizeof t);
         t.N = N;
@@ -1255,7 +1255,7 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         for (int g = g_hi; g >= g_lo && !found; --g)
             for (int pass = 0; pass < 2 && !found; ++pass) {
                 const bool a_tm = tm_first ? pass == 0 : pass == 1;
-                if ((a_tm && v->a_operand == 1) || (!a_tm && v->a_operand == 2) || (a_tm && v->mma_order == 1))
+                if ((a_tm && v->a_operand == 1) || (!a_tm && v->a_operand == 2) || (a_tm && NT != 1))
                     continue;
                 for (int c = 0; c < ncombos && !found; ++c) {
                     TcArgs q = t;

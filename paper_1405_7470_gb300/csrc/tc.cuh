@@ -258,6 +258,10 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
     const uint32_t sbase = smem_addr(smem);
 
     const int N = a.N, G = a.G, CBp = a.CBp, KB = a.KB, nkb = a.nkb;
+    // The A terms in tensor memory are compiled into the BF16 instances only: with three
+    // terms the A reads from tensor memory measured slower beside the epilogue's loads, and
+    // the warp-collective stores would otherwise sit in the three-term conversion loop too.
+    constexpr bool kATmem = NT == 1;
     const int Np = a.Np;  // accumulator columns per operator (N rounded up to 16)
     // K columns the MMAs read: N rounded up to the 16 of one instruction.  A K-block
     // wider than that keeps its last columns unread, so nothing writes them.
@@ -401,7 +405,7 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
             const uint64_t bd = b0 + ((uint32_t)(brow * W + kb * bkb) >> 4);
             const uint32_t at_tm = a_tmb + (uint32_t)(at * (Kn / 2) + kb * KB / 2);
             for (int ki = 0; ki < steps; ++ki) {
-                if (a.a_tmem)
+                if (kATmem && a.a_tmem)
                     tc_mma_ta(dtm + dcol, at_tm + 8u * ki, bd + 2 * ki, id, accumulate);
                 else
                     tc_mma(dtm + dcol, ad + 2 * ki, bd + 2 * ki, id, accumulate);  // +32 bytes per K step
@@ -522,7 +526,7 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
             auto put = [&](int c8, const float *x) {
                 uint4 tt4[3];
                 split8<NT>(x, tt4);
-                if (a.a_tmem) {
+                if (kATmem && a.a_tmem) {
 #pragma unroll
                     for (int tt = 0; tt < NT; ++tt)
                         tmem_st4(abase + (uint32_t)(tt * (Kn / 2) + c8 * 4), tt4[tt]);
@@ -536,7 +540,7 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
             };
             // block kb written: make it visible to the tensor core and hand it to the MMA warp
             auto block_done = [&](int kb) {
-                if (a.a_tmem) {
+                if (kATmem && a.a_tmem) {
                     tmem_wait_st();
                     tc_fence_before();
                 } else {
@@ -568,6 +572,7 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
                         put(part + Hc * m, xv[m]);
                 block_done(0);
             } else {
+                const int full8 = rowv ? N / 8 : 0;  // chunks with all 8 values inside the row
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!mbar_wait(&a_empty[ab * kTcMaxKB + kb], (na & 1u) ^ 1u)) {
                         ok = false;
@@ -575,19 +580,45 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
                     }
                     tc_fence_after();
                     const int c8_lo = kb * KB / 8, c8_hi = min(Kn, (kb + 1) * KB) / 8;
-                    int c8 = c8_lo + part;
-                    // two chunks in flight (their loads before either conversion)
-                    for (; c8 + Hc < c8_hi; c8 += 2 * Hc) {
-                        float x[8], y[8];
-                        load_chunk(c8, x);
-                        load_chunk(c8 + Hc, y);
-                        put(c8, x);
-                        put(c8 + Hc, y);
-                    }
-                    for (; c8 < c8_hi; c8 += Hc) {
-                        float x[8];
-                        load_chunk(c8, x);
-                        put(c8, x);
+                    if (kATmem && a.a_tmem) {
+                        // tcgen05.st is warp-collective: every lane runs the same chunks (the
+                        // trip count depends on the warp's share only), rows past the tile are
+                        // zeros by predicated loads
+                        for (int c8 = c8_lo + part; c8 < c8_hi; c8 += Hc) {
+                            float x[8];
+                            load_chunk(c8, x);
+                            put(c8, x);
+                        }
+                    } else if (from_stage) {
+                        // staged tile: compile-time stride along j; two whole chunks in flight, then
+                        // the chunks cut by N or past the tile (zeros) one by one
+                        const int f_hi = min(full8, c8_hi);
+                        int c8 = c8_lo + part;
+                        for (; c8 + Hc < f_hi; c8 += 2 * Hc) {
+                            float x[8], y[8];
+                            const float *p0 = src_s + c8 * 8 * JS, *p1 = src_s + (c8 + Hc) * 8 * JS;
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) {
+                                x[q] = p0[q * JS];
+                                y[q] = p1[q * JS];
+                            }
+                            put(c8, x);
+                            put(c8 + Hc, y);
+                        }
+                        for (; c8 < c8_hi; c8 += Hc) {
+                            float x[8];
+                            const float *p0 = src_s + c8 * 8 * JS;
+#pragma unroll
+                            for (int q = 0; q < 8; ++q)
+                                x[q] = (rowv && c8 * 8 + q < N) ? p0[q * JS] : 0.f;
+                            put(c8, x);
+                        }
+                    } else {
+                        for (int c8 = c8_lo + part; c8 < c8_hi; c8 += Hc) {
+                            float x[8];
+                            load_chunk(c8, x);
+                            put(c8, x);
+                        }
                     }
                     block_done(kb);
                 }

@@ -7,21 +7,20 @@
 
 namespace lc {
 
+lc_status tc_geo_launch_node(const TcArgs &a, int nterms, int grid, cudaStream_t s);
+
 lc_status tc_geo_launch(const TcArgs &a, int layout, int nterms, int grid, cudaStream_t s)
 {
-    // kernel instance per (layout, terms, operators); 8-column epilogue chunks
-    static void *const fns[2][2][2] = {
-        {{reinterpret_cast<void *>(&tc_contract_kernel<LC_LAYOUT_ELEM_MAJOR, 1, 8, 2>),
-          reinterpret_cast<void *>(&tc_contract_kernel<LC_LAYOUT_ELEM_MAJOR, 1, 8, 3>)},
-         {reinterpret_cast<void *>(&tc_contract_kernel<LC_LAYOUT_ELEM_MAJOR, 3, 8, 2>),
-          reinterpret_cast<void *>(&tc_contract_kernel<LC_LAYOUT_ELEM_MAJOR, 3, 8, 3>)}},
-        {{reinterpret_cast<void *>(&tc_contract_kernel<LC_LAYOUT_NODE_MAJOR, 1, 8, 2>),
-          reinterpret_cast<void *>(&tc_contract_kernel<LC_LAYOUT_NODE_MAJOR, 1, 8, 3>)},
-         {reinterpret_cast<void *>(&tc_contract_kernel<LC_LAYOUT_NODE_MAJOR, 3, 8, 2>),
-          reinterpret_cast<void *>(&tc_contract_kernel<LC_LAYOUT_NODE_MAJOR, 3, 8, 3>)}}};
     if (a.F < 2 || a.F > 3 || a.chunk != 8)
         return LC_ERR_INVALID_VARIANT;
-    return tc_launch_fn(fns[layout == LC_LAYOUT_NODE_MAJOR][nterms == 3][a.F == 3], a, grid, s);
+    if (layout == LC_LAYOUT_NODE_MAJOR)
+        return tc_geo_launch_node(a, nterms, grid, s);  // node-major instances (tc_geo_node.cu)
+    // element-major instance per (terms, operators); 8-column epilogue chunks
+    static void *const fns[2][2] = {{reinterpret_cast<void *>(&tc_contract_kernel<LC_LAYOUT_ELEM_MAJOR, 1, 8, 2>),
+                                     reinterpret_cast<void *>(&tc_contract_kernel<LC_LAYOUT_ELEM_MAJOR, 1, 8, 3>)},
+                                    {reinterpret_cast<void *>(&tc_contract_kernel<LC_LAYOUT_ELEM_MAJOR, 3, 8, 2>),
+                                     reinterpret_cast<void *>(&tc_contract_kernel<LC_LAYOUT_ELEM_MAJOR, 3, 8, 3>)}};
+    return tc_launch_fn(fns[nterms == 3][a.F == 3], a, grid, s);
 }
 
 }  // namespace lc

@@ -164,14 +164,16 @@ def test_variant_plan_reports_the_resolved_launch(lib):
     assert p["cols_per_op"] == 40 and p["mma_n"] == 128 and p["stacked"] == 1 and p["mma_per_tile"] == 15
     assert p["threads"] == 128 * (4 + 2) + 64 and p["store_rows"] == 128
     assert 0 < p["smem_bytes"] <= 232448 and p["a_in_tmem"] == 0 and p["tmem_cols"] == 512
-    # the A terms in tensor memory: one accumulator region (hi*hi last, 6 MMAs per K step), two
-    # accumulators of 128 columns and two A buffers of 3 x 24 columns; no A in shared memory
-    v.mma_order, v.a_operand, v.stages = 0, 2, 2
-    q = lc.variant_plan(k, 1 << 21, 35, 3, v)
-    assert q["a_in_tmem"] == 1 and q["stacked"] == 0 and q["mma_per_tile"] == 18 and q["a_buffers"] == 2
+    # BF16 with the A terms in tensor memory: two accumulators of 128 columns and two A
+    # buffers of 24 columns; no A in shared memory
+    w = lc.Variant(engine="tcgen05", layout="elem", precision="bf16", tile_e=128, elems_per_thread=64, split_i=0,
+                   unroll=4, prefetch_smem=1, stages=2, store_rows=128, a_operand=2)
+    q = lc.variant_plan(k, 1 << 21, 35, 3, w)
+    assert q["a_in_tmem"] == 1 and q["stacked"] == 0 and q["mma_per_tile"] == 3 and q["a_buffers"] == 2
     assert q["cols_per_op"] == 40 and q["mma_n"] == 128 and q["tmem_cols"] == 512
-    assert q["smem_bytes"] < p["smem_bytes"]
-    v.mma_order = 1  # the stacked order cannot keep A in tensor memory
+    w.a_operand = 1
+    assert lc.variant_plan(k, 1 << 21, 35, 3, w)["a_in_tmem"] == 0
+    v.a_operand = 2  # the three-term path keeps A in shared memory
     assert lib.lc_variant_validate(k.handle, 1 << 21, 35, 3, ctypes.byref(v)) == 3
     v.mma_order, v.a_operand, v.stages = 1, 0, 1
     s = lc.variant_plan(k, 1 << 21, 35, 3, lc.variant_default(k, 1 << 21, 35, 3, "elem", "fp32"))
