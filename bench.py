@@ -70,6 +70,7 @@ PER_CONFIG = [
     ("precision/bf16", ["--workload", "precision", "--precision", "bf16"]),
     ("precision/bf16x3", ["--workload", "precision", "--precision", "bf16x3"]),
     ("grouped", ["--workload", "grouped"]),
+    ("grouped/fp32", ["--workload", "grouped", "--precision", "fp32"]),
     ("geo/bf16x3", ["--workload", "geo"]),
     ("saxpy", ["--workload", "saxpy"]),
     ("lift", ["--workload", "lift"]),
@@ -81,6 +82,14 @@ L2_BYTES = 129 * 1000 * 1000  # GB300 L2
 # prefetch_smem, stages, ctas_per_sm)
 GROUPED_CANDIDATES = [(8, 8, 4, 1, 2, 3), (4, 8, 4, 1, 2, 3), (4, 8, 4, 1, 1, 3), (8, 4, 4, 1, 2, 2),
                       (4, 8, 4, 1, 2, 2), (8, 8, 4, 1, 2, 1), (8, 8, 1, 1, 1, 1)]
+# tensor-core descriptors tried for the grouped launch (BF16 / BF16X3): (K-block width,
+# epilogue threads per row, stages, store rows); the groups without a tensor-core plan run
+# in the library's FP32 SIMT grouped launch after it
+GROUPED_TC_CANDIDATES = [(64, 4, 1, 128), (1, 4, 1, 128), (64, 3, 1, 128), (64, 4, 2, 32), (64, 2, 2, 128),
+                         (1, 3, 2, 32)]
+# the library's SIMT descriptor for those groups (elems_per_thread, split_i, unroll,
+# prefetch_smem, stages, ctas_per_sm)
+GROUPED_SIMT_FALLBACK = (8, 8, 4, 1, 2, 3)
 
 # sources that decide a tensor-core launch: the kernel, its helpers, the planner
 TC_SOURCES = ("tc.cu", "tma.cuh", "lc_internal.h", "api.cu")
@@ -337,7 +346,7 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     wl = dict(WORKLOADS[args.workload])
     wl["storage"] = "fp64" if wl["precision"] == "fp64" else "fp32"
-    if not args.precision and wl["storage"] == "fp32" and args.workload not in ("grouped", "saxpy", "geo", "lift"):
+    if not args.precision and wl["storage"] == "fp32" and args.workload not in ("saxpy", "geo", "lift"):
         args.precision = "bf16x3"
     if args.precision:
         if (args.precision == "fp64") != (wl["storage"] == "fp64"):
@@ -352,8 +361,8 @@ def main():
             return
         return run_reference(args, wl)
     if args.workload == "grouped":
-        if args.precision not in ("", "fp32", "bf16x3"):
-            ap.error("the grouped launch runs the FP32 SIMT engine")
+        if args.precision not in ("fp32", "bf16", "bf16x3"):
+            ap.error("the grouped launch runs BF16 / BF16X3 tensor-core or FP32 SIMT arithmetic")
         return run_grouped(args, wl, world, rank, local_rank)
     if args.workload == "geo":
         return run_geo(args, wl, world, rank, local_rank)
@@ -611,11 +620,24 @@ def run_grouped(args, wl, world, rank, local_rank):
         stream.synchronize()
         return a.elapsed_time(b) / reps
 
-    # descriptor: the fastest of a few SIMT tile shapes, each planned and captured once
+    prec = wl["precision"]
+    tensor = prec in ("bf16", "bf16x3")
+
+    def simt_variant(c):
+        re_, rc, unr, pf, st, cps = c
+        return lc.Variant(layout=args.layout, elems_per_thread=re_, split_i=rc, unroll=unr, prefetch_smem=pf,
+                          stages=st, ctas_per_sm=cps)
+
+    def tc_variant(c):
+        kbw, tpr, st, rows = c
+        return lc.Variant(engine="tcgen05", layout=args.layout, precision=prec, tile_e=128, elems_per_thread=kbw,
+                          split_i=0, unroll=tpr, prefetch_smem=1, stages=st, store_rows=0 if node else rows)
+
+    # descriptor: the fastest of a few tile shapes, each planned and captured once
+    cands = [tc_variant(c) for c in GROUPED_TC_CANDIDATES] if tensor else \
+        [simt_variant(c) for c in GROUPED_CANDIDATES]
     best = None
-    for re_, rc, unr, pf, st, cps in GROUPED_CANDIDATES:
-        v = lc.Variant(layout=args.layout, elems_per_thread=re_, split_i=rc, unroll=unr, prefetch_smem=pf,
-                       stages=st, ctas_per_sm=cps)
+    for v in cands:
         try:
             plan = lc.GroupedPlan(kernel, v, groups, use_graph=True, stream=stream)
         except lc.LcError:
@@ -629,6 +651,25 @@ def run_grouped(args, wl, world, rank, local_rank):
         raise RuntimeError("no grouped plan fits")
     _, v, plan = best
     vd = lc.variant_dict(v)
+    # the two launches of a tensor-core plan timed apart (a plan over each part's groups)
+    parts = None
+    if tensor:
+        on_tc = [plan.group_variant(k).engine == lc.ENGINE["tcgen05"] for k in range(len(sizes))]
+        parts = {}
+        for name, sel, pv in (("tcgen05", on_tc, v), ("simt", [not x for x in on_tc],
+                                                          simt_variant(GROUPED_SIMT_FALLBACK))):
+            # (a plan over the part's groups alone makes the same per-group choices)
+            sub = [g for g, k in zip(groups, sel) if k]
+            if not sub:
+                continue
+            pp = lc.GroupedPlan(kernel, pv, sub, use_graph=True, stream=stream)
+            ms = timed(lambda: pp.run(stream), 10)
+            psz = [sz for sz, k in zip(sizes, sel) if k]
+            pfl = sum(2.0 * E * N * N * F for N, E in psz)
+            pby = sum(4.0 * (E * N * (1 + F) + F * N * N) for N, E in psz)
+            parts[name] = {"groups": [N for N, _ in psz], "ms": ms, "flops": pfl, "bytes": pby,
+                           "hbm_frac": pby / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+            del pp
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -658,7 +699,7 @@ def run_grouped(args, wl, world, rank, local_rank):
     launch_s = statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends)) * 1e-3
 
     # the same groups as one launch per group, each with its default descriptor
-    vs = [lc.variant_default(kernel, E, N, F, args.layout, "fp32") for N, E in sizes]
+    vs = [lc.variant_default(kernel, E, N, F, args.layout, prec) for N, E in sizes]
 
     def per_group():
         for vg, (D, u, out) in zip(vs, groups):
@@ -716,7 +757,22 @@ def run_grouped(args, wl, world, rank, local_rank):
     if rank == 0:
         alu_peak = sms * 128 * 2 * peaks["sm_max_mhz"] * 1e6
         t_alu, t_hbm = flops / alu_peak, nbytes / (peaks["hbm_gbs"] * 1e9)
-        if t_alu > t_hbm:
+        if parts:
+            # the roofline of the launch that takes longer: the tensor-core one is HBM-bound,
+            # the SIMT one (N = 165 in FP32) ALU-bound
+            top = max(parts, key=lambda k: parts[k]["ms"])
+            pt = parts[top]
+            if top == "tcgen05":
+                ach = pt["bytes"] / (pt["ms"] * 1e-3) / 1e9
+                roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": peaks["source"],
+                        "kernel": "tc_grouped_kernel"}
+            else:
+                ach = pt["flops"] / (pt["ms"] * 1e-3) / 1e12
+                roof = {"bound": "alu", "achieved": ach, "peak": alu_peak / 1e12, "unit": "TFLOP/s",
+                        "frac": ach / (alu_peak / 1e12), "traffic": None, "kernel": "grouped_kernel",
+                        "peak_source": f"derived: {sms} SMs x 128 FMA lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz"}
+        elif t_alu > t_hbm:
             ach = flops / launch_s / 1e12
             roof = {"bound": "alu", "achieved": ach, "peak": alu_peak / 1e12, "unit": "TFLOP/s",
                     "frac": ach / (alu_peak / 1e12), "traffic": None,
@@ -729,12 +785,15 @@ def run_grouped(args, wl, world, rank, local_rank):
         line = {
             "metric": "contraction GFLOP/s", "value": flops * world / (ms_per_step * 1e-3) / 1e9, "unit": "GFLOP/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if not tensor else
+            f"{prec} on the tensor cores (f32 accumulate); f32 for groups without a tensor-core plan",
             "data": "synthetic",
             "config": {"workload": wl["desc"], "groups": [{"N": N, "E": E} for N, E in sizes],
                        "E_total": int(sum(E for _, E in sizes)), "F": F, "layout": args.layout,
-                       "precision": "fp32", "variant": vd,
-                       "variant_choice": f"fastest of {len(GROUPED_CANDIDATES)} grouped tile shapes",
+                       "precision": prec, "variant": vd,
+                       "variant_choice": f"fastest of {len(cands)} grouped tile shapes",
+                       "parts": parts,
                        "parallelism": f"replicas x{world}",
                        "l2": "inputs+outputs larger than L2 (no flush needed)", "bytes_per_step": nbytes,
                        "per_group_launches_ms": per_group_ms, "grouped_plan": plan.info()},
@@ -787,6 +846,8 @@ def run_geo(args, wl, world, rank, local_rank):
     Dd, ud, rd = (torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in (D, u_in, r_in))
     out = torch.empty((F, N, E) if node else (F, E, N), device="cuda")
     cands = [v for v in lc.enumerate_variants(kernel, E, N, F, args.layout, wl["precision"])]
+    if args.variant == "default":
+        cands = [lc.variant_default(kernel, E, N, F, args.layout, wl["precision"])]
     best = None
     with torch.cuda.stream(stream):
         for v in cands:
@@ -877,21 +938,21 @@ def run_saxpy(args, wl, world, rank, local_rank):
     a = 0.7071
     stream = torch.cuda.Stream()
     best = None
-    for unroll in (1, 2, 4, 8):
-        for ctas in (2, 4, 8):
-            v = lc.variant_default(kernel, n, 1, 1, "elem", "fp32")
-            v.unroll, v.ctas_per_sm = unroll, ctas
-            with torch.cuda.stream(stream):
+    shapes = [(4, 4)] if args.variant == "default" else [(u_, c_) for u_ in (1, 2, 4, 8) for c_ in (2, 4, 8)]
+    for unroll, ctas in shapes:
+        v = lc.variant_default(kernel, n, 1, 1, "elem", "fp32")
+        v.unroll, v.ctas_per_sm = unroll, ctas
+        with torch.cuda.stream(stream):
+            lc.elementwise(kernel, v, [z, x, y], [a], stream=stream)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for _ in range(3):
                 lc.elementwise(kernel, v, [z, x, y], [a], stream=stream)
-                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                ev0.record(stream)
-                for _ in range(3):
-                    lc.elementwise(kernel, v, [z, x, y], [a], stream=stream)
-                ev1.record(stream)
-            ev1.synchronize()
-            t = ev0.elapsed_time(ev1) / 3
-            if best is None or t < best[0]:
-                best = (t, v)
+            ev1.record(stream)
+        ev1.synchronize()
+        t = ev0.elapsed_time(ev1) / 3
+        if best is None or t < best[0]:
+            best = (t, v)
     v = best[1]
     nbytes = 12.0 * n
 
@@ -961,7 +1022,7 @@ def run_lift(args, wl, world, rank, local_rank):
     out = torch.zeros((E, N), device="cuda")
     stream = torch.cuda.Stream()
     best = None
-    for ctas in (1, 2, 3, 4, 6, 8):
+    for ctas in ((4,) if args.variant == "default" else (1, 2, 3, 4, 6, 8)):
         v = lc.variant_default(k, E, N, 1, "elem", "fp32")
         v.ctas_per_sm = ctas
         with torch.cuda.stream(stream):

@@ -388,10 +388,22 @@ lc_status lc_grouped_workspace_size(const lc_kernel *k, const lc_variant *v, con
                                     int32_t ngroups, size_t *bytes);
 
 /*
- * Plan one persistent launch over all groups: every group gets a SIMT tile shape with
- * the same CTA size; all (group, tile) work is cut into one contiguous range per CTA,
- * balanced by estimated cost.  The variant (FP32 SIMT engine) gives the register block
- * (elems_per_thread, split_i), unroll (1 or 4), prefetch_smem, stages and ctas_per_sm.
+ * Plan one persistent launch over all groups.
+ * FP32 SIMT variant: every group gets a SIMT tile shape with the same CTA size; all
+ * (group, tile) work is cut into one contiguous range per CTA, balanced by estimated
+ * cost.  The variant gives the register block (elems_per_thread, split_i), unroll (1 or
+ * 4), prefetch_smem, stages and ctas_per_sm.
+ * Tensor-core variant (TCGEN05, BF16 or BF16X3, at most 16 groups): each group that has
+ * a tensor-core plan (lc_variant_validate's rules; the epilogue works in 8-column chunks)
+ * for the variant, or else for the first of its changes "stages = 1", "the other K-block
+ * width (elems_per_thread 1 <-> 64)", "store_rows = 32" (element-major) and their
+ * combinations, with the same CTA size (unroll), runs in one tensor-core launch, one CTA per SM at most: every (group,
+ * column block) unit gets at least one CTA, and the rest go to the unit whose estimated
+ * time (tiles x per-tile cost / CTAs) is the largest.  More units than SMs is
+ * LC_ERR_INVALID_VARIANT.  Groups without a tensor-core plan (e.g. N above the plans'
+ * limit) run after it in a FP32 SIMT grouped launch (8 x 8 register blocks, unroll 4, two
+ * stages, three CTAs per SM);
+ * their results are FP32's, below both reduced-precision bounds.
  *   workspace_dev  caller-owned device memory holding the group and work tables
  *                  (lc_grouped_workspace_size bytes, 16-byte aligned); it must outlive
  *                  the plan, as must the groups' buffers, which the plan references.
@@ -409,8 +421,17 @@ lc_status lc_grouped_plan_create(const lc_kernel *k, const lc_variant *v, const 
 /* Enqueue the planned launch (graph replay when captured) on `stream`. */
 lc_status lc_grouped_run(lc_grouped_plan *plan, void *stream);
 
-/* Grid size and number of (group, tile-range) segments of a plan. */
+/* Grid size (both launches) and number of (group, tile-range) segments of a plan (a
+ * tensor-core CTA counts as one segment). */
 lc_status lc_grouped_plan_info(const lc_grouped_plan *plan, int32_t *grid, int32_t *segments);
+
+/*
+ * The descriptor that serves group `group` (0-based, < ngroups) of a plan: the variant as
+ * given (SIMT plans; tensor-core groups that have a plan for it), the tensor-core variant
+ * the planner fell back to for that group, or the FP32 SIMT descriptor of the groups
+ * without a tensor-core plan.  Errors: LC_ERR_INVALID_ARGUMENT.
+ */
+lc_status lc_grouped_plan_group(const lc_grouped_plan *plan, int32_t group, lc_variant *v);
 
 void lc_grouped_plan_destroy(lc_grouped_plan *plan);
 

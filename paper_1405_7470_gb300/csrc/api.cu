@@ -2101,13 +2101,20 @@ lc_status lc_contract_host(const lc_kernel *kh, const lc_variant *v, const void 
 // ------------------------------------------------------------------ grouped launch
 
 struct lc_grouped_plan {
+    // SIMT part (every group of a SIMT plan; the groups without a tensor plan of a tensor plan)
     void *fn = nullptr;
     GroupedArgs args{};
     int grid = 0, threads = 0;
     size_t smem = 0;
+    // tensor-core part
+    void *fn_tc = nullptr;
+    lc::TcGroupedParams tcp{};
+    int grid_tc = 0, threads_tc = 0;
+    size_t smem_tc = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int ngroups = 0, nsegs = 0;
+    std::vector<lc_variant> group_variant;  // the descriptor serving each group
 };
 
 namespace lc {
@@ -2324,6 +2331,194 @@ static lc_status grouped_plan_host(const Kernel &K, const lc_variant *v, const l
     return LC_OK;
 }
 
+// Tensor-core part of a grouped plan: the groups with a tensor-core plan for the variant
+// (their indices in `tc_groups`, the rest in `simt_groups`), one (group, column block) unit per
+// CTA set, CTAs handed out so that the slowest unit's estimated time is the least, at most one
+// CTA per SM.
+struct GroupedPlanTc {
+    TcGroupedParams P{};
+    std::vector<lc_variant> gv;  // per group: the tensor-core variant serving it
+    std::vector<int4> map;
+    int grid = 0, threads = 0, nterms = 1;
+    size_t smem = 0;
+    std::vector<int> tc_groups, simt_groups;
+};
+
+static lc_status grouped_plan_tc(const Kernel &K, const lc_variant *v, const lc_group *groups, int ng,
+                                 GroupedPlanTc &T)
+{
+    if (ng > kTcMaxGroups)
+        return LC_ERR_INVALID_ARGUMENT;
+    for (int gi = 0; gi < ng; ++gi) {
+        const lc_group &G = groups[gi];
+        if (!G.D_dev || (G.E > 0 && (!G.u_dev || !G.out_dev)))
+            return LC_ERR_INVALID_ARGUMENT;
+        if (!aligned16(G.D_dev) || !aligned16(G.u_dev) || !aligned16(G.out_dev))
+            return LC_ERR_MISALIGNED;
+    }
+    const int sms = sm_count();
+    if (sms <= 0)
+        return LC_ERR_NO_DEVICE;
+    T.nterms = v->precision == LC_PREC_BF16X3 ? 3 : 1;
+    T.gv.assign(ng, *v);
+    struct Unit {
+        int g, blk;
+        long long tiles;
+        double cost;  // estimated seconds per tile
+    };
+    std::vector<Unit> units;
+    for (int gi = 0; gi < ng; ++gi) {
+        const lc_group &G = groups[gi];
+        // the variant as given, else the first of: one stage, the other K-block width
+        // (1 <-> 64), 32-row stores (element-major), that has a plan; the CTA size stays
+        Resolved r;
+        lc_status rs = LC_ERR_INVALID_VARIANT;
+        lc_variant vg = *v;
+        const bool node = v->layout == LC_LAYOUT_NODE_MAJOR;
+        for (int q = 0; q < 8 && G.E > 0 && rs != LC_OK; ++q) {
+            vg = *v;
+            if (q & 1)
+                vg.stages = 1;
+            if (q & 2)
+                vg.elems_per_thread = v->elems_per_thread == 64 ? 1 : 64;
+            if (q & 4) {
+                if (node)
+                    continue;
+                vg.store_rows = 32;
+            }
+            if (q > 0 && memcmp(&vg, v, sizeof vg) == 0)
+                continue;
+            rs = resolve(K, G.E, G.N, G.F, &vg, r, true);
+            if (rs == LC_ERR_NO_DEVICE || rs == LC_ERR_CUDA || rs == LC_ERR_INVALID_ARGUMENT ||
+                rs == LC_ERR_ASSUMPTION)
+                return rs;
+        }
+        if (rs != LC_OK) {
+            T.simt_groups.push_back(gi);  // no tensor-core plan (or nothing to do)
+            continue;
+        }
+        T.gv[gi] = vg;
+        TcArgs t = r.tc;
+        t.D = static_cast<const float *>(G.D_dev);
+        t.u = static_cast<const float *>(G.u_dev);
+        t.out = static_cast<float *>(G.out_dev);
+        t.r = nullptr;
+        t.err = error_word();
+        t.chunk = 8;  // one kernel instance for all groups: 8-column epilogue chunks
+        const int tg = (int)T.tc_groups.size();
+        T.P.g[tg] = t;
+        T.tc_groups.push_back(gi);
+        T.smem = std::max(T.smem, (size_t)t.smem_bytes);
+        T.threads = 128 * (t.threads_per_row + t.conv_threads_per_row) + 64;
+        // per tile: its HBM bytes at the SM's share of the copy rate (0.6 efficiency), or the
+        // MMA chain at about 300 cycles an instruction, plus a fixed pipeline cost
+        const int kn = (G.N + 15) / 16 * 16;
+        const int mmas = (T.nterms == 1 ? 1 : (t.stack ? 5 : 6)) * (kn / 16);
+        for (int b = 0; b < t.nblocks; ++b) {
+            const int gb = std::min(t.G, G.F - b * t.G);
+            const double bytes = 128.0 * G.N * 4.0 * (1 + gb);
+            const double cost = std::max(bytes / (6.7e12 / sms) / 0.6, mmas * 300.0 / 1.9e9) + 4e-7;
+            units.push_back({tg, b, t.ntiles, cost});
+        }
+    }
+    T.P.ngroups = (int)T.tc_groups.size();
+    if (units.empty())
+        return LC_OK;
+    if ((int)units.size() > sms)
+        return LC_ERR_INVALID_VARIANT;  // more units than SMs: one CTA per unit does not fit
+    std::vector<int> n(units.size(), 1);
+    int used = (int)units.size();
+    while (used < sms) {
+        size_t m = units.size();
+        double worst = -1;
+        for (size_t q = 0; q < units.size(); ++q) {
+            if (n[q] >= units[q].tiles)
+                continue;
+            const double load = units[q].tiles * units[q].cost / n[q];
+            if (load > worst) {
+                worst = load;
+                m = q;
+            }
+        }
+        if (m == units.size())
+            break;
+        ++n[m];
+        ++used;
+    }
+    for (size_t q = 0; q < units.size(); ++q)
+        for (int r = 0; r < n[q]; ++r)
+            T.map.push_back(make_int4(units[q].g, units[q].blk, r, n[q]));
+    T.grid = (int)T.map.size();
+    return LC_OK;
+}
+
+// The SIMT descriptor that serves the groups of a tensor-core grouped plan without a tensor
+// plan (8 x 8 register blocks, unroll 4, two stages, three CTAs per SM: the fastest grouped
+// SIMT shape measured on the uneven-batching workload).
+static lc_variant grouped_simt_fallback(const lc_variant *v)
+{
+    lc_variant s;
+    memset(&s, 0, sizeof s);
+    s.struct_size = sizeof(lc_variant);
+    s.engine = LC_ENGINE_SIMT;
+    s.layout = v->layout;
+    s.precision = LC_PREC_FP32;
+    s.elems_per_thread = 8;
+    s.split_i = 8;
+    s.tile_e = 64;
+    s.unroll = 4;
+    s.prefetch_smem = 1;
+    s.stages = 2;
+    s.ctas_per_sm = 3;
+    return s;
+}
+
+// Both parts of a grouped plan and the workspace layout: SIMT tables first, then the tensor
+// part's unit table (16-byte aligned).
+struct GroupedPlanAll {
+    GroupedPlanHost S;
+    GroupedPlanTc T;
+    std::vector<lc_group> simt_groups;
+    lc_variant simt_v;
+    bool has_simt = false;
+    size_t off_map = 0, bytes = 0;
+};
+
+static lc_status grouped_plan_all(const Kernel &K, const lc_variant *v, const lc_group *groups, int ng,
+                                  GroupedPlanAll &A)
+{
+    if (!v || v->struct_size != sizeof(lc_variant) || !groups || ng <= 0)
+        return LC_ERR_INVALID_ARGUMENT;
+    if (v->engine != LC_ENGINE_TCGEN05) {
+        lc_status st = grouped_plan_host(K, v, groups, ng, A.S);
+        if (st != LC_OK)
+            return st;
+        A.has_simt = true;
+        A.bytes = A.S.bytes;
+        return LC_OK;
+    }
+    if (v->precision != LC_PREC_BF16 && v->precision != LC_PREC_BF16X3)
+        return LC_ERR_INVALID_VARIANT;
+    lc_status st = grouped_plan_tc(K, v, groups, ng, A.T);
+    if (st != LC_OK)
+        return st;
+    for (int gi : A.T.simt_groups)
+        if (groups[gi].E > 0)
+            A.simt_groups.push_back(groups[gi]);
+    if (!A.simt_groups.empty()) {
+        A.simt_v = grouped_simt_fallback(v);
+        st = grouped_plan_host(K, &A.simt_v, A.simt_groups.data(), (int)A.simt_groups.size(), A.S);
+        if (st != LC_OK)
+            return st;
+        A.has_simt = true;
+    }
+    A.off_map = A.has_simt ? (A.S.bytes + 15) / 16 * 16 : 0;
+    A.bytes = A.off_map + sizeof(int4) * A.T.map.size();
+    if (A.bytes == 0)
+        A.bytes = 16;
+    return LC_OK;
+}
+
 }  // namespace lc
 
 lc_status lc_device_error(int clear)
@@ -2349,11 +2544,11 @@ lc_status lc_grouped_workspace_size(const lc_kernel *kh, const lc_variant *v, co
 {
     if (!kh || !bytes)
         return LC_ERR_INVALID_ARGUMENT;
-    GroupedPlanHost P;
-    lc_status st = grouped_plan_host(kh->k, v, groups, ngroups, P);
+    GroupedPlanAll A;
+    lc_status st = grouped_plan_all(kh->k, v, groups, ngroups, A);
     if (st != LC_OK)
         return st;
-    *bytes = P.bytes;
+    *bytes = A.bytes;
     return LC_OK;
 }
 
@@ -2370,46 +2565,85 @@ lc_status lc_grouped_plan_create(const lc_kernel *kh, const lc_variant *v, const
     int major = 0, minor = 0;
     if (current_cc(&major, &minor) != 0 || major != 10 || minor != 3)
         return LC_ERR_NO_DEVICE;
-    GroupedPlanHost P;
-    lc_status st = grouped_plan_host(kh->k, v, groups, ngroups, P);
+    GroupedPlanAll A;
+    lc_status st = grouped_plan_all(kh->k, v, groups, ngroups, A);
     if (st != LC_OK)
         return st;
-    if (workspace_bytes < P.bytes)
+    if (workspace_bytes < A.bytes)
         return LC_ERR_BUFFER_TOO_SMALL;
-    void *fn = grouped_kernel_ptr(v->layout, v->elems_per_thread, v->split_i, v->unroll, v->prefetch_smem);
-    if (!fn)
-        return LC_ERR_INVALID_VARIANT;
+    const GroupedPlanHost &P = A.S;
+    const lc_variant *sv = v->engine == LC_ENGINE_TCGEN05 ? &A.simt_v : v;
+    void *fn = nullptr;
+    if (A.has_simt) {
+        fn = grouped_kernel_ptr(sv->layout, sv->elems_per_thread, sv->split_i, sv->unroll, sv->prefetch_smem);
+        if (!fn)
+            return LC_ERR_INVALID_VARIANT;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     unsigned char *ws = static_cast<unsigned char *>(workspace);
-    std::vector<unsigned char> host(P.bytes, 0);
-    memcpy(host.data() + P.off_groups, P.groups.data(), sizeof(SimtArgs) * P.groups.size());
-    memcpy(host.data() + P.off_segs, P.segs.data(), sizeof(GroupSeg) * P.segs.size());
-    memcpy(host.data() + P.off_cta, P.cta_seg.data(), sizeof(int) * P.cta_seg.size());
-    cudaError_t e = cudaMemcpyAsync(ws, host.data(), P.bytes, cudaMemcpyHostToDevice, s);
+    std::vector<unsigned char> host(A.bytes, 0);
+    if (A.has_simt) {
+        memcpy(host.data() + P.off_groups, P.groups.data(), sizeof(SimtArgs) * P.groups.size());
+        memcpy(host.data() + P.off_segs, P.segs.data(), sizeof(GroupSeg) * P.segs.size());
+        memcpy(host.data() + P.off_cta, P.cta_seg.data(), sizeof(int) * P.cta_seg.size());
+    }
+    if (!A.T.map.empty())
+        memcpy(host.data() + A.off_map, A.T.map.data(), sizeof(int4) * A.T.map.size());
+    cudaError_t e = cudaMemcpyAsync(ws, host.data(), A.bytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && fn)
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
     if (e != cudaSuccess)
         return cuda_fail(e);
     lc_grouped_plan *plan = new (std::nothrow) lc_grouped_plan;
     if (!plan)
         return LC_ERR_INVALID_ARGUMENT;
-    plan->fn = fn;
-    plan->args.groups = reinterpret_cast<const SimtArgs *>(ws + P.off_groups);
-    plan->args.segs = reinterpret_cast<const GroupSeg *>(ws + P.off_segs);
-    plan->args.cta_seg = reinterpret_cast<const int *>(ws + P.off_cta);
-    plan->args.err = error_word();
-    plan->grid = P.grid;
-    plan->threads = P.threads;
-    plan->smem = P.smem;
+    if (A.has_simt) {
+        plan->fn = fn;
+        plan->args.groups = reinterpret_cast<const SimtArgs *>(ws + P.off_groups);
+        plan->args.segs = reinterpret_cast<const GroupSeg *>(ws + P.off_segs);
+        plan->args.cta_seg = reinterpret_cast<const int *>(ws + P.off_cta);
+        plan->args.err = error_word();
+        plan->grid = P.grid;
+        plan->threads = P.threads;
+        plan->smem = P.smem;
+        plan->nsegs = (int)P.segs.size();
+    }
+    if (A.T.grid > 0) {
+        plan->tcp = A.T.P;
+        plan->tcp.map = reinterpret_cast<const int4 *>(ws + A.off_map);
+        plan->grid_tc = A.T.grid;
+        plan->threads_tc = A.T.threads;
+        plan->smem_tc = A.T.smem;
+        plan->nsegs += A.T.grid;
+        st = tc_grouped_launch(plan->tcp, v->layout, A.T.nterms, 0, 0, plan->smem_tc, s, &plan->fn_tc);
+        if (st != LC_OK) {
+            delete plan;
+            return st;
+        }
+    }
     plan->ngroups = ngroups;
-    plan->nsegs = (int)P.segs.size();
+    plan->group_variant.assign(ngroups, *v);
+    if (v->engine == LC_ENGINE_TCGEN05) {
+        for (int gi = 0; gi < ngroups; ++gi)
+            plan->group_variant[gi] = A.T.gv[gi];
+        for (int gi : A.T.simt_groups)
+            plan->group_variant[gi] = A.simt_v;
+    }
     if (use_graph) {
-        void *params[] = {&plan->args};
         e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t le = cudaLaunchKernel(fn, dim3(plan->grid), dim3(plan->threads), params, plan->smem, s);
+            cudaError_t le = cudaSuccess;
+            if (plan->fn_tc) {
+                void *params[] = {&plan->tcp};
+                le = cudaLaunchKernel(plan->fn_tc, dim3(plan->grid_tc), dim3(plan->threads_tc), params,
+                                      plan->smem_tc, s);
+            }
+            if (le == cudaSuccess && plan->fn) {
+                void *params[] = {&plan->args};
+                le = cudaLaunchKernel(plan->fn, dim3(plan->grid), dim3(plan->threads), params, plan->smem, s);
+            }
             e = cudaStreamEndCapture(s, &plan->graph);
             if (le != cudaSuccess)
                 e = le;
@@ -2432,12 +2666,19 @@ lc_status lc_grouped_run(lc_grouped_plan *plan, void *stream)
     if (!plan)
         return LC_ERR_INVALID_ARGUMENT;
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e;
+    cudaError_t e = cudaSuccess;
     if (plan->exec) {
         e = cudaGraphLaunch(plan->exec, s);
     } else {
-        void *params[] = {&plan->args};
-        e = cudaLaunchKernel(plan->fn, dim3(plan->grid), dim3(plan->threads), params, plan->smem, s);
+        if (plan->fn_tc) {
+            void *params[] = {&plan->tcp};
+            e = cudaLaunchKernel(plan->fn_tc, dim3(plan->grid_tc), dim3(plan->threads_tc), params, plan->smem_tc,
+                                 s);
+        }
+        if (e == cudaSuccess && plan->fn) {
+            void *params[] = {&plan->args};
+            e = cudaLaunchKernel(plan->fn, dim3(plan->grid), dim3(plan->threads), params, plan->smem, s);
+        }
     }
     if (e != cudaSuccess)
         return cuda_fail(e);
@@ -2448,8 +2689,16 @@ lc_status lc_grouped_plan_info(const lc_grouped_plan *plan, int32_t *grid, int32
 {
     if (!plan || !grid || !segments)
         return LC_ERR_INVALID_ARGUMENT;
-    *grid = plan->grid;
+    *grid = plan->grid + plan->grid_tc;
     *segments = plan->nsegs;
+    return LC_OK;
+}
+
+lc_status lc_grouped_plan_group(const lc_grouped_plan *plan, int32_t group, lc_variant *v)
+{
+    if (!plan || !v || group < 0 || group >= plan->ngroups)
+        return LC_ERR_INVALID_ARGUMENT;
+    *v = plan->group_variant[group];
     return LC_OK;
 }
 

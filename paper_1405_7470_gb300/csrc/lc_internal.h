@@ -136,6 +136,16 @@ struct TcArgs {
 
 lc_status tc_launch(const TcArgs &a, int layout, int nterms, int grid, cudaStream_t s);
 
+// Grouped tensor-core launch: per-group plans and the per-CTA unit table.
+static constexpr int kTcMaxGroups = 16;
+struct TcGroupedParams {
+    TcArgs g[kTcMaxGroups];
+    const int4 *map;  // per CTA: {group, column block, first tile, tile step} (device memory)
+    int ngroups;
+};
+lc_status tc_grouped_launch(const TcGroupedParams &P, int layout, int nterms, int grid, int threads, size_t smem,
+                            cudaStream_t s, void **fn_out);
+
 // Surface lift of the dG operator (lift.cu).
 struct LiftArgs {
     const float *L;        // [N][M] lift matrix

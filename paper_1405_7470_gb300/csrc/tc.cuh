@@ -246,8 +246,13 @@ __device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t *r)
 // with per-element geometric factors, out[d,e,i] = sum_f r[e,d,f] * (sum_j D[f,i,j] u[e,j]),
 // every operator in the CTA's one column block; the epilogue mixes the F partial sums of a
 // node with its element's F x F factors before the store.
+//
+// The body is shared by the plain launch (column block and tile share from the CTA index)
+// and the grouped launch (each CTA one (group, column block) unit of a table): `blk` is the
+// CTA's column block, its tiles are my_first, my_first + my_step, ... below a.ntiles.
 template <int LAYOUT, int NT, int CW, int FG>
-__global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_constant__ TcArgs a)
+__device__ __forceinline__ void tc_body(const TcArgs &a, const int blk, const long long my_first,
+                                        const long long my_step)
 {
     constexpr bool NODE = LAYOUT == LC_LAYOUT_NODE_MAJOR;
     constexpr int TE = 128;
@@ -274,7 +279,6 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
     const int NW = 4 * He, NC = 4 * Hc;  // epilogue warps 0..NW-1, conversion warps NW..NW+NC-1
     const int row = 32 * (warp & 3) + lane;  // tile row (== TMEM lane for epilogue warps)
     const int part = (warp < NW ? warp : warp - NW) >> 2;  // which share of the row's K chunks / columns
-    const int blk = blockIdx.x % a.nblocks;  // this CTA's column block
     const int f0 = blk * G;
     const int Gb = min(G, a.F - f0);  // operators in this block
 
@@ -339,8 +343,6 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
     tc_fence_after();
     const uint32_t tmem_base = *tmem_holder;
 
-    const long long my_first = blockIdx.x / a.nblocks;
-    const long long my_step = gridDim.x / a.nblocks;
     // bulk-copy bytes of u tile t (0: not fetchable by the bulk engine, read from global)
     auto tile_bulk_bytes = [&](long long t) -> uint32_t {
         const int TEv = (int)min((long long)TE, E - t * TE);
@@ -913,6 +915,21 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
     tc_fence_after();
     if (warp == mma_warp)
         tmem_dealloc(tmem_base, (uint32_t)a.tmem_alloc);
+}
+
+template <int LAYOUT, int NT, int CW, int FG>
+__global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_constant__ TcArgs a)
+{
+    tc_body<LAYOUT, NT, CW, FG>(a, (int)(blockIdx.x % a.nblocks), blockIdx.x / a.nblocks, gridDim.x / a.nblocks);
+}
+
+// Grouped launch: CTA b runs unit P.map[b] = {group, column block, first tile, tile step} of
+// the group's own plan P.g[group] (one unit per CTA, no group switching inside a CTA).
+template <int LAYOUT, int NT>
+__global__ void __launch_bounds__(832, 1) tc_grouped_kernel(const __grid_constant__ TcGroupedParams P)
+{
+    const int4 m = P.map[blockIdx.x];
+    tc_body<LAYOUT, NT, 8, 0>(P.g[m.x], m.y, m.z, m.w);
 }
 
 // Set the shared-memory size of one kernel instance and launch it.

@@ -93,6 +93,7 @@ SIGNATURES = {
                                ctypes.c_int),
     "lc_grouped_run": ([_P, _P], ctypes.c_int),
     "lc_grouped_plan_info": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)], ctypes.c_int),
+    "lc_grouped_plan_group": ([_P, _I32, _VP], ctypes.c_int),
     "lc_grouped_plan_destroy": ([_P], None),
     "lc_enumerate_variants": ([_P, _I64, _I32, _I32, _I32, _I32, _VP, _I32, ctypes.POINTER(_I32)], ctypes.c_int),
     "lc_autotune": ([_P, _I64, _I32, _I32, _I32, _I32, _P, _P, _P, _I32, _VP, _P, _I32, ctypes.POINTER(_I32), _P],
@@ -364,6 +365,12 @@ class GroupedPlan:
         g, sgs = ctypes.c_int32(), ctypes.c_int32()
         check(self._lib.lc_grouped_plan_info(self._h, ctypes.byref(g), ctypes.byref(sgs)), "lc_grouped_plan_info")
         return dict(grid=g.value, segments=sgs.value)
+
+    def group_variant(self, k: int) -> lc_variant:
+        """The descriptor that serves group k (lc_grouped_plan_group)."""
+        v = lc_variant()
+        check(self._lib.lc_grouped_plan_group(self._h, k, ctypes.byref(v)), "lc_grouped_plan_group")
+        return v
 
     def __del__(self):
         if getattr(self, "_h", None) and self._h.value:

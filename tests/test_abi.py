@@ -257,3 +257,23 @@ def test_geometric_factor_kernel_rules(lib):
     text = kg.print(v)
     assert "out[d, e, i] <- sum((f, j), G[e, d, f]*D[f, i, j]*u[e, j])" in text
     assert "G: GlobalArg" in text
+
+
+def test_grouped_tensor_plan_arguments(lib):
+    """Grouped plans on the tensor cores: at most 16 groups, BF16 / BF16X3 only, null or
+    misaligned buffers refused before any device query."""
+    kernel = lc.Kernel()
+    G = lc.lc_group
+    arr = (G * 17)()
+    for g in arr:
+        g.E, g.N, g.F, g.D_dev, g.u_dev, g.out_dev = 100, 35, 3, 256, 512, 1024
+    need = ctypes.c_size_t(0)
+    v = lc.Variant(engine="tcgen05", precision="bf16x3", tile_e=128, elems_per_thread=64, unroll=4, stages=1,
+                   store_rows=128)
+    assert lib.lc_grouped_workspace_size(kernel.handle, ctypes.byref(v), arr, 17, ctypes.byref(need)) == 1
+    vf = lc.Variant(engine="tcgen05", precision="fp32", tile_e=128, elems_per_thread=64, unroll=4, stages=1)
+    assert lib.lc_grouped_workspace_size(kernel.handle, ctypes.byref(vf), arr, 2, ctypes.byref(need)) == 3
+    arr[0].D_dev = 0
+    assert lib.lc_grouped_workspace_size(kernel.handle, ctypes.byref(v), arr, 2, ctypes.byref(need)) == 1
+    arr[0].D_dev = 258
+    assert lib.lc_grouped_workspace_size(kernel.handle, ctypes.byref(v), arr, 2, ctypes.byref(need)) == 5
