@@ -1162,8 +1162,8 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         const int NT = v->precision == LC_PREC_BF16X3 ? 3 : 1;
         if (v->mma_order < 0 || v->mma_order > 2 || (v->mma_order != 0 && NT != 3))
             return LC_ERR_INVALID_VARIANT;
-        if (v->a_operand < 0 || v->a_operand > 2 || (v->a_operand == 2 && NT != 1))
-            return LC_ERR_INVALID_VARIANT;  // A terms in tensor memory: BF16 only
+        if (v->a_operand < 0 || v->a_operand > 2 || (v->a_operand == 2 && geo && NT != 1))
+            return LC_ERR_INVALID_VARIANT;  // three-term A in tensor memory: not in the geometric-factor kernel
         TcArgs &t = r.tc;
         memset(&t, 0, sizeof t);
         t.N = N;
@@ -1250,12 +1250,13 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         // the most operators per CTA first; for each, the planner's A placement first: tensor
         // memory for BF16 (it frees shared memory for stages and slots), shared memory for
         // BF16X3 (the stacked order needs both accumulators' columns, and a long chain of MMAs
-        // reading A from tensor memory measured slower beside the epilogue's loads)
+        // reading A from tensor memory measured slower beside the epilogue's loads); BF16X3
+        // takes tensor-memory A where no shared-memory plan fits (N above about 100)
         const bool tm_first = v->a_operand == 2 || (v->a_operand == 0 && NT == 1);
         for (int g = g_hi; g >= g_lo && !found; --g)
             for (int pass = 0; pass < 2 && !found; ++pass) {
                 const bool a_tm = tm_first ? pass == 0 : pass == 1;
-                if ((a_tm && v->a_operand == 1) || (!a_tm && v->a_operand == 2) || (a_tm && NT != 1))
+                if ((a_tm && v->a_operand == 1) || (!a_tm && v->a_operand == 2) || (a_tm && geo && NT != 1))
                     continue;
                 for (int c = 0; c < ncombos && !found; ++c) {
                     TcArgs q = t;
@@ -1628,7 +1629,8 @@ lc_status lc_variant_validate(const lc_kernel *kh, int64_t E, int32_t N, int32_t
         if (E < 0 || N < 1 || N > 128)
             return LC_ERR_INVALID_ARGUMENT;
         return (v->engine == LC_ENGINE_SIMT && v->precision == LC_PREC_FP32 && v->layout == LC_LAYOUT_ELEM_MAJOR &&
-                v->ctas_per_sm >= 0 && v->ctas_per_sm <= 8 && v->max_ctas >= 0)
+                v->ctas_per_sm >= 0 && v->ctas_per_sm <= 8 && v->max_ctas >= 0 && v->prefetch_smem >= 0 &&
+                v->prefetch_smem <= 1)
                    ? LC_OK
                    : LC_ERR_INVALID_VARIANT;
     }
@@ -1727,6 +1729,7 @@ lc_status lc_variant_default(const lc_kernel *kh, int64_t E, int32_t N, int32_t 
         d.elems_per_thread = 4;
         d.split_i = 4;
         d.unroll = 4;
+        d.prefetch_smem = 1;
         d.stages = 1;
         d.ctas_per_sm = 4;
         *v = d;

@@ -8,9 +8,15 @@
 // the limit, so the tensor cores would buy nothing here).
 //
 // One CTA walks element tiles of TE elements (persistent, grid-stride):
+//   stage    (add_prefetch, descriptor prefetch_smem = 1) the bulk-copy engine fetches, two
+//            tiles ahead of the compute, the tile's vmapP rows, its face scales and a u
+//            window: the rows of the tile and of `halo` elements on either side, one
+//            contiguous run.  Exterior traces inside the window (on a structured mesh, all
+//            of them) are read from shared memory, the others from global memory;
+//            (prefetch_smem = 0: every operand is read from global memory)
 //   gather   the tile's fluxes flux[m][t] = s[e, m / Nfp] * (u[e, fmask[m]] - u[vmapP[e, m]]),
-//            m-fastest so the vmapP rows are read contiguously, written transposed into
-//            shared memory (rows of odd stride per m: no bank conflicts);
+//            m-fastest, several items per thread in flight, written transposed into shared
+//            memory (padded rows per m);
 //   lift     each thread accumulates a RE x 4 register block (elements x nodes) over m with
 //            L^T (resident in shared memory for the CTA's lifetime), m ascending;
 //   store    out rows, adding to the previous values when accumulating.
@@ -19,14 +25,41 @@
 #include <algorithm>
 
 #include "lc_internal.h"
+#include "tma.cuh"
 
 namespace lc {
 
 static constexpr int kLiftTE = 64;     // elements per tile
 static constexpr int kLiftRE = 4;      // elements per thread
 static constexpr int kLiftRC = 4;      // nodes per thread
-static constexpr int kLiftPad = 1;     // padding of a flux row: odd stride, conflict-free transposed writes
+static constexpr int kLiftPad = 4;     // padding of a flux row: 16-byte rows (one vector load of a thread's
+                                       // four elements), transposed writes at most 4-way bank conflicts
+static constexpr int kLiftG = 4;       // gathered items per thread in flight
 
+__host__ __device__ inline size_t lift_r4(size_t n) { return (n + 3) & ~(size_t)3; }
+
+// Shared memory: L^T [M][NP], the flux tile [M][TP], {node, face} per face node, two
+// mbarriers, then (staged) two buffers of {u window, vmapP tile, scale tile}, 16-byte aligned.
+struct LiftSmem {
+    size_t flux, fmf, bars, buf, buf_bytes, win, vm, sc, total;
+};
+__host__ __device__ inline LiftSmem lift_smem(int N, int M, int Nf, int halo)
+{
+    LiftSmem L;
+    const size_t NP = (size_t)(N + kLiftRC - 1) / kLiftRC * kLiftRC, TP = kLiftTE + kLiftPad;
+    L.flux = sizeof(float) * (size_t)M * NP;
+    L.fmf = L.flux + sizeof(float) * (size_t)M * TP;
+    L.bars = L.fmf + sizeof(int2) * (size_t)M;
+    L.buf = (L.bars + 2 * sizeof(uint64_t) + 15) & ~(size_t)15;
+    L.win = 0;
+    L.vm = halo < 0 ? 0 : sizeof(float) * lift_r4((size_t)(kLiftTE + 2 * halo) * N);
+    L.sc = L.vm + sizeof(int) * lift_r4((size_t)kLiftTE * M);
+    L.buf_bytes = halo < 0 ? 0 : L.sc + sizeof(float) * lift_r4((size_t)kLiftTE * Nf);
+    L.total = L.buf + 2 * L.buf_bytes;
+    return L;
+}
+
+template <bool STAGED>
 __global__ void __launch_bounds__(512) lift_kernel(LiftArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -35,9 +68,12 @@ __global__ void __launch_bounds__(512) lift_kernel(LiftArgs a)
     const int CG = (N + kLiftRC - 1) / kLiftRC;  // column groups
     const int NP = CG * kLiftRC;                 // padded node count
     const int TP = kLiftTE + kLiftPad;           // flux row stride
+    const int H = STAGED ? a.halo : 0;
+    const LiftSmem lay = lift_smem(N, M, Nf, STAGED ? H : -1);
     float *LT = reinterpret_cast<float *>(smem_raw);  // [M][NP]
-    float *flux = LT + (size_t)M * NP;                // [M][TP]
-    int *fm = reinterpret_cast<int *>(flux + (size_t)M * TP);  // [M]
+    float *flux = reinterpret_cast<float *>(smem_raw + lay.flux);  // [M][TP]
+    int2 *fmf = reinterpret_cast<int2 *>(smem_raw + lay.fmf);      // [M] {node, face}
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + lay.bars);
     const long long E = a.E;
     const int tid = threadIdx.x, nthr = blockDim.x;
     for (int idx = tid; idx < M * NP; idx += nthr) {
@@ -47,36 +83,147 @@ __global__ void __launch_bounds__(512) lift_kernel(LiftArgs a)
     for (int m = tid; m < M; m += nthr) {
         const int j = a.fmask[m];
         const bool bad = j < 0 || j >= N;
-        fm[m] = bad ? 0 : j;  // out of range: recorded, node 0 read instead
+        fmf[m] = make_int2(bad ? 0 : j, m / Nfp);  // out of range: recorded, node 0 read instead
         if (bad)
             atomicOr(a.err, 2u);
     }
+    const long long ntiles = (E + kLiftTE - 1) / kLiftTE;
+    // bulk parts (16-byte multiples) of tile t's three runs; the rest is read by plain loads
+    auto runs = [&](long long t, long long &lo, int &wn, int &vn, int &sn) {
+        const long long e0 = t * kLiftTE;
+        const int TEv = (int)min((long long)kLiftTE, E - e0);
+        lo = max(0LL, e0 - H);
+        const long long hi = min(E, e0 + kLiftTE + H);
+        wn = (int)((hi - lo) * N);
+        vn = TEv * M;
+        sn = TEv * Nf;
+    };
+    auto issue = [&](long long t, int b) {
+        long long lo;
+        int wn, vn, sn;
+        runs(t, lo, wn, vn, sn);
+        unsigned char *buf = smem_raw + lay.buf + (size_t)b * lay.buf_bytes;
+        const uint32_t wb = (uint32_t)(wn * 4) & ~15u, vb = (uint32_t)(vn * 4) & ~15u, sb = (uint32_t)(sn * 4) & ~15u;
+        mbar_arrive_expect_tx(&bars[b], wb + vb + sb);
+        const long long e0 = t * kLiftTE;
+        if (wb)
+            bulk_g2s(buf + lay.win, a.u + lo * N, wb, &bars[b]);
+        if (vb)
+            bulk_g2s(buf + lay.vm, a.vmapP + e0 * M, vb, &bars[b]);
+        if (sb)
+            bulk_g2s(buf + lay.sc, a.s + e0 * Nf, sb, &bars[b]);
+    };
+    if (STAGED && tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
     __syncthreads();
+    if (STAGED && tid == 0) {
+        for (int b = 0; b < 2; ++b)
+            if (blockIdx.x + (long long)b * gridDim.x < ntiles)
+                issue(blockIdx.x + (long long)b * gridDim.x, b);
+    }
+    // the gather walks idx = te * M + m = tid, tid + nthr, ...: one step adds dte to te and
+    // dm (< M) to m, with a carry
+    const int dte = nthr / M, dm = nthr - dte * M;
+    const int te_first = tid / M, m_first = tid - te_first * M;
     // register block of this thread: elements eg*RE.., nodes cg*RC..
     const int cg = tid % CG, eg = tid / CG;
     const bool active = eg < kLiftTE / kLiftRE;
-    const long long ntiles = (E + kLiftTE - 1) / kLiftTE;
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int k = 0;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
         const long long e0 = t * kLiftTE;
         const int TEv = (int)min((long long)kLiftTE, E - e0);
-        // gather the tile's fluxes (m fastest: contiguous vmapP rows)
-        for (int idx = tid; idx < kLiftTE * M; idx += nthr) {
-            const int te = idx / M, m = idx - te * M;
-            float v = 0.f;
-            if (te < TEv) {
-                const long long e = e0 + te;
-                const int q = a.vmapP[e * M + m];
-                if (q >= 0 && (long long)q < E * N) {
-                    const float jump = __fsub_rn(a.u[e * N + fm[m]], a.u[q]);
-                    v = __fmul_rn(a.s[e * Nf + m / Nfp], jump);
+        const int b = k & 1;
+        long long lo = 0;
+        int wn = 0, vn = 0, sn = 0;
+        const float *win = nullptr, *scb = nullptr;
+        const int *vm = nullptr;
+        if (STAGED) {
+            runs(t, lo, wn, vn, sn);
+            unsigned char *buf = smem_raw + lay.buf + (size_t)b * lay.buf_bytes;
+            const bool ok = mbar_wait(&bars[b], (uint32_t)((k >> 1) & 1));
+            if (!__syncthreads_and(ok)) {
+                if (tid == 0)
+                    atomicOr(a.err, 1u);
+                break;
+            }
+            float *w = reinterpret_cast<float *>(buf + lay.win);
+            int *v = reinterpret_cast<int *>(buf + lay.vm);
+            float *c = reinterpret_cast<float *>(buf + lay.sc);
+            // the parts past the last 16-byte multiple of each run
+            for (int q = ((wn * 4) & ~15) / 4 + tid; q < wn; q += nthr)
+                w[q] = a.u[lo * N + q];
+            for (int q = ((vn * 4) & ~15) / 4 + tid; q < vn; q += nthr)
+                v[q] = a.vmapP[e0 * M + q];
+            for (int q = ((sn * 4) & ~15) / 4 + tid; q < sn; q += nthr)
+                c[q] = a.s[e0 * Nf + q];
+            __syncthreads();
+            win = w;
+            vm = v;
+            scb = c;
+        }
+        const long long wb = lo * N;  // flat u index of the window's first value
+        // gather the tile's fluxes, kLiftG items per thread in flight: all index loads first,
+        // then all trace loads, then the fluxes
+        int te_c = te_first, m_c = m_first;
+        while (te_c < kLiftTE) {
+            int te[kLiftG], m[kLiftG], q[kLiftG];
+            float ui[kLiftG], ux[kLiftG], sc[kLiftG];
+#pragma unroll
+            for (int g = 0; g < kLiftG; ++g) {
+                te[g] = te_c;
+                m[g] = m_c;
+                te_c += dte;
+                m_c += dm;
+                if (m_c >= M) {
+                    m_c -= M;
+                    ++te_c;
+                }
+                const bool live = te[g] < TEv;
+                q[g] = live ? (STAGED ? vm[te[g] * M + m[g]] : a.vmapP[(e0 + te[g]) * M + m[g]]) : 0;
+            }
+#pragma unroll
+            for (int g = 0; g < kLiftG; ++g) {
+                const bool live = te[g] < TEv;
+                const bool in = live && q[g] >= 0 && (long long)q[g] < E * N;
+                const int2 nf = fmf[live ? m[g] : 0];
+                if (STAGED) {
+                    const long long qw = (long long)q[g] - wb;  // position in the window
+                    ux[g] = in ? ((qw >= 0 && qw < wn) ? win[qw] : a.u[q[g]]) : 0.f;
+                    ui[g] = live ? win[(e0 + te[g] - lo) * N + nf.x] : 0.f;  // the tile lies in the window
+                    sc[g] = live ? scb[te[g] * Nf + nf.y] : 0.f;
                 } else {
-                    v = __int_as_float(0x7fc00000);  // out-of-range index: NaN, recorded
-                    atomicOr(a.err, 2u);
+                    ux[g] = in ? a.u[q[g]] : 0.f;
+                    ui[g] = live ? a.u[(e0 + te[g]) * N + nf.x] : 0.f;
+                    sc[g] = live ? a.s[(e0 + te[g]) * Nf + nf.y] : 0.f;
                 }
             }
-            flux[(size_t)m * TP + te] = v;
+#pragma unroll
+            for (int g = 0; g < kLiftG; ++g) {
+                if (te[g] >= kLiftTE)
+                    break;
+                float v = 0.f;
+                if (te[g] < TEv) {
+                    if (q[g] >= 0 && (long long)q[g] < E * N) {
+                        v = __fmul_rn(sc[g], __fsub_rn(ui[g], ux[g]));
+                    } else {
+                        v = __int_as_float(0x7fc00000);  // out-of-range index: NaN, recorded
+                        atomicOr(a.err, 2u);
+                    }
+                }
+                flux[(size_t)m[g] * TP + te[g]] = v;
+            }
         }
+        fence_async_smem();
         __syncthreads();
+        if (STAGED && tid == 0) {
+            // buffer b is consumed: fetch the tile two steps ahead into it
+            const long long nt = t + 2LL * gridDim.x;
+            if (nt < ntiles)
+                issue(nt, b);
+        }
         if (active) {
             float acc[kLiftRE][kLiftRC];
 #pragma unroll
@@ -89,7 +236,8 @@ __global__ void __launch_bounds__(512) lift_kernel(LiftArgs a)
 #pragma unroll 4
             for (int m = 0; m < M; ++m) {
                 const float4 l4 = *reinterpret_cast<const float4 *>(lp);
-                const float fv[4] = {fp[0], fp[1], fp[2], fp[3]}, lv[4] = {l4.x, l4.y, l4.z, l4.w};
+                const float4 f4 = *reinterpret_cast<const float4 *>(fp);
+                const float fv[4] = {f4.x, f4.y, f4.z, f4.w}, lv[4] = {l4.x, l4.y, l4.z, l4.w};
 #pragma unroll
                 for (int x = 0; x < kLiftRE; ++x)
 #pragma unroll
@@ -116,11 +264,7 @@ __global__ void __launch_bounds__(512) lift_kernel(LiftArgs a)
     }
 }
 
-size_t lift_smem_bytes(int N, int M)
-{
-    const int NP = (N + kLiftRC - 1) / kLiftRC * kLiftRC;
-    return sizeof(float) * ((size_t)M * NP + (size_t)M * (kLiftTE + kLiftPad)) + sizeof(int) * (size_t)M;
-}
+size_t lift_smem_bytes(int N, int M, int Nf, int halo) { return lift_smem(N, M, Nf, halo).total; }
 
 int lift_threads(int N)
 {
@@ -131,11 +275,14 @@ int lift_threads(int N)
 
 lc_status lift_launch(const LiftArgs &a, int grid, cudaStream_t s)
 {
-    const size_t smem = lift_smem_bytes(a.N, a.M);
-    cudaError_t e = cudaFuncSetAttribute(lift_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = lift_smem_bytes(a.N, a.M, a.Nf, a.halo);
+    void *fn = a.halo >= 0 ? reinterpret_cast<void *>(&lift_kernel<true>) : reinterpret_cast<void *>(&lift_kernel<false>);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return cuda_fail(e);
-    lift_kernel<<<grid, lift_threads(a.N), smem, s>>>(a);
+    LiftArgs args = a;
+    void *params[] = {&args};
+    e = cudaLaunchKernel(fn, dim3(grid), dim3(lift_threads(a.N)), params, smem, s);
     e = cudaGetLastError();
     return e == cudaSuccess ? LC_OK : cuda_fail(e);
 }
@@ -159,9 +306,11 @@ lc_status lc_lift(const lc_kernel *kh, const lc_variant *v, const float *L, cons
         return LC_ERR_INVALID_ARGUMENT;
     if (!L || !fmask || (E > 0 && (!vmapP || !s || !u || !out)))
         return LC_ERR_INVALID_ARGUMENT;
-    // FP32 SIMT engine; ctas_per_sm and max_ctas size the persistent grid; nothing else is used
+    // FP32 SIMT engine; prefetch_smem (the u window), ctas_per_sm and max_ctas size the
+    // persistent grid; nothing else is used
     if (v->engine != LC_ENGINE_SIMT || v->precision != LC_PREC_FP32 || v->layout != LC_LAYOUT_ELEM_MAJOR ||
-        v->ctas_per_sm < 0 || v->ctas_per_sm > 8 || v->max_ctas < 0)
+        v->ctas_per_sm < 0 || v->ctas_per_sm > 8 || v->max_ctas < 0 || v->prefetch_smem < 0 ||
+        v->prefetch_smem > 1)
         return LC_ERR_INVALID_VARIANT;
     for (const void *p : {(const void *)L, (const void *)fmask, (const void *)vmapP, (const void *)s,
                           (const void *)u, (const void *)out})
@@ -182,7 +331,21 @@ lc_status lc_lift(const lc_kernel *kh, const lc_variant *v, const float *L, cons
     int major = 0, minor = 0;
     if (current_cc(&major, &minor) != 0 || major != 10 || minor != 3)
         return LC_ERR_NO_DEVICE;
-    if (lift_smem_bytes(N, Nf * Nfp) > smem_optin_limit())
+    // the window's halo: 64 elements (the largest face-neighbour offset of a structured
+    // strip of width 64), halved while the CTA's shared memory would exceed a quarter of the
+    // SM's (four CTAs per SM), none without prefetch_smem
+    // The staged path needs 16-byte aligned u, vmapP and s (bulk copies); others read every
+    // operand from global memory.
+    int halo = -1;
+    if (v->prefetch_smem && ((((uintptr_t)u | (uintptr_t)vmapP | (uintptr_t)s) & 15u) == 0)) {
+        // (a multiple of 4: the window's first row then starts on a 16-byte boundary)
+        halo = 64;
+        while (halo > 0 && lift_smem_bytes(N, Nf * Nfp, Nf, halo) > smem_optin_limit() / 2)
+            halo = halo > 4 ? halo / 2 : 0;
+        if (lift_smem_bytes(N, Nf * Nfp, Nf, halo) > smem_optin_limit())
+            halo = -1;
+    }
+    if (lift_smem_bytes(N, Nf * Nfp, Nf, halo) > smem_optin_limit())
         return LC_ERR_INVALID_VARIANT;
     if (E == 0)
         return LC_OK;
@@ -202,6 +365,7 @@ lc_status lc_lift(const lc_kernel *kh, const lc_variant *v, const float *L, cons
     a.Nfp = Nfp;
     a.M = Nf * Nfp;
     a.accumulate = accumulate;
+    a.halo = halo;
     a.err = error_word();
     const long long ntiles = (E + 63) / 64;
     long long grid = std::min<long long>(ntiles, (long long)(v->ctas_per_sm ? v->ctas_per_sm : 4) * sms);

@@ -6,9 +6,12 @@
 namespace lc {
 
 lc_status tc_launch_node(const TcArgs &a, int nterms, int grid, cudaStream_t s);
+lc_status tc_launch_tmem3(const TcArgs &a, int layout, int grid, cudaStream_t s);
 
 lc_status tc_launch(const TcArgs &a, int layout, int nterms, int grid, cudaStream_t s)
 {
+    if (nterms == 3 && a.a_tmem)
+        return tc_launch_tmem3(a, layout, grid, s);  // three terms, A in tensor memory (tc_tmem3.cu)
     if (layout == LC_LAYOUT_NODE_MAJOR)
         return tc_launch_node(a, nterms, grid, s);  // the node-major instances (tc_node.cu)
     // element-major instance per (terms, epilogue chunk width)

@@ -250,7 +250,7 @@ __device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t *r)
 // The body is shared by the plain launch (column block and tile share from the CTA index)
 // and the grouped launch (each CTA one (group, column block) unit of a table): `blk` is the
 // CTA's column block, its tiles are my_first, my_first + my_step, ... below a.ntiles.
-template <int LAYOUT, int NT, int CW, int FG>
+template <int LAYOUT, int NT, int CW, int FG, bool ATM>
 __device__ __forceinline__ void tc_body(const TcArgs &a, const int blk, const long long my_first,
                                         const long long my_step)
 {
@@ -263,10 +263,12 @@ __device__ __forceinline__ void tc_body(const TcArgs &a, const int blk, const lo
     const uint32_t sbase = smem_addr(smem);
 
     const int N = a.N, G = a.G, CBp = a.CBp, KB = a.KB, nkb = a.nkb;
-    // The A terms in tensor memory are compiled into the BF16 instances only: with three
-    // terms the A reads from tensor memory measured slower beside the epilogue's loads, and
-    // the warp-collective stores would otherwise sit in the three-term conversion loop too.
-    constexpr bool kATmem = NT == 1;
+    // The A terms in tensor memory are compiled into the BF16 instances and into separate
+    // three-term instances (ATM): in the three-term instances for shared-memory A, the
+    // warp-uniform conversion loops the tensor-memory stores need measured slower, and with
+    // three terms the A reads from tensor memory are slower beside the epilogue's loads, so
+    // those plans take them only where the shared-memory plan does not fit (large N).
+    constexpr bool kATmem = ATM;
     const int Np = a.Np;  // accumulator columns per operator (N rounded up to 16)
     // K columns the MMAs read: N rounded up to the 16 of one instruction.  A K-block
     // wider than that keeps its last columns unread, so nothing writes them.
@@ -917,19 +919,20 @@ __device__ __forceinline__ void tc_body(const TcArgs &a, const int blk, const lo
         tmem_dealloc(tmem_base, (uint32_t)a.tmem_alloc);
 }
 
-template <int LAYOUT, int NT, int CW, int FG>
+template <int LAYOUT, int NT, int CW, int FG, bool ATM = (NT == 1)>
 __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_constant__ TcArgs a)
 {
-    tc_body<LAYOUT, NT, CW, FG>(a, (int)(blockIdx.x % a.nblocks), blockIdx.x / a.nblocks, gridDim.x / a.nblocks);
+    tc_body<LAYOUT, NT, CW, FG, ATM>(a, (int)(blockIdx.x % a.nblocks), blockIdx.x / a.nblocks,
+                                     gridDim.x / a.nblocks);
 }
 
 // Grouped launch: CTA b runs unit P.map[b] = {group, column block, first tile, tile step} of
 // the group's own plan P.g[group] (one unit per CTA, no group switching inside a CTA).
-template <int LAYOUT, int NT>
+template <int LAYOUT, int NT, bool ATM = (NT == 1)>
 __global__ void __launch_bounds__(832, 1) tc_grouped_kernel(const __grid_constant__ TcGroupedParams P)
 {
     const int4 m = P.map[blockIdx.x];
-    tc_body<LAYOUT, NT, 8, 0>(P.g[m.x], m.y, m.z, m.w);
+    tc_body<LAYOUT, NT, 8, 0, ATM>(P.g[m.x], m.y, m.z, m.w);
 }
 
 // Set the shared-memory size of one kernel instance and launch it.

@@ -9,11 +9,17 @@ namespace lc {
 lc_status tc_grouped_launch(const TcGroupedParams &P, int layout, int nterms, int grid, int threads, size_t smem,
                             cudaStream_t s, void **fn_out)
 {
-    static void *const fns[2][2] = {{reinterpret_cast<void *>(&tc_grouped_kernel<LC_LAYOUT_ELEM_MAJOR, 1>),
-                                     reinterpret_cast<void *>(&tc_grouped_kernel<LC_LAYOUT_ELEM_MAJOR, 3>)},
+    // three terms: the instance with tensor-memory A stores when any group's plan uses them
+    bool atm = false;
+    for (int g = 0; g < P.ngroups; ++g)
+        atm = atm || P.g[g].a_tmem;
+    static void *const fns[2][3] = {{reinterpret_cast<void *>(&tc_grouped_kernel<LC_LAYOUT_ELEM_MAJOR, 1>),
+                                     reinterpret_cast<void *>(&tc_grouped_kernel<LC_LAYOUT_ELEM_MAJOR, 3>),
+                                     reinterpret_cast<void *>(&tc_grouped_kernel<LC_LAYOUT_ELEM_MAJOR, 3, true>)},
                                     {reinterpret_cast<void *>(&tc_grouped_kernel<LC_LAYOUT_NODE_MAJOR, 1>),
-                                     reinterpret_cast<void *>(&tc_grouped_kernel<LC_LAYOUT_NODE_MAJOR, 3>)}};
-    void *fn = fns[layout == LC_LAYOUT_NODE_MAJOR][nterms == 3];
+                                     reinterpret_cast<void *>(&tc_grouped_kernel<LC_LAYOUT_NODE_MAJOR, 3>),
+                                     reinterpret_cast<void *>(&tc_grouped_kernel<LC_LAYOUT_NODE_MAJOR, 3, true>)}};
+    void *fn = fns[layout == LC_LAYOUT_NODE_MAJOR][nterms == 3 ? (atm ? 2 : 1) : 0];
     if (fn_out)
         *fn_out = fn;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

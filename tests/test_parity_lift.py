@@ -68,10 +68,14 @@ def _needs_gpu():
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("accumulate", [False, True])
-def test_integer_inputs_bit_exact(accumulate):
+@pytest.mark.parametrize("prefetch", [1, 0])
+def test_integer_inputs_bit_exact(accumulate, prefetch):
+    """Both trace paths: the staged u window (prefetch 1; width 200 puts two faces' neighbours
+    outside the 64-element halo, read from global memory) and global loads only (prefetch 0)."""
     torch = _needs_gpu()
     k = lc.Kernel(lc.LIFT_DOMAIN, lc.LIFT_INSTRUCTION)
-    for E, order, width in ((5000 + 13, 4, 64), (777, 2, 8), (64, 3, 4), (1, 1, 1), (3000, 5, 32)):
+    for E, order, width in ((5000 + 13, 4, 64), (777, 2, 8), (64, 3, 4), (1, 1, 1), (3000, 5, 32),
+                            (5000, 4, 200)):
         L, fmask, vmapP, s, u = synth.surface_mesh(E, order=order, width=width, seed=E)
         rng = np.random.default_rng(order)
         L = rng.integers(-3, 4, L.shape).astype(np.float32)
@@ -82,6 +86,7 @@ def test_integer_inputs_bit_exact(accumulate):
         for ctas in (0, 2):
             v = lc.variant_default(k, E, u.shape[1], 1, "elem", "fp32")
             v.max_ctas = ctas
+            v.prefetch_smem = prefetch
             Ld, fd, vd, sd, ud, od = _dev(L, fmask, vmapP, s, u, out0 if accumulate else np.zeros_like(u))
             lc.lift(k, v, Ld, fd, vd, sd, ud, od, accumulate=accumulate)
             torch.cuda.synchronize()
@@ -143,3 +148,29 @@ def test_full_size_sampled():
     got = out.index_select(0, torch.from_numpy(rows).cuda()).cpu().numpy()
     want = oracle.lift(L, fmask, vmapP, s, u)[rows]
     assert oracle.rel_fro_error(got, want) <= 1e-6
+
+
+@pytest.mark.gpu
+def test_window_from_unaligned_u():
+    """u starting 4 bytes past a 16-byte boundary: no bulk copies, every operand read from
+    global memory (the staged path needs 16-byte aligned u, vmapP and s)."""
+    torch = _needs_gpu()
+    k = lc.Kernel(lc.LIFT_DOMAIN, lc.LIFT_INSTRUCTION)
+    L, fmask, vmapP, s, u = synth.surface_mesh(3001, order=4, width=64, seed=5)
+    rng = np.random.default_rng(9)
+    u = rng.integers(-8, 9, u.shape).astype(np.float32)
+    Ld, fd, vd, sd, _ = _dev(L, fmask, vmapP, s, u)
+    flat = torch.empty(u.size + 4, dtype=torch.float32, device="cuda")
+    ud = flat[1:1 + u.size].view(u.shape)
+    ud.copy_(torch.from_numpy(u))
+    v = lc.variant_default(k, u.shape[0], u.shape[1], 1, "elem", "fp32")
+    assert v.prefetch_smem == 1
+    out = lc.lift(k, v, Ld, fd, vd, sd, ud)
+    torch.cuda.synchronize()
+    assert lc.device_error() == 0
+    want = oracle.lift(L, fmask, vmapP, s, u)
+    got = out.cpu().numpy().astype(np.float64)
+    Nfp = fmask.size // 4
+    mag = (np.repeat(np.abs(s.astype(np.float64)), Nfp, axis=1) *
+           (np.abs(u[:, fmask].astype(np.float64)) + np.abs(u.ravel()[vmapP].astype(np.float64)))) @ np.abs(L.T)
+    assert np.all(np.abs(got - want) <= (fmask.size + 4) * 2.0 ** -24 * mag + 1e-30)

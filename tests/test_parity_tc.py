@@ -82,7 +82,7 @@ def test_random_inputs_within_bounds(lc, layout, prec):
             v = lc.variant_default(kernel, E, N, F, layout, prec)
         except lc.LcError:
             # the shared-memory plan of the three-term path does not fit for large N
-            assert prec == "bf16x3" and N > 100
+            assert prec == "bf16x3" and N > 128
             continue
         got = run(lc, kernel, v, D, uu, layout)
         target = oracle.contract_bf16x3(D, uu, layout) if prec == "bf16x3" else oracle.contract_bf16(D, uu, layout)
@@ -204,3 +204,33 @@ def test_full_size_fp32_three_tensor_sampled(lc, layout):
                         "elem", "bf16x3")
     assert np.all(np.abs(got - target) <= bound)
     assert oracle.rel_fro_error(got, oracle.contract_rows(D, u, rows)) <= 1e-6
+
+
+@pytest.mark.parametrize("layout", ["elem", "node"])
+@pytest.mark.parametrize("E,N,F", [(1000, 35, 3), (517, 100, 2), (300, 120, 3), (129, 128, 1), (777, 56, 4)])
+def test_bf16x3_a_in_tensor_memory(lc, layout, E, N, F):
+    """Three-term split with the A terms in tensor memory (a_operand = 2; the planner's plan
+    for N above about 100): integer inputs bit-exact, random inputs within the FP32
+    accumulation bound of the split products and 1e-6 of the exact result."""
+    kernel = lc.Kernel()
+    for kbw, tpr in ((1, 4), (64, 2), (32, 3)):
+        v = lc.Variant(engine="tcgen05", layout=layout, precision="bf16x3", tile_e=128, elems_per_thread=kbw,
+                       split_i=0, unroll=tpr, prefetch_smem=1, stages=1, a_operand=2)
+        if lc.variant_validate(kernel, E, N, F, v) != 0:
+            continue
+        assert lc.variant_plan(kernel, E, N, F, v)["a_in_tmem"] == 1
+        D, u = synth.integer_operands(E, N, F, seed=E + N + kbw)
+        uu = synth.to_node_major(u) if layout == "node" else u
+        got = run(lc, kernel, v, D, uu, layout)
+        assert np.array_equal(got, oracle.contract(D, uu, layout)), (E, N, F, kbw, tpr)
+        D, u = synth.operands(E, N, F, np.float32, seed=E + 3 * N)
+        uu = synth.to_node_major(u) if layout == "node" else u
+        got = run(lc, kernel, v, D, uu, layout)
+        Ds, us = oracle.bf16_split3(D), oracle.bf16_split3(uu)
+        bound = accum_bound(np.abs(Ds[0]) + np.abs(Ds[1]) + np.abs(Ds[2]), np.abs(us[0]) + np.abs(us[1]) + np.abs(us[2]),
+                            layout, "bf16x3")
+        assert np.all(np.abs(got - oracle.contract_bf16x3(D, uu, layout)) <= bound), (E, N, F, kbw)
+        assert oracle.rel_fro_error(got, oracle.contract(D, uu, layout)) <= 1e-6
+    # the planner's own choice for N = 120 keeps the tensor cores
+    v = lc.variant_default(kernel, 300, 120, 3, layout, "bf16x3")
+    assert lc.variant_dict(v)["engine"] == "tcgen05"
