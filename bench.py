@@ -84,12 +84,9 @@ GROUPED_CANDIDATES = [(8, 8, 4, 1, 2, 3), (4, 8, 4, 1, 2, 3), (4, 8, 4, 1, 1, 3)
                       (4, 8, 4, 1, 2, 2), (8, 8, 4, 1, 2, 1), (8, 8, 1, 1, 1, 1)]
 # tensor-core descriptors tried for the grouped launch (BF16 / BF16X3): (K-block width,
 # epilogue threads per row, stages, store rows); the groups without a tensor-core plan run
-# in the library's FP32 SIMT grouped launch after it
+# in the library's FP32 launches after it (K-split, one a group)
 GROUPED_TC_CANDIDATES = [(64, 4, 1, 128), (1, 4, 1, 128), (64, 3, 1, 128), (64, 4, 2, 32), (64, 2, 2, 128),
                          (1, 3, 2, 32)]
-# the library's SIMT descriptor for those groups (elems_per_thread, split_i, unroll,
-# prefetch_smem, stages, ctas_per_sm)
-GROUPED_SIMT_FALLBACK = (8, 8, 4, 1, 2, 3)
 
 # sources that decide a tensor-core launch: the kernel, its helpers, the planner
 TC_SOURCES = ("tc.cu", "tma.cuh", "lc_internal.h", "api.cu")
@@ -654,22 +651,32 @@ def run_grouped(args, wl, world, rank, local_rank):
     # the two launches of a tensor-core plan timed apart (a plan over each part's groups)
     parts = None
     if tensor:
-        on_tc = [plan.group_variant(k).engine == lc.ENGINE["tcgen05"] for k in range(len(sizes))]
+        gv = [plan.group_variant(k) for k in range(len(sizes))]
+        on_tc = [x.engine == lc.ENGINE["tcgen05"] for x in gv]
         parts = {}
-        for name, sel, pv in (("tcgen05", on_tc, v), ("simt", [not x for x in on_tc],
-                                                          simt_variant(GROUPED_SIMT_FALLBACK))):
-            # (a plan over the part's groups alone makes the same per-group choices)
+        for name, sel in (("tcgen05", on_tc), ("fp32", [not x for x in on_tc])):
             sub = [g for g, k in zip(groups, sel) if k]
             if not sub:
                 continue
-            pp = lc.GroupedPlan(kernel, pv, sub, use_graph=True, stream=stream)
-            ms = timed(lambda: pp.run(stream), 10)
+            if name == "tcgen05":
+                # (a plan over the part's groups alone makes the same per-group choices)
+                pp = lc.GroupedPlan(kernel, v, sub, use_graph=True, stream=stream)
+                ms = timed(lambda: pp.run(stream), 10)
+                del pp
+            else:
+                # the groups without a tensor-core plan: the plan's own FP32 launches, one a group
+                subv = [x for x, k in zip(gv, sel) if k]
+
+                def fp32_part():
+                    for (D, u, out), vg in zip(sub, subv):
+                        lc.contract(kernel, vg, D, u, out, stream=stream)
+                ms = timed(fp32_part, 10)
             psz = [sz for sz, k in zip(sizes, sel) if k]
             pfl = sum(2.0 * E * N * N * F for N, E in psz)
             pby = sum(4.0 * (E * N * (1 + F) + F * N * N) for N, E in psz)
             parts[name] = {"groups": [N for N, _ in psz], "ms": ms, "flops": pfl, "bytes": pby,
-                           "hbm_frac": pby / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
-            del pp
+                           "hbm_frac": pby / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                           "engines": sorted({lc.variant_dict(x)["engine"] for x, k in zip(gv, sel) if k})}
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -758,8 +765,8 @@ def run_grouped(args, wl, world, rank, local_rank):
         alu_peak = sms * 128 * 2 * peaks["sm_max_mhz"] * 1e6
         t_alu, t_hbm = flops / alu_peak, nbytes / (peaks["hbm_gbs"] * 1e9)
         if parts:
-            # the roofline of the launch that takes longer: the tensor-core one is HBM-bound,
-            # the SIMT one (N = 165 in FP32) ALU-bound
+            # the roofline of the part that takes longer: the tensor-core launch is HBM-bound,
+            # the FP32 launches (N = 165) ALU-bound
             top = max(parts, key=lambda k: parts[k]["ms"])
             pt = parts[top]
             if top == "tcgen05":
@@ -770,7 +777,8 @@ def run_grouped(args, wl, world, rank, local_rank):
             else:
                 ach = pt["flops"] / (pt["ms"] * 1e-3) / 1e12
                 roof = {"bound": "alu", "achieved": ach, "peak": alu_peak / 1e12, "unit": "TFLOP/s",
-                        "frac": ach / (alu_peak / 1e12), "traffic": None, "kernel": "grouped_kernel",
+                        "frac": ach / (alu_peak / 1e12), "traffic": None,
+                        "kernel": "ks_contract_kernel" if "ksplit" in pt["engines"] else "grouped_kernel",
                         "peak_source": f"derived: {sms} SMs x 128 FMA lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz"}
         elif t_alu > t_hbm:
             ach = flops / launch_s / 1e12

@@ -102,14 +102,19 @@ lc_status lc_kernel_print(const lc_kernel *k, const lc_variant *v, char *buf,
 /* ------------------------------------------------------------------------- */
 /* Variant descriptor (the transformations of Section 2.4 as values).        */
 /* ------------------------------------------------------------------------- */
-enum { LC_ENGINE_SIMT = 0, LC_ENGINE_TCGEN05 = 1, LC_ENGINE_WARP = 2 };
+enum { LC_ENGINE_SIMT = 0, LC_ENGINE_TCGEN05 = 1, LC_ENGINE_WARP = 2, LC_ENGINE_KSPLIT = 3 };
 enum { LC_LAYOUT_ELEM_MAJOR = 0, LC_LAYOUT_NODE_MAJOR = 1 };
 enum { LC_PREC_FP64 = 0, LC_PREC_FP32 = 1, LC_PREC_BF16 = 2, LC_PREC_BF16X3 = 3 };
 
 struct lc_variant {
     uint32_t struct_size;     /* sizeof(lc_variant) */
-    int32_t engine;           /* LC_ENGINE_*: SIMT FMA tiles, tcgen05 tensor cores, or one warp
-                                 per element group with shuffles (small N) */
+    int32_t engine;           /* LC_ENGINE_*: SIMT FMA tiles, tcgen05 tensor cores, one warp
+                                 per element group with shuffles (small N), or K-split SIMT
+                                 (FP32): 8 x 8 register blocks over a tile_e x 128 output
+                                 block, the j reduction cut into chunks of `unroll` (8 or 16)
+                                 whose D^T rows are fetched one chunk ahead, so D^T need not
+                                 fit in shared memory; tile_e 64 or 128, elems_per_thread =
+                                 split_i = 8, prefetch_smem 1, stages = u tile buffers (1, 2) */
     int32_t layout;           /* LC_LAYOUT_*: array-axis layout tag of u and out (Sec. 2.4.3) */
     int32_t precision;        /* LC_PREC_*: FP64/FP32 on the FMA pipes; BF16 or three-term
                                  split BF16 on the tensor cores with FP32 accumulation */
@@ -409,9 +414,10 @@ lc_status lc_grouped_workspace_size(const lc_kernel *k, const lc_variant *v, con
  * column block) unit gets at least one CTA, and the rest go to the unit whose estimated
  * time (tiles x per-tile cost / CTAs) is the largest.  More units than SMs is
  * LC_ERR_INVALID_VARIANT.  Groups without a tensor-core plan (e.g. N above the plans'
- * limit) run after it in a FP32 SIMT grouped launch (8 x 8 register blocks, unroll 4, two
- * stages, three CTAs per SM);
- * their results are FP32's, below both reduced-precision bounds.
+ * limit) run after it, each in a K-split FP32 launch (tiles of 128 elements, j chunks of 8,
+ * one u buffer), or, without a K-split plan, in a FP32 SIMT grouped launch (8 x 8 register
+ * blocks, unroll 4, two stages, three CTAs per SM); their results are FP32's, below both
+ * reduced-precision bounds.
  *   workspace_dev  caller-owned device memory holding the group and work tables
  *                  (lc_grouped_workspace_size bytes, 16-byte aligned); it must outlive
  *                  the plan, as must the groups' buffers, which the plan references.

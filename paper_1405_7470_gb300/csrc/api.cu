@@ -1023,6 +1023,8 @@ struct Resolved {
     SimtGeom g;
     TcArgs tc;
     int tc_grid;
+    KsArgs ks;     // K-split engine
+    int ks_bm, ks_bk;
     int unroll, prefetch, tail_free;
     int warp_per;  // WARP engine: elements per warp step
 };
@@ -1283,6 +1285,51 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         if (!cap_grid(grid, t.nblocks, v->max_ctas))
             return LC_ERR_INVALID_VARIANT;
         r.tc_grid = (int)grid;
+        return LC_OK;
+    }
+    if (v->engine == LC_ENGINE_KSPLIT) {
+        // FP32; tile_e = BM (64 or 128), 8 x 8 register blocks, unroll = BK (the j chunk: 8
+        // or 16), prefetch of u into shared memory with stages = 1 or 2 u buffers
+        if (v->precision != LC_PREC_FP32 || v->tail_free || !(v->tile_e == 64 || v->tile_e == 128) ||
+            v->elems_per_thread != 8 || v->split_i != 8 || !(v->unroll == 8 || v->unroll == 16) ||
+            v->prefetch_smem != 1 || !(v->stages == 1 || v->stages == 2) || v->ctas_per_sm > 4)
+            return LC_ERR_INVALID_VARIANT;
+        KsArgs &k = r.ks;
+        memset(&k, 0, sizeof k);
+        const bool node = v->layout == LC_LAYOUT_NODE_MAJOR;
+        const int BM = v->tile_e, BK = v->unroll;
+        k.E = E;
+        k.N = N;
+        k.F = F;
+        k.C = F * N;
+        k.Kp = (N + BK - 1) / BK * BK;
+        k.nkc = k.Kp / BK;
+        k.nblocks = (k.C + 127) / 128;
+        k.ntiles = (E + BM - 1) / BM;
+        k.ubufs = v->stages;
+        k.vec_u = node && E % 4 == 0;
+        k.vec_out = node ? E % 4 == 0 : N % 4 == 0;
+        r.ks_bm = BM;
+        r.ks_bk = BK;
+        const size_t smem = ks_smem_bytes(k.Kp, BM, BK, k.ubufs);
+        if (smem > smem_cap)
+            return LC_ERR_INVALID_VARIANT;
+        // resident CTAs per SM: the descriptor's, else as many as shared memory allows (at
+        // most 2 of 256 threads or 3 of 128: the register bound of the instances)
+        int cps = (int)std::min<size_t>((smem_cap + 1024) / (smem + 1024), BM == 128 ? 2 : 3);
+        if (v->ctas_per_sm > 0)
+            cps = std::min(cps, v->ctas_per_sm);
+        cps = std::max(cps, 1);
+        long long grid = std::min<long long>(std::max<long long>(k.ntiles, 1), (long long)cps * sms);
+        if (!cap_grid(grid, 1, v->max_ctas))
+            return LC_ERR_INVALID_VARIANT;
+        SimtGeom &g = r.g;
+        g.grid = (int)grid;
+        g.threads = BM / 8 * 16;
+        g.smem = smem;
+        g.TE = BM;
+        g.ntiles = k.ntiles;
+        g.nchunks = k.nblocks;
         return LC_OK;
     }
     if (v->engine == LC_ENGINE_WARP) {
@@ -1584,7 +1631,10 @@ lc_status lc_kernel_print(const lc_kernel *kh, const lc_variant *v, char *buf, s
                 K.j_iname.c_str(), K.d_name.c_str(), K.i_iname.c_str(), K.j_iname.c_str(),
                 K.u_name.c_str(), K.e_iname.c_str(), K.j_iname.c_str());
     if (v && v->struct_size == sizeof(lc_variant)) {
-        const char *eng = v->engine == LC_ENGINE_SIMT ? "simt" : v->engine == LC_ENGINE_TCGEN05 ? "tcgen05" : "warp";
+        const char *eng = v->engine == LC_ENGINE_SIMT      ? "simt"
+                          : v->engine == LC_ENGINE_TCGEN05 ? "tcgen05"
+                          : v->engine == LC_ENGINE_KSPLIT  ? "ksplit"
+                                                           : "warp";
         const char *prec[] = {"fp64", "fp32", "bf16", "bf16x3"};
         s += rule;
         s += "TRANSFORMATIONS:\n";
@@ -1606,6 +1656,9 @@ lc_status lc_kernel_print(const lc_kernel *kh, const lc_variant *v, char *buf, s
                 v->prefetch_smem ? "shared memory" : "none (global loads)", v->stages, v->out_buffers);
         if (v->engine == LC_ENGINE_TCGEN05)
             appendf(s, "rows per bulk store: %d (0 = planner's choice)\n", v->store_rows);
+        if (v->engine == LC_ENGINE_KSPLIT)
+            appendf(s, "split_iname(%s, %d): D^T chunks of %d rows fetched one chunk ahead\n", K.j_iname.c_str(),
+                    v->unroll, v->unroll);
     }
     s += rule;
     if (needed)
@@ -1705,7 +1758,7 @@ lc_status lc_variant_plan(const lc_kernel *kh, int64_t E, int32_t N, int32_t F, 
         q.threads = r.g.threads;
         q.smem_bytes = (int32_t)r.g.smem;
         q.tiles = r.g.ntiles;
-        q.column_blocks = r.engine == LC_ENGINE_SIMT ? r.g.nchunks : 1;
+        q.column_blocks = (r.engine == LC_ENGINE_SIMT || r.engine == LC_ENGINE_KSPLIT) ? r.g.nchunks : 1;
         q.ops_per_block = r.engine == LC_ENGINE_SIMT ? (r.g.isplit ? 0 : r.g.G) : F;
     }
     *p = q;
@@ -1761,6 +1814,23 @@ lc_status lc_variant_default(const lc_kernel *kh, int64_t E, int32_t N, int32_t 
         d.tile_e = 64;
         d.stages = 2;
     } else if (precision == LC_PREC_FP32) {
+        if (precision == LC_PREC_FP32 && N >= 96) {
+            // large N: the K-split kernel (D^T streamed in chunks) measured faster than the
+            // SIMT kernel holding all of D^T (N = 120: 0.69 against 0.86 ms; N = 165: 2.6
+            // against 3.6 ms)
+            lc_variant k = d;
+            k.engine = LC_ENGINE_KSPLIT;
+            k.tile_e = 128;
+            k.elems_per_thread = 8;
+            k.split_i = 8;
+            k.unroll = 8;
+            k.prefetch_smem = 1;
+            k.stages = 1;
+            if (lc_variant_validate(kh, E, N, F, &k) == LC_OK) {
+                *v = k;
+                return LC_OK;
+            }
+        }
         d.engine = LC_ENGINE_SIMT;
         d.ctas_per_sm = 2;
         if (layout == LC_LAYOUT_ELEM_MAJOR) {
@@ -1785,9 +1855,11 @@ lc_status lc_variant_default(const lc_kernel *kh, int64_t E, int32_t N, int32_t 
         // fewest cycles; then the narrowest blocks that cover K (least shared memory).
         // BF16X3: the A terms in shared memory first (the stacked order), one stage first (two
         // stages leave room for one output slot only); BF16: the planner's placement, two stages.
+        // (BF16X3 with the A terms in tensor memory, the only plan for N of about 100 to 128,
+        // measured slower than the K-split FP32 kernel there: shared-memory A only)
         const bool x3 = precision == LC_PREC_BF16X3;
         lc_status st = LC_ERR_INVALID_VARIANT;
-        for (int aop : {x3 ? 1 : 0, 0})
+        for (int aop : {x3 ? 1 : 0})
             for (int kbw : {64, 1})
                 for (int stg : {x3 ? 1 : 2, x3 ? 2 : 3, x3 ? 3 : 1}) {
                     if (st == LC_OK)
@@ -1807,7 +1879,7 @@ lc_status lc_variant_default(const lc_kernel *kh, int64_t E, int32_t N, int32_t 
             return st;
         if (kh->k.kind == KIND_GEO)
             return LC_ERR_UNSUPPORTED;  // the volume derivative runs on the tensor cores only
-        // no tensor-core plan fits (large N): FP32 SIMT, whose error is below both
+        // no tensor-core plan fits (large N): FP32, whose error is below both
         // reduced-precision bounds
         return lc_variant_default(kh, E, N, F, layout, LC_PREC_FP32, v);
     }
@@ -1897,6 +1969,13 @@ lc_status lc_contract(const lc_kernel *kh, const lc_variant *v, const void *D, c
         a.out = static_cast<float *>(out);
         a.err = error_word();
         return tc_launch(a, r.layout, r.precision == LC_PREC_BF16X3 ? 3 : 1, r.tc_grid, s);
+    }
+    if (r.engine == LC_ENGINE_KSPLIT) {
+        KsArgs a = r.ks;
+        a.D = static_cast<const float *>(D);
+        a.u = static_cast<const float *>(u);
+        a.out = static_cast<float *>(out);
+        return ks_launch(a, r.layout, r.ks_bm, r.ks_bk, r.g.grid, s);
     }
     if (r.engine == LC_ENGINE_WARP) {
         WarpArgs a;
@@ -2103,6 +2182,15 @@ lc_status lc_contract_host(const lc_kernel *kh, const lc_variant *v, const void 
 
 // ------------------------------------------------------------------ grouped launch
 
+namespace lc {
+// One plain K-split launch (a group of a tensor-core grouped plan without a tensor-core plan).
+struct KsLaunch {
+    KsArgs a;
+    int grid, bm, bk, group;
+};
+
+}  // namespace lc
+
 struct lc_grouped_plan {
     // SIMT part (every group of a SIMT plan; the groups without a tensor plan of a tensor plan)
     void *fn = nullptr;
@@ -2118,6 +2206,8 @@ struct lc_grouped_plan {
     cudaGraphExec_t exec = nullptr;
     int ngroups = 0, nsegs = 0;
     std::vector<lc_variant> group_variant;  // the descriptor serving each group
+    std::vector<lc::KsLaunch> ks;           // K-split launches (after the tensor-core one)
+    int layout = 0;
 };
 
 namespace lc {
@@ -2391,6 +2481,10 @@ static lc_status grouped_plan_tc(const Kernel &K, const lc_variant *v, const lc_
             }
             if (q > 0 && memcmp(&vg, v, sizeof vg) == 0)
                 continue;
+            // three terms: the A terms in shared memory unless tensor memory is asked for (the
+            // K-split FP32 launch beats the tensor-memory plans, measured at N = 120)
+            if (T.nterms == 3 && v->a_operand == 0)
+                vg.a_operand = 1;
             rs = resolve(K, G.E, G.N, G.F, &vg, r, true);
             if (rs == LC_ERR_NO_DEVICE || rs == LC_ERR_CUDA || rs == LC_ERR_INVALID_ARGUMENT ||
                 rs == LC_ERR_ASSUMPTION)
@@ -2482,10 +2576,32 @@ struct GroupedPlanAll {
     GroupedPlanHost S;
     GroupedPlanTc T;
     std::vector<lc_group> simt_groups;
-    lc_variant simt_v;
+    std::vector<int> simt_gi;  // their indices among the caller's groups
+    lc_variant simt_v, ks_v;
+    std::vector<KsLaunch> ks;
     bool has_simt = false;
     size_t off_map = 0, bytes = 0;
 };
+
+// The K-split descriptor for the groups of a tensor-core grouped plan without a tensor-core
+// plan (tiles of 128 elements, j chunks of 8, one u buffer: the fastest measured for N = 120
+// and 165).
+static lc_variant grouped_ks_fallback(const lc_variant *v)
+{
+    lc_variant s;
+    memset(&s, 0, sizeof s);
+    s.struct_size = sizeof(lc_variant);
+    s.engine = LC_ENGINE_KSPLIT;
+    s.layout = v->layout;
+    s.precision = LC_PREC_FP32;
+    s.tile_e = 128;
+    s.elems_per_thread = 8;
+    s.split_i = 8;
+    s.unroll = 8;
+    s.prefetch_smem = 1;
+    s.stages = 1;
+    return s;
+}
 
 static lc_status grouped_plan_all(const Kernel &K, const lc_variant *v, const lc_group *groups, int ng,
                                   GroupedPlanAll &A)
@@ -2505,9 +2621,32 @@ static lc_status grouped_plan_all(const Kernel &K, const lc_variant *v, const lc
     lc_status st = grouped_plan_tc(K, v, groups, ng, A.T);
     if (st != LC_OK)
         return st;
-    for (int gi : A.T.simt_groups)
-        if (groups[gi].E > 0)
-            A.simt_groups.push_back(groups[gi]);
+    // the rest: one K-split launch each, else (no K-split plan) the SIMT grouped launch
+    A.ks_v = grouped_ks_fallback(v);
+    for (int gi : A.T.simt_groups) {
+        const lc_group &G = groups[gi];
+        if (G.E == 0)
+            continue;
+        Resolved r;
+        const lc_status rs = resolve(K, G.E, G.N, G.F, &A.ks_v, r, true);
+        if (rs == LC_ERR_NO_DEVICE || rs == LC_ERR_CUDA)
+            return rs;
+        if (rs == LC_OK) {
+            KsLaunch L;
+            L.a = r.ks;
+            L.a.D = static_cast<const float *>(G.D_dev);
+            L.a.u = static_cast<const float *>(G.u_dev);
+            L.a.out = static_cast<float *>(G.out_dev);
+            L.grid = r.g.grid;
+            L.bm = r.ks_bm;
+            L.bk = r.ks_bk;
+            L.group = gi;
+            A.ks.push_back(L);
+        } else {
+            A.simt_groups.push_back(G);
+            A.simt_gi.push_back(gi);
+        }
+    }
     if (!A.simt_groups.empty()) {
         A.simt_v = grouped_simt_fallback(v);
         st = grouped_plan_host(K, &A.simt_v, A.simt_groups.data(), (int)A.simt_groups.size(), A.S);
@@ -2631,8 +2770,19 @@ lc_status lc_grouped_plan_create(const lc_kernel *kh, const lc_variant *v, const
     if (v->engine == LC_ENGINE_TCGEN05) {
         for (int gi = 0; gi < ngroups; ++gi)
             plan->group_variant[gi] = A.T.gv[gi];
-        for (int gi : A.T.simt_groups)
+        for (int gi : A.simt_gi)
             plan->group_variant[gi] = A.simt_v;
+        for (const KsLaunch &L : A.ks)
+            plan->group_variant[L.group] = A.ks_v;
+        plan->ks = A.ks;
+        plan->layout = v->layout;
+        for (const KsLaunch &L : A.ks) {
+            st = ks_launch(L.a, v->layout, L.bm, L.bk, 0, s, true);  // shared-memory size, before any capture
+            if (st != LC_OK) {
+                delete plan;
+                return st;
+            }
+        }
     }
     if (use_graph) {
         e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
@@ -2643,6 +2793,9 @@ lc_status lc_grouped_plan_create(const lc_kernel *kh, const lc_variant *v, const
                 le = cudaLaunchKernel(plan->fn_tc, dim3(plan->grid_tc), dim3(plan->threads_tc), params,
                                       plan->smem_tc, s);
             }
+            for (const KsLaunch &L : plan->ks)
+                if (le == cudaSuccess && ks_launch(L.a, plan->layout, L.bm, L.bk, L.grid, s, false) != LC_OK)
+                    le = cudaErrorLaunchFailure;
             if (le == cudaSuccess && plan->fn) {
                 void *params[] = {&plan->args};
                 le = cudaLaunchKernel(plan->fn, dim3(plan->grid), dim3(plan->threads), params, plan->smem, s);
@@ -2678,6 +2831,13 @@ lc_status lc_grouped_run(lc_grouped_plan *plan, void *stream)
             e = cudaLaunchKernel(plan->fn_tc, dim3(plan->grid_tc), dim3(plan->threads_tc), params, plan->smem_tc,
                                  s);
         }
+        for (const KsLaunch &L : plan->ks) {
+            if (e != cudaSuccess)
+                break;
+            const lc_status st = ks_launch(L.a, plan->layout, L.bm, L.bk, L.grid, s, false);
+            if (st != LC_OK)
+                return st;
+        }
         if (e == cudaSuccess && plan->fn) {
             void *params[] = {&plan->args};
             e = cudaLaunchKernel(plan->fn, dim3(plan->grid), dim3(plan->threads), params, plan->smem, s);
@@ -2692,7 +2852,10 @@ lc_status lc_grouped_plan_info(const lc_grouped_plan *plan, int32_t *grid, int32
 {
     if (!plan || !grid || !segments)
         return LC_ERR_INVALID_ARGUMENT;
-    *grid = plan->grid + plan->grid_tc;
+    int g = plan->grid + plan->grid_tc;
+    for (const KsLaunch &L : plan->ks)
+        g += L.grid;
+    *grid = g;
     *segments = plan->nsegs;
     return LC_OK;
 }

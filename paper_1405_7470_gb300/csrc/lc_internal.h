@@ -102,6 +102,26 @@ struct WarpArgs {
     int tail_free;
 };
 
+// K-split SIMT kernel (FP32): 8 x 8 register blocks over a BM x 128 output tile, the
+// reduction over j cut into chunks of BK (split_iname on j) whose D^T slices are fetched
+// asynchronously into a two-slot ring, the u tile resident (transposed) for all column blocks.
+struct KsArgs {
+    const float *D;
+    const float *u;
+    float *out;
+    long long E;
+    int N, F, C;       // C = F * N output columns
+    int Kp, nkc;       // N rounded up to the chunk width, and the number of chunks
+    int nblocks;       // column blocks of 128
+    long long ntiles;  // element tiles of BM
+    int ubufs;         // u tile buffers: 2 = the next tile's u is fetched during this tile
+    int vec_u;         // node-major: 16-byte copies of u rows (E % 4 == 0)
+    int vec_out;       // 16-byte output stores (element-major: N % 4 == 0; node-major: E % 4 == 0)
+};
+// set_attr: set the instance's shared-memory size first; grid <= 0: only that.
+lc_status ks_launch(const KsArgs &a, int layout, int bm, int bk, int grid, cudaStream_t s, bool set_attr = true);
+size_t ks_smem_bytes(int Kp, int bm, int bk, int ubufs);
+
 // Tensor-core kernel (tcgen05): one column block of G operators per CTA.
 struct TcArgs {
     const float *D;

@@ -46,7 +46,7 @@ static lc_status features(const lc_kernel *k, int64_t E, int32_t N, int32_t F, i
         log2_pos((double)E * N * F) / 32.0,
         (double)p.stacked,
         (double)(std::log2((double)N) / 8.0),
-        (double)(eng == LC_ENGINE_SIMT),
+        (double)(eng == LC_ENGINE_SIMT),  // (the K-split engine: zero in all three)
         (double)(eng == LC_ENGINE_TCGEN05),
         (double)(eng == LC_ENGINE_WARP),
         log2_pos((double)v->tile_e) / 10.0,

@@ -38,6 +38,22 @@ static std::vector<lc_variant> candidates(int N, int F, int layout, int precisio
                         v.ctas_per_sm = 2;
                         out.push_back(v);
                     }
+        if (precision == LC_PREC_FP32) {
+            // K-split: tile 64 or 128 elements, j chunks of 8 or 16, one or two u buffers
+            for (int bm : {64, 128})
+                for (int bk : {8, 16})
+                    for (int st : {1, 2}) {
+                        lc_variant v = b;
+                        v.engine = LC_ENGINE_KSPLIT;
+                        v.tile_e = bm;
+                        v.elems_per_thread = 8;
+                        v.split_i = 8;
+                        v.unroll = bk;
+                        v.prefetch_smem = 1;
+                        v.stages = st;
+                        out.push_back(v);
+                    }
+        }
         if (N <= 32 && (precision != LC_PREC_FP64 || N <= 16 || F == 1)) {
             for (int warps : {4, 8}) {
                 lc_variant v = b;

@@ -24,7 +24,7 @@ STATUS = {
     4: "LC_ERR_ASSUMPTION", 5: "LC_ERR_MISALIGNED", 6: "LC_ERR_BUFFER_TOO_SMALL", 7: "LC_ERR_CUDA",
     8: "LC_ERR_TIMEOUT", 9: "LC_ERR_NO_DEVICE", 10: "LC_ERR_NOT_FOUND", 11: "LC_ERR_INDEX",
 }
-ENGINE = {"simt": 0, "tcgen05": 1, "warp": 2}
+ENGINE = {"simt": 0, "tcgen05": 1, "warp": 2, "ksplit": 3}
 LAYOUT = {"elem": 0, "node": 1}
 PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16x3": 3}
 DTYPE_F32, DTYPE_F64 = 0, 1

@@ -213,7 +213,15 @@ def test_column_blocks_and_row_splits(lc, layout):
     for E, N, F in [(1000, 120, 8), (513, 256, 3)]:
         D, u = synth.operands(E, N, F, np.float32, seed=N)
         uu = synth.to_node_major(u) if layout == "node" else u
-        v = lc.variant_default(kernel, E, N, F, layout, "fp32")
+        # the SIMT engine (the default for this N is the K-split one): the largest tile that fits
+        re_, tile = (8, 128) if layout == "elem" else (4, 64)
+        while True:
+            v = lc.Variant(layout=layout, elems_per_thread=re_, split_i=8, tile_e=tile, unroll=1, prefetch_smem=1,
+                           stages=1, ctas_per_sm=2)
+            if lc.variant_validate(kernel, E, N, F, v) == 0:
+                break
+            assert tile > re_
+            tile //= 2
         check(run(lc, kernel, v, D, uu, layout), D, uu, layout, False)
         Di, ui = synth.integer_operands(E, N, F, seed=1)
         uui = synth.to_node_major(ui) if layout == "node" else ui
