@@ -88,21 +88,43 @@ GROUPED_CANDIDATES = [(8, 8, 4, 1, 2, 3), (4, 8, 4, 1, 2, 3), (4, 8, 4, 1, 1, 3)
 GROUPED_TC_CANDIDATES = [(64, 4, 1, 128), (1, 4, 1, 128), (64, 3, 1, 128), (64, 4, 2, 32), (64, 2, 2, 128),
                          (1, 3, 2, 32)]
 
-# sources that decide a tensor-core launch: the kernel, its helpers, the planner
-TC_SOURCES = ("tc.cu", "tma.cuh", "lc_internal.h", "api.cu")
+# sources that decide each measured kernel's launch: the kernel, its helpers, the planner
+TC_SOURCES = ('tc.cu', 'tc.cuh', 'tma.cuh', 'lc_internal.h', 'api.cu')
+GEO_SOURCES = ('tc_geo.cu', 'tc.cuh', 'tma.cuh', 'lc_internal.h', 'api.cu')
+LIFT_SOURCES = ('lift.cu', 'tma.cuh', 'lc_internal.h', 'api.cu')
+SAXPY_SOURCES = ('frontend.cu', 'lc_internal.h', 'api.cu')
 
-# DRAM bytes per launch from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum),
-# keyed by (workload, layout, precision, engine); valid only while the kernel sources hash
-# to `src`.  `variant` records the descriptor the capture ran.
+# DRAM bytes per launch from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of one
+# full-size launch, keyed by (workload, layout, precision, engine); valid only while the kernel's
+# sources hash to `src`.  `variant` records the descriptor the capture ran.
 NCU_TRAFFIC = {
-    # full size (E = 2^21): dram__bytes_read.sum + dram__bytes_write.sum of one launch, 293.70 MB
-    # + 818.53 MB (the remaining 62 MB of output was still in L2 when the kernel ended)
+    # E = 2^21: 293.74 MB read + 818.24 MB written (the rest of the output still in L2 at the end)
     ("fp32_three", "elem", "bf16x3", "tcgen05"): {
-        "bytes": 293_700_000 + 818_530_000, "files": TC_SOURCES, "src": "e1886cc104db6c29",
+        "bytes": 293_741_568 + 818_236_416, "files": TC_SOURCES, "src": "e482d15eaccb6162",
         "variant": {"tile_e": 128, "elems_per_thread": 64, "split_i": 0, "unroll": 4, "stages": 1,
                     "store_rows": 128}},
+    # volume derivative, E = 2^21: 369.21 MB read + 818.90 MB written
+    ("geo", "elem", "bf16x3", "tcgen05"): {
+        "bytes": 369_205_504 + 818_903_808, "files": GEO_SOURCES, "src": "1d512953fbe7dd1d",
+        "variant": {"tile_e": 128, "elems_per_thread": 64, "split_i": 0, "unroll": 4, "stages": 1,
+                    "a_operand": 1}},
+    # surface lift, E = 2^21: 832.54 MB read + 268.27 MB written
+    ("lift", "elem", "fp32", "simt"): {
+        "bytes": 832_543_232 + 268_273_408, "files": LIFT_SOURCES, "src": "f5e76986811ec96a",
+        "variant": {"tile_e": 64, "prefetch_smem": 1, "ctas_per_sm": 4}},
+    # saxpy, n = 2^28: 2147.52 MB read + 1036.25 MB written
+    ("saxpy", "elem", "fp32", "simt"): {
+        "bytes": 2_147_521_024 + 1_036_252_928, "files": SAXPY_SOURCES, "src": "e22327623d23fd95",
+        "variant": {"elems_per_thread": 4, "unroll": 4, "ctas_per_sm": 4}},
 }
 
+
+def ncu_traffic(workload: str, layout: str, precision: str, engine: str):
+    """The recorded DRAM bytes of one launch, or None when absent or the sources changed since."""
+    rec = NCU_TRAFFIC.get((workload, layout, precision, engine))
+    if rec and rec.get("bytes") and rec.get("src") == csrc_hash(rec.get("files")):
+        return rec["bytes"]
+    return None
 
 
 def csrc_hash(files=None) -> str:
@@ -250,9 +272,7 @@ def roofline_for(v, wl, peaks, sms, t_launch_s, workload_key):
     t_hbm = nbytes / (peaks["hbm_gbs"] * 1e9)
     engine = v["engine"]
     traffic = None
-    rec = NCU_TRAFFIC.get((workload_key, v["layout"], v["precision"], engine))
-    if rec and rec.get("bytes") and rec.get("src") == csrc_hash(rec.get("files")):
-        traffic = rec["bytes"]
+    traffic = ncu_traffic(workload_key, v["layout"], v["precision"], engine)
     if engine == "tcgen05":
         # tensor pipe: one bf16 product per kept term pair (1 for bf16, 6 for bf16x3)
         npairs = 6 if wl["precision"] == "bf16x3" else 1
@@ -913,7 +933,9 @@ def run_geo(args, wl, world, rank, local_rank):
                        "bytes_per_step": nbytes, "l2": "inputs+outputs larger than L2 (no flush needed)",
                        "unfused_bytes_per_step": 4.0 * (E * N + 2 * F * E * N + E * F * F + F * E * N)},
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": peaks["source"]},
+                         "frac": ach / peaks["hbm_gbs"],
+                         "traffic": ncu_traffic("geo", args.layout, wl["precision"], "tcgen05"),
+                         "peak_source": peaks["source"]},
             "cpu_baseline": None, "e2e": None, "gpu_launches": args.steps, "clocks": clk,
             "rel_error_vs_oracle": rel_err, "hbm_gbs_achieved": nbytes / (ms * 1e-3) / 1e9,
         }
@@ -998,7 +1020,8 @@ def run_saxpy(args, wl, world, rank, local_rank):
                        "variant_choice": "fastest unroll x CTAs/SM of 12", "bytes_per_step": nbytes,
                        "l2": "inputs+outputs larger than L2 (no flush needed)"},
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": peaks["source"]},
+                         "frac": ach / peaks["hbm_gbs"], "traffic": ncu_traffic("saxpy", "elem", "fp32", "simt"),
+                         "peak_source": peaks["source"]},
             "cpu_baseline": None, "e2e": None, "gpu_launches": args.steps, "clocks": clk,
             "bit_exact_vs_oracle_sample": exact,
         }
@@ -1081,7 +1104,8 @@ def run_lift(args, wl, world, rank, local_rank):
                        "variant_choice": "fastest CTAs/SM of 6", "bytes_per_step": nbytes,
                        "l2": "inputs+outputs larger than L2 (no flush needed)"},
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": peaks["source"]},
+                         "frac": ach / peaks["hbm_gbs"], "traffic": ncu_traffic("lift", "elem", "fp32", "simt"),
+                         "peak_source": peaks["source"]},
             "cpu_baseline": None, "e2e": None, "gpu_launches": args.steps, "clocks": clk,
             "rel_error_vs_oracle": rel_err, "hbm_gbs_achieved": nbytes / (ms * 1e-3) / 1e9,
         }
