@@ -249,6 +249,20 @@ def evaluate(params, recs, pool=None, seeds=None, reps: int = 5, rounds: int = 3
                 retimed=pool is not None)
 
 
+def by_path(recs, ev):
+    """Held-out regrets grouped by the requested path; reduced-precision requests that the
+    library serves with FP32 kernels (no tensor-core candidate) form their own groups."""
+    groups = {}
+    for rec, m, d in zip(recs, ev["mlp_per_shape"], ev["default_per_shape"]):
+        path = rec["shape"]["path"]
+        tensor = any(v.get("engine") == "tcgen05" for _, v in rec["cands"])
+        key = path if (path == "fp32" or tensor) else path + " served by FP32"
+        g = groups.setdefault(key, ([], []))
+        g[0].append(m)
+        g[1].append(d)
+    return {k: dict(shapes=len(m), mlp=regret_stats(m), default=regret_stats(d)) for k, (m, d) in groups.items()}
+
+
 def make_pool(shapes):
     return ProblemPool(max(s["E"] * s["N"] for s in shapes), max(s["E"] * s["N"] * s["F"] for s in shapes),
                        max(s["F"] * s["N"] ** 2 for s in shapes))
@@ -277,6 +291,7 @@ def run_experiment(out_path: str, n_shapes: int = 600, n_train: int = 500, reps:
     res = dict(n_shapes=n_shapes, n_train=n_train, samples=int(len(y)), epochs=epochs,
                autotune_wall_s=tune_total, autotune_wall_s_per_shape=float(np.mean([r["tune_s"] for r in recs])),
                train_wall_s=train_s, retime_wall_s=retime_s, loss_history=hist, heldout=ev_te,
+               heldout_by_path=by_path(te, ev_te),
                heldout_from_tuning_pass=dict(mlp=ev_te_pass["mlp"], default=ev_te_pass["default"]),
                train_fit=dict(mlp=ev_tr["mlp"]),
                candidates_per_shape=float(np.mean([len(r["cands"]) for r in recs])))
