@@ -130,8 +130,11 @@ struct lc_variant {
                                  row: the same, 2 for 4) */
     int32_t prefetch_smem;    /* add_prefetch of the u tile into shared memory by TMA (1) or
                                  direct global loads into registers (0); tensor-core engine: 1,
-                                 or (BF16) 2 = each converting thread takes its values into
-                                 registers and frees the stage at once (K of one block only) */
+                                 or 2 = each converting thread takes its values into registers,
+                                 splits them into their bf16 terms and frees the stage at once,
+                                 so only its stores wait for the A buffer (K of one block, at
+                                 most 3 chunks of 8 nodes a thread for BF16, 2 for BF16X3;
+                                 others take the plain path) */
     int32_t tail_free;        /* 1: no guard on the last e tile; only accepted when an
                                  assumption "E mod m = 0" with m a multiple of tile_e holds */
     int32_t stages;           /* u tiles in flight in shared memory (TMA ring depth), >= 1 */

@@ -1152,7 +1152,7 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         // elems_per_thread = K-block width (16, 32 or 64 bf16 = 32/64/128-byte swizzle rows),
         // K padded to a multiple of it; 1 = the widest block that divides K padded to 16
         const int kbw = v->elems_per_thread;
-        if (v->tile_e != 128 || !(v->prefetch_smem == 1 || (v->prefetch_smem == 2 && v->precision == LC_PREC_BF16)) ||
+        if (v->tile_e != 128 || !(v->prefetch_smem == 1 || v->prefetch_smem == 2) ||
             !(kbw == 1 || kbw == 16 || kbw == 32 || kbw == 64) ||
             v->unroll < 1 || v->unroll > 4)
             return LC_ERR_INVALID_VARIANT;
@@ -1171,12 +1171,13 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         t.N = N;
         t.F = F;
         t.E = E;
+        t.Kt = (N + 15) / 16 * 16;
         if (kbw == 1) {
-            t.Kp = (N + 15) / 16 * 16;
+            t.Kp = t.Kt;
             t.KB = t.Kp % 64 == 0 ? 64 : (t.Kp % 32 == 0 ? 32 : 16);
         } else {
             t.KB = kbw;
-            t.Kp = (N + kbw - 1) / kbw * kbw;
+            t.Kp = (t.Kt + kbw - 1) / kbw * kbw;
         }
         t.nkb = t.Kp / t.KB;
         if (t.nkb > 16)
@@ -1205,6 +1206,12 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
                 q.Np = np8;  // one accumulator region: the narrowest padding (smaller B, fewer columns)
             else
                 q.Np = cbp(np16) <= 256 ? np16 : np8;
+            // three terms, whole-tile epilogue (node-major, or element-major stores of whole
+            // tiles): the operators packed without padding where that narrows the MMAs, whose
+            // time grows with their N (the epilogue chunks may then cross an operator's end)
+            if (NT == 3 && !geo && (node || t.store_quarters == 4) && N >= 8 && cbp(N) < cbp(q.Np) &&
+                (!want_stack || 2 * cbp(N) <= 256))
+                q.Np = N;
             q.chunk = q.Np % 16 == 0 && !geo ? 16 : 8;
             q.CB = G * q.Np;
             q.CBp = cbp(q.Np);
@@ -1217,7 +1224,7 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
             while (q.tmem_cols < (q.stack ? 2 : 1) * q.CBp)
                 q.tmem_cols *= 2;
             q.a_tmem = a_tm;
-            q.a_cols = a_tm ? NT * ((N + 15) / 16 * 16) / 2 : 0;
+            q.a_cols = a_tm ? NT * q.Kt / 2 : 0;
             const int need = 2 * q.tmem_cols + q.abufs * q.a_cols;
             if (need > 512)
                 return false;
@@ -1277,6 +1284,9 @@ static lc_status resolve(const Kernel &K, long long E, int N, int F, const lc_va
         const int G = t.G;
         t.nblocks = (F + G - 1) / G;
         t.ntiles = (E + 127) / 128;
+        // element-major whole-tile slots: the store warp issues the bulk stores and waits for
+        // their reads, so the epilogue warps go on to the next tile at once
+        t.store_warp = !node && t.store_quarters == 4;
         t.bulk_u = node ? (E % 4 == 0) : 1;
         t.bulk_store = !node && ((E * (long long)N) % 4 == 0);
         long long work = t.ntiles * t.nblocks;
@@ -1737,12 +1747,12 @@ lc_status lc_variant_plan(const lc_kernel *kh, int64_t E, int32_t N, int32_t F, 
         const TcArgs &t = r.tc;
         const int nt = r.precision == LC_PREC_BF16X3 ? 3 : 1;
         q.grid = r.tc_grid;
-        q.threads = 128 * (t.threads_per_row + t.conv_threads_per_row) + 64;
+        q.threads = tc_threads(t);
         q.smem_bytes = (int32_t)t.smem_bytes;
         q.tiles = t.ntiles;
         q.column_blocks = t.nblocks;
         q.ops_per_block = t.G;
-        q.k_mma = (N + 15) / 16 * 16;
+        q.k_mma = t.Kt;
         q.k_block = t.KB;
         q.cols_per_op = t.Np;
         q.mma_n = t.CBp;
@@ -1851,6 +1861,8 @@ lc_status lc_variant_default(const lc_kernel *kh, int64_t E, int32_t N, int32_t 
         d.tile_e = 128;
         d.split_i = 0;
         d.unroll = 4;
+        // BF16X3: three epilogue and conversion threads per row with the stage released early
+        // (element-major), two with two stages (node-major): the fastest measured at N = 35
         // 64-wide K-blocks first: a tcgen05.mma reading 128-byte swizzled rows costs the
         // fewest cycles; then the narrowest blocks that cover K (least shared memory).
         // BF16X3: the A terms in shared memory first (the stacked order), one stage first (two
@@ -1859,9 +1871,14 @@ lc_status lc_variant_default(const lc_kernel *kh, int64_t E, int32_t N, int32_t 
         // measured slower than the K-split FP32 kernel there: shared-memory A only)
         const bool x3 = precision == LC_PREC_BF16X3;
         lc_status st = LC_ERR_INVALID_VARIANT;
+        const bool x3node = x3 && layout == LC_LAYOUT_NODE_MAJOR;
+        if (x3) {
+            d.unroll = x3node ? 2 : 3;
+            d.prefetch_smem = x3node ? 1 : 2;
+        }
         for (int aop : {x3 ? 1 : 0})
             for (int kbw : {64, 1})
-                for (int stg : {x3 ? 1 : 2, x3 ? 2 : 3, x3 ? 3 : 1}) {
+                for (int stg : {x3 && !x3node ? 1 : 2, x3 && !x3node ? 2 : 3, 1}) {
                     if (st == LC_OK)
                         break;
                     d.a_operand = aop;
@@ -2506,10 +2523,10 @@ static lc_status grouped_plan_tc(const Kernel &K, const lc_variant *v, const lc_
         T.P.g[tg] = t;
         T.tc_groups.push_back(gi);
         T.smem = std::max(T.smem, (size_t)t.smem_bytes);
-        T.threads = 128 * (t.threads_per_row + t.conv_threads_per_row) + 64;
+        T.threads = tc_threads(t);
         // per tile: its HBM bytes at the SM's share of the copy rate (0.6 efficiency), or the
         // MMA chain at about 300 cycles an instruction, plus a fixed pipeline cost
-        const int kn = (G.N + 15) / 16 * 16;
+        const int kn = t.Kt;
         const int mmas = (T.nterms == 1 ? 1 : (t.stack ? 5 : 6)) * (kn / 16);
         for (int b = 0; b < t.nblocks; ++b) {
             const int gb = std::min(t.G, G.F - b * t.G);

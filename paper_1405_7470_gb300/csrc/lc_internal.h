@@ -136,6 +136,7 @@ struct TcArgs {
     int chunk;      // epilogue chunk: 16 columns when Np is a multiple of 16, else 8
     int CB, CBp;    // columns per block (G * Np) and the MMA N (CB rounded up to 16)
     int Kp, KB, nkb;  // K padded to the block width, K-block width (16/32/64 -> 32/64/128-byte swizzle), blocks
+    int Kt;         // K the MMAs read: N rounded up to 16 (zeros past N)
     int stack;      // BF16X3 with two B terms stacked along N (2 * CBp <= 256): 5 MMAs per K step, not 6
     int tmem_cols;  // columns per accumulator (power of two >= CBp, or >= 2 * CBp when stacked)
     int a_tmem;     // 1: the A terms live in tensor memory after the two accumulators
@@ -148,6 +149,7 @@ struct TcArgs {
     int abufs;      // A-operand buffers (1 or 2)
     int obufs;      // element-major output staging slots of one operator-tile (1 to 4)
     int store_quarters;  // element-major: TMEM lane quarters (32 rows each) per bulk store: 1, 2 or 4
+    int store_warp;      // 1: whole-tile element-major slots are written out by the CTA's store warp
     long long ntiles;
     int bulk_u, bulk_store;
     unsigned int *err;
@@ -155,6 +157,10 @@ struct TcArgs {
 };
 
 lc_status tc_launch(const TcArgs &a, int layout, int nterms, int grid, cudaStream_t s);
+
+// Threads of a tensor-core CTA: 4 x (epilogue + conversion threads per tile row) warps, then
+// the producer, MMA and store warps.
+static inline int tc_threads(const TcArgs &a) { return 128 * (a.threads_per_row + a.conv_threads_per_row) + 96; }
 
 // Grouped tensor-core launch: per-group plans and the per-CTA unit table.
 static constexpr int kTcMaxGroups = 16;

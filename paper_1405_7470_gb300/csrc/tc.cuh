@@ -28,7 +28,9 @@
 //                  major through shared-memory slots and bulk stores (every operator
 //                  of the tile per slot, or one operator per slot in store groups of
 //                  lane quarters), node-major straight from registers (coalesced
-//                  along e).
+//                  along e);
+//   store warp     issues the bulk stores of the whole-tile slots and hands each slot
+//                  back once the copies have read it (idle in the other layouts).
 // Setup: the MMA warp allocates the accumulators; all threads split D into the
 // B-operand terms, resident for the CTA's lifetime.
 // Every mbarrier wait is bounded in time; on a timeout the kernel sets the device
@@ -272,7 +274,10 @@ __device__ __forceinline__ void tc_body(const TcArgs &a, const int blk, const lo
     const int Np = a.Np;  // accumulator columns per operator (N rounded up to 16)
     // K columns the MMAs read: N rounded up to the 16 of one instruction.  A K-block
     // wider than that keeps its last columns unread, so nothing writes them.
-    const int Kn = (N + 15) & ~15;
+    const int Kn = a.Kt;
+    // K columns that hold nodes (N rounded up to a chunk of 8, at most Kn): the conversion
+    // writes these; the chunks beyond, up to Kn, stay zero from the set-up (A in shared memory)
+    const int Kz8 = (kATmem && a.a_tmem) ? Kn : min(Kn, (N + 7) & ~7);
     const int W = 2 * KB;  // bytes per row of a K-block
     const long long E = a.E;
     const int S = a.stages, NA = a.abufs;
@@ -297,8 +302,10 @@ __device__ __forceinline__ void tc_body(const TcArgs &a, const int blk, const lo
     volatile int *abort_flag = reinterpret_cast<volatile int *>(bar + 11);
     // A buffers are handed over per K-block: a_full/a_empty[ab * kTcMaxKB + kb]
     uint64_t *a_full = bar + 16, *a_empty = bar + 16 + 2 * kTcMaxKB;
+    // element-major whole-tile staging slots handed between the epilogue and the store warp
+    uint64_t *slot_full = bar + 16 + 4 * kTcMaxKB, *slot_empty = slot_full + 4;
 
-    const int prod_warp = NW + NC, mma_warp = NW + NC + 1;
+    const int prod_warp = NW + NC, mma_warp = NW + NC + 1, store_warp = NW + NC + 2;
     if (warp == mma_warp)
         tmem_alloc(tmem_holder, (uint32_t)a.tmem_alloc);
     if (tid == 0) {
@@ -313,6 +320,10 @@ __device__ __forceinline__ void tc_body(const TcArgs &a, const int blk, const lo
         for (int q = 0; q < 2 * kTcMaxKB; ++q) {
             mbar_init(&a_full[q], NC);
             mbar_init(&a_empty[q], 1);
+        }
+        for (int q = 0; q < 4; ++q) {
+            mbar_init(&slot_full[q], NW);
+            mbar_init(&slot_empty[q], 1);
         }
         *abort_flag = 0;
         fence_mbar_init();
@@ -337,6 +348,22 @@ __device__ __forceinline__ void tc_body(const TcArgs &a, const int blk, const lo
 #pragma unroll
             for (int tt = 0; tt < NT; ++tt)
                 *reinterpret_cast<uint4 *>(smem + (uint32_t)kb * bkb + swz_off(tt * CBp + n, ch, W)) = t[tt];
+        }
+        // A chunks past the last node (all zeros in every tile) are written once here; the
+        // conversion warps skip them
+        if (!(kATmem && a.a_tmem)) {
+            const int zc = Kn / 8 - Kz8 / 8;  // zero chunks per row
+            for (int idx = tid; idx < NA * NT * TE * zc; idx += blockDim.x) {
+                int rest = idx;
+                const int c8 = Kz8 / 8 + rest % zc;
+                rest /= zc;
+                const int rw = rest % TE;
+                rest /= TE;
+                const int tt = rest % NT, ab = rest / NT;
+                const int kb = (c8 * 8) / KB, ch = ((c8 * 8) % KB) / 8;
+                *reinterpret_cast<uint4 *>(smem + offA + (uint32_t)ab * bufA + (uint32_t)tt * termA +
+                                           (uint32_t)kb * TE * W + swz_off(rw, ch, W)) = make_uint4(0u, 0u, 0u, 0u);
+            }
         }
     }
     fence_async_smem();
@@ -472,6 +499,52 @@ __device__ __forceinline__ void tc_body(const TcArgs &a, const int blk, const lo
             if (*abort_flag)
                 break;
         }
+    } else if (warp == store_warp) {
+        // ---------------- store warp: element-major whole-tile slots -> out.  Once every
+        // epilogue warp has staged tile k into slot k % R, one lane issues the bulk stores of
+        // the block's operators, waits until they have read the slot and hands it back, so
+        // the epilogue warps never wait on the bulk-copy engine themselves.
+        if (!NODE && a.store_quarters == 4) {
+            const int R = a.obufs;
+            int k = 0;
+            bool ok = true;
+            for (long long t = my_first; t < a.ntiles; t += my_step, ++k) {
+                const int s = k % R;
+                if (!mbar_wait(&slot_full[s], (uint32_t)(k / R) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                const long long e0 = t * TE;
+                const int total = (int)min((long long)TE, E - e0) * N;
+                const float *ost = ost0 + (size_t)s * G * TE * N;
+                if (a.bulk_store && ((total * 4) & 15) == 0) {
+                    if (lane == 0) {
+                        for (int g = 0; g < Gb; ++g)
+                            bulk_s2g(a.out + ((size_t)(f0 + g) * E + e0) * N, ost + (size_t)g * TE * N,
+                                     (uint32_t)total * 4u);
+                        bulk_commit();
+                        bulk_wait_read0();
+                    }
+                } else {
+                    // unaligned tail: plain copy
+                    for (int g = 0; g < Gb; ++g) {
+                        const float *src = ost + (size_t)g * TE * N;
+                        float *dst = a.out + ((size_t)(f0 + g) * E + e0) * N;
+                        for (int idx = lane; idx < total; idx += 32)
+                            dst[idx] = src[idx];
+                    }
+                }
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(&slot_empty[s]);
+                if (*abort_flag)
+                    break;
+            }
+            if (lane == 0)
+                bulk_wait0();
+            if (!ok && lane == 0)
+                fail();
+        }
     } else if (warp >= NW) {
         // ---------------- conversion warps: fp32 u tile -> bf16 A-operand terms, K-block by K-block
         // A thread converts K chunks c8 (8 values of j) of its tile row: within K-block kb the
@@ -479,17 +552,16 @@ __device__ __forceinline__ void tc_body(const TcArgs &a, const int blk, const lo
         // swizzle) or to tensor memory (tcgen05.st into this warp's lane quarter, warp-uniform
         // loops; rows past the tile and nodes past N are zeros).
         // Early release (descriptor prefetch_smem = 2): when K is one block and a thread has at
-        // most 3 chunks, it loads all of them into registers first and hands the u stage back to
-        // the producer at once, so the next tile's bulk copy overlaps this tile's conversion and
-        // MMAs (it helps one-stage plans; beside a long MMA chain the extra shared-memory
-        // traffic during the MMAs can cost more than it saves).
-        constexpr int kMaxEarly = 3;
+        // most kMaxEarly chunks, it loads them, splits them into their terms in registers and
+        // hands the u stage back to the producer at once, so the next tile's bulk copy overlaps
+        // this tile's conversion and MMAs, and only the stores of the terms wait for the A
+        // buffer (threads with more chunks take the plain path).
+        // chunks a thread may hold: three (BF16, one term each) or two (three terms each)
+        constexpr int kMaxEarly = NT == 1 ? 3 : 2;
         int k = 0;
         bool ok = true;
-        const int nch8 = Kn / 8;
-        // (BF16 only: holding 3 x 8 values across the three-term split would spill registers)
-        const int my_chunks =
-            (NT == 1 && nkb == 1 && a.early_release) ? (nch8 - part + Hc - 1) / Hc : kMaxEarly + 1;
+        const int nch8 = Kz8 / 8;
+        const int my_chunks = (nkb == 1 && a.early_release) ? (nch8 - part + Hc - 1) / Hc : kMaxEarly + 1;
         const uint32_t lane_q = (uint32_t)(32 * (warp & 3)) << 16;
         for (long long t = my_first; t < a.ntiles && ok; t += my_step, ++k) {
             const int s = k % S, ab = k % NA;
@@ -527,9 +599,8 @@ __device__ __forceinline__ void tc_body(const TcArgs &a, const int blk, const lo
                 }
             };
             // chunk c8 -> the A terms
-            auto put = [&](int c8, const float *x) {
-                uint4 tt4[3];
-                split8<NT>(x, tt4);
+            // the NT terms of chunk c8 -> the A buffer
+            auto put_terms = [&](int c8, const uint4 *tt4) {
                 if (kATmem && a.a_tmem) {
 #pragma unroll
                     for (int tt = 0; tt < NT; ++tt)
@@ -541,6 +612,11 @@ __device__ __forceinline__ void tc_body(const TcArgs &a, const int blk, const lo
                     for (int tt = 0; tt < NT; ++tt)
                         *reinterpret_cast<uint4 *>(Ab + off + tt * termA) = tt4[tt];
                 }
+            };
+            auto put = [&](int c8, const float *x) {
+                uint4 tt4[3];
+                split8<NT>(x, tt4);
+                put_terms(c8, tt4);
             };
             // block kb written: make it visible to the tensor core and hand it to the MMA warp
             auto block_done = [&](int kb) {
@@ -555,12 +631,22 @@ __device__ __forceinline__ void tc_body(const TcArgs &a, const int blk, const lo
                     mbar_arrive(&a_full[ab * kTcMaxKB + kb]);
             };
             bool released = false;
-            if (NT == 1 && from_stage && my_chunks <= kMaxEarly) {
-                float xv[kMaxEarly][8];
+            if (from_stage && my_chunks <= kMaxEarly) {
+                // the chunks are split into their terms before the A buffer is free, so that
+                // only the stores of the terms wait for the MMAs of the previous tile
+                uint4 tv[kMaxEarly][3];
 #pragma unroll
-                for (int m = 0; m < kMaxEarly; ++m)
-                    if (m < my_chunks)
-                        load_chunk(part + Hc * m, xv[m]);
+                for (int m = 0; m < kMaxEarly; ++m) {
+                    const int c8 = part + Hc * m;
+                    float x[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        x[q] = (m < my_chunks && rowv && c8 * 8 + q < N) ? src_s[(c8 * 8 + q) * JS] : 0.f;
+                    split8<NT>(x, tv[m]);
+                }
+                // the loads are complete before the stage is handed back (no load may be
+                // deferred past the arrive to the point where the values are used)
+                __threadfence_block();
                 __syncwarp();
                 if (lane == 0)
                     mbar_arrive(&u_empty[s]);  // the stage is free for the next bulk copy
@@ -573,7 +659,7 @@ __device__ __forceinline__ void tc_body(const TcArgs &a, const int blk, const lo
 #pragma unroll
                 for (int m = 0; m < kMaxEarly; ++m)
                     if (m < my_chunks)
-                        put(part + Hc * m, xv[m]);
+                        put_terms(part + Hc * m, tv[m]);
                 block_done(0);
             } else {
                 const int full8 = rowv ? N / 8 : 0;  // chunks with all 8 values inside the row
@@ -583,7 +669,7 @@ __device__ __forceinline__ void tc_body(const TcArgs &a, const int blk, const lo
                         break;
                     }
                     tc_fence_after();
-                    const int c8_lo = kb * KB / 8, c8_hi = min(Kn, (kb + 1) * KB) / 8;
+                    const int c8_lo = kb * KB / 8, c8_hi = min(Kz8, (kb + 1) * KB) / 8;
                     if (kATmem && a.a_tmem) {
                         // tcgen05.st is warp-collective: every lane runs the same chunks (the
                         // trip count depends on the warp's share only), rows past the tile are
@@ -658,6 +744,9 @@ __device__ __forceinline__ void tc_body(const TcArgs &a, const int blk, const lo
         const bool stack = NT == 3 && a.stack;
         // Load, sum and store the chunks of columns [c_begin, c_end) of this warp's lane
         // quarter; element-major values go to stage + ((operator - f_stage) * TE + row) * N.
+        // operators packed without padding (Np = N, N not a multiple of the chunk): a chunk of
+        // columns c = f N + i may run into the next operator
+        const bool packed = Np == N && N % CW != 0;
         auto drain = [&](int c_begin, int c_end, const uint32_t tbase, float *stage, int f_stage, long long e0,
                          int TEv) {
             constexpr int EB = EpiBatch<NT, CW>::value;
@@ -682,6 +771,35 @@ __device__ __forceinline__ void tc_body(const TcArgs &a, const int blk, const lo
 #pragma unroll
                         for (int qq = 0; qq < CW; ++qq)
                             r[k4][qq] = __float_as_uint(__uint_as_float(r[k4][qq]) + __uint_as_float(r2[k4][qq]));
+                    }
+                    if (packed) {
+                        if (NODE) {
+                            if (row < TEv) {
+                                float *o = a.out + ((size_t)f0 * N + cc) * E + e0 + row;  // (f0 + f) N + i = f0 N + c
+#pragma unroll
+                                for (int qq = 0; qq < CW; ++qq) {
+                                    if (cc + qq < c_end)
+                                        *o = __uint_as_float(r[k4][qq]);
+                                    o += E;
+                                }
+                            }
+                        } else {
+                            // (f, row, i) at (f TE + row) N + i: past the operator's last node the
+                            // next operator's row starts (TE - 1) N further on
+                            float *o = stage + ((fl - f_stage) * TE + row) * N + i0;
+                            const int jump = (TE - 1) * N, rest = N - i0;
+                            if (rest >= CW && cc + CW <= c_end) {
+#pragma unroll
+                                for (int qq = 0; qq < CW; ++qq)  // the chunk inside one operator
+                                    o[qq] = __uint_as_float(r[k4][qq]);
+                            } else {
+#pragma unroll
+                                for (int qq = 0; qq < CW; ++qq)
+                                    if (cc + qq < c_end)
+                                        o[qq + (qq >= rest ? jump : 0)] = __uint_as_float(r[k4][qq]);
+                            }
+                        }
+                        continue;
                     }
                     if (NODE) {
                         if (row < TEv) {
@@ -795,19 +913,15 @@ __device__ __forceinline__ void tc_body(const TcArgs &a, const int blk, const lo
                 const int TEv = (int)min((long long)TE, E - e0);
                 const bool got = mbar_wait(&acc_full[b], (uint32_t)((k >> 1) & 1));
                 float *ost = ost0 + (size_t)(k % R) * G * TE * N;
-                if (NODE) {
-                    if (!got || *abort_flag) {  // node-major warps meet at no named barrier
-                        ok = got;
-                        break;
-                    }
-                } else {
-                    if (tid == 0)
-                        bulk_wait_read(R - 1);  // the stores that last read this slot are done reading
-                    // the epilogue warps leave together (they meet at named barriers)
-                    if (bar_or(1, NWT, !got || *abort_flag)) {
-                        ok = got;
-                        break;
-                    }
+                // every warp goes its own way (no named barrier; every wait is bounded)
+                if (!got || *abort_flag) {
+                    ok = got;
+                    break;
+                }
+                // element-major: the store warp has finished reading this slot
+                if (!NODE && !mbar_wait(&slot_empty[k % R], ((uint32_t)(k / R) & 1u) ^ 1u)) {
+                    ok = false;
+                    break;
                 }
                 tc_fence_after();
                 const uint32_t tbase = tmem_base + (uint32_t)b * a.tmem_cols + ((uint32_t)(q * 32) << 16);
@@ -819,29 +933,13 @@ __device__ __forceinline__ void tc_body(const TcArgs &a, const int blk, const lo
                 }
                 release_acc(b);
                 if (!NODE) {
+                    // this warp's staged values, ordered before the store warp's bulk copies
                     fence_async_smem();
-                    asm volatile("bar.sync 1, %0;" ::"r"(NWT) : "memory");
-                    const int total = TEv * N;
-                    if (a.bulk_store && ((total * 4) & 15) == 0) {
-                        if (tid == 0) {
-                            for (int g = 0; g < Gb; ++g)
-                                bulk_s2g(a.out + ((size_t)(f0 + g) * E + e0) * N, ost + (size_t)g * TE * N,
-                                         (uint32_t)total * 4u);
-                            bulk_commit();
-                        }
-                    } else {
-                        // unaligned tail: plain copy; the next barrier on this slot orders reuse
-                        for (int g = 0; g < Gb; ++g) {
-                            const float *src = ost + (size_t)g * TE * N;
-                            float *dst = a.out + ((size_t)(f0 + g) * E + e0) * N;
-                            for (int idx = tid; idx < total; idx += NWT)
-                                dst[idx] = src[idx];
-                        }
-                    }
+                    __syncwarp();
+                    if (lane == 0)
+                        mbar_arrive(&slot_full[k % R]);
                 }
             }
-            if (!NODE && tid == 0)
-                bulk_wait0();
         } else {
             // ---- element-major, one operator per slot, store groups of SQ quarters
             const int gq = q / SQ, qin = q % SQ;  // store group, quarter within it
@@ -920,7 +1018,7 @@ __device__ __forceinline__ void tc_body(const TcArgs &a, const int blk, const lo
 }
 
 template <int LAYOUT, int NT, int CW, int FG, bool ATM = (NT == 1)>
-__global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_constant__ TcArgs a)
+__global__ void __launch_bounds__(864, 1) tc_contract_kernel(const __grid_constant__ TcArgs a)
 {
     tc_body<LAYOUT, NT, CW, FG, ATM>(a, (int)(blockIdx.x % a.nblocks), blockIdx.x / a.nblocks,
                                      gridDim.x / a.nblocks);
@@ -929,7 +1027,7 @@ __global__ void __launch_bounds__(832, 1) tc_contract_kernel(const __grid_consta
 // Grouped launch: CTA b runs unit P.map[b] = {group, column block, first tile, tile step} of
 // the group's own plan P.g[group] (one unit per CTA, no group switching inside a CTA).
 template <int LAYOUT, int NT, bool ATM = (NT == 1)>
-__global__ void __launch_bounds__(832, 1) tc_grouped_kernel(const __grid_constant__ TcGroupedParams P)
+__global__ void __launch_bounds__(864, 1) tc_grouped_kernel(const __grid_constant__ TcGroupedParams P)
 {
     const int4 m = P.map[blockIdx.x];
     tc_body<LAYOUT, NT, 8, 0, ATM>(P.g[m.x], m.y, m.z, m.w);
@@ -943,7 +1041,7 @@ static inline lc_status tc_launch_fn(void *fn, const TcArgs &a, int grid, cudaSt
         return cuda_fail(e);
     TcArgs args = a;
     void *params[] = {&args};
-    e = cudaLaunchKernel(fn, dim3(grid), dim3(128 * (a.threads_per_row + a.conv_threads_per_row) + 64), params,
+    e = cudaLaunchKernel(fn, dim3(grid), dim3(tc_threads(a)), params,
                          a.smem_bytes, s);
     if (e != cudaSuccess)
         return cuda_fail(e);

@@ -71,8 +71,6 @@ static std::vector<lc_variant> candidates(int N, int F, int layout, int precisio
         const bool node = layout == LC_LAYOUT_NODE_MAJOR;
         // stage ring depth 1, 2, 3, and one stage released early (prefetch_smem = 2)
         for (int st : {1, 2, 3, 0}) {
-            if (st == 0 && precision != LC_PREC_BF16)
-                continue;  // early release of the stage: BF16 only
             for (int tpr : {2, 3, 4})
                 for (int g : {0, 1})
                     for (int kbw : {1, 64})

@@ -160,9 +160,10 @@ def test_variant_plan_reports_the_resolved_launch(lib):
     p = lc.variant_plan(k, 1 << 21, 35, 3, v)
     assert p["tiles"] == (1 << 21) // 128 and p["column_blocks"] == 1 and p["ops_per_block"] == 3
     assert p["k_mma"] == 48 and p["k_block"] == 64
-    # N = 35 pads to 40 columns per operator so that the D terms stack: 5 MMAs per K step
-    assert p["cols_per_op"] == 40 and p["mma_n"] == 128 and p["stacked"] == 1 and p["mma_per_tile"] == 15
-    assert p["threads"] == 128 * (4 + 2) + 64 and p["store_rows"] == 128
+    # the three operators packed without padding: 105 columns, MMA N 112, the D terms stacked
+    # (MMA N 224): 5 MMAs per K step
+    assert p["cols_per_op"] == 35 and p["mma_n"] == 112 and p["stacked"] == 1 and p["mma_per_tile"] == 15
+    assert p["threads"] == 128 * (4 + 2) + 96 and p["store_rows"] == 128
     assert 0 < p["smem_bytes"] <= 232448 and p["a_in_tmem"] == 0 and p["tmem_cols"] == 512
     # BF16 with the A terms in tensor memory: two accumulators of 128 columns and two A
     # buffers of 24 columns; no A in shared memory
@@ -184,6 +185,21 @@ def test_variant_plan_reports_the_resolved_launch(lib):
     v.unroll = 9
     with pytest.raises(lc.LcError):
         lc.variant_plan(k, 1 << 21, 35, 3, v)
+
+
+def test_early_release_and_store_warp_plan(lib):
+    """prefetch_smem = 2 (early release of the u stage) is a valid tensor-core descriptor for
+    both reduced-precision paths; every tensor-core CTA carries the producer, MMA and store
+    warps beside its epilogue and conversion warps."""
+    k = lc.Kernel()
+    for prec in ("bf16", "bf16x3"):
+        v = lc.Variant(engine="tcgen05", layout="elem", precision=prec, tile_e=128, elems_per_thread=64,
+                       split_i=0, unroll=4, prefetch_smem=2, stages=1, store_rows=128)
+        assert lib.lc_variant_validate(k.handle, 1 << 21, 35, 3, ctypes.byref(v)) == 0
+        assert lc.variant_plan(k, 1 << 21, 35, 3, v)["threads"] == 128 * (4 + 2) + 96
+    s = lc.variant_default(k, 4096, 35, 3, "elem", "fp32")
+    s.prefetch_smem = 2
+    assert lib.lc_variant_validate(k.handle, 4096, 35, 3, ctypes.byref(s)) != 0
 
 
 def test_max_ctas_bounds_the_grid(lib):

@@ -117,3 +117,4 @@ def test_full_size_sampled(lc):
     got = out.index_select(1, torch.from_numpy(rows).cuda()).cpu().numpy().astype(np.float64)
     ref = oracle.contract_geo_rows(D, u, r, rows)
     assert oracle.rel_fro_error(got, ref) <= 1e-6
+

@@ -127,3 +127,39 @@ def test_simt_descriptor_grid_many_tiles(lc, layout, prec):
             ran += 1
     assert ran >= 20, ran
 
+
+
+
+EARLY_SHAPES = [(3000 + 77, 35, 3), (1500 + 33, 20, 2), (1200 + 7, 17, 3), (900 + 1, 48, 1), (2000 + 5, 84, 4)]
+
+
+@pytest.mark.parametrize("layout", ["elem", "node"])
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
+def test_tc_early_release_many_tiles(lc, layout, prec):
+    """prefetch_smem = 2: each converting thread takes its chunks of the u tile into registers
+    and hands the stage back before converting (one K-block, at most three chunks a thread;
+    otherwise the plain path runs), bit-exact on integer inputs with every CTA walking several
+    tiles; chunks past the last node are the zeros written at set-up."""
+    kernel = lc.Kernel()
+    ran = 0
+    for E, N, F in EARLY_SHAPES:
+        D, u = synth.integer_operands(E, N, F, seed=E + 2 * N + F)
+        uu = synth.to_node_major(u) if layout == "node" else u
+        ref = oracle.contract(D, uu, layout)
+        combos = itertools.product((1, 2), (1, 64), ((128, 2), (32, 1), (0, 0)), (0, 1))
+        for k, (stages, kbw, (rows, ob), split) in enumerate(combos):
+            tpr = 1 + k % 4
+            if layout == "node" and (rows, ob) != (0, 0):
+                continue
+            v = lc.Variant(engine="tcgen05", layout=layout, precision=prec, tile_e=128, elems_per_thread=kbw,
+                           split_i=split, unroll=tpr, prefetch_smem=2, stages=stages, out_buffers=ob,
+                           store_rows=rows)
+            if lc.variant_validate(kernel, E, N, F, v) != 0:
+                continue
+            v.max_ctas = 2 * lc.variant_plan(kernel, E, N, F, v)["column_blocks"]
+            assert tiles_per_cta(lc, kernel, E, N, F, v) >= 4
+            got = run(lc, kernel, v, D, uu, layout)
+            assert np.array_equal(got, ref), (E, N, F, stages, kbw, rows, ob, split, tpr)
+            ran += 1
+    assert ran >= 30, ran
+

@@ -239,3 +239,25 @@ def test_bf16x3_a_in_tensor_memory(lc, layout, E, N, F):
     # the default for N = 120 is the faster K-split FP32 kernel (FP32 error, below the bound)
     v = lc.variant_default(kernel, 300, 120, 3, layout, "bf16x3")
     assert lc.variant_dict(v)["engine"] == "ksplit"
+
+
+
+@pytest.mark.parametrize("layout", ["elem", "node"])
+def test_three_term_early_release_random(lc, layout):
+    """BF16X3 with early release of the stage (prefetch_smem = 2): random inputs within the
+    per-output bound of the six-product target and 1e-6 of the exact result."""
+    kernel = lc.Kernel()
+    for si, (E, N, F) in enumerate(((1000, 35, 3), (517, 20, 1), (300, 17, 2), (4099, 10, 3))):
+        D, u = synth.operands(E, N, F, np.float32, seed=800 + si, scale_exp=3.0 if si % 2 else None)
+        uu = synth.to_node_major(u) if layout == "node" else u
+        v = lc.Variant(engine="tcgen05", layout=layout, precision="bf16x3", tile_e=128, elems_per_thread=64,
+                       split_i=0, unroll=4, prefetch_smem=2, stages=1)
+        assert lc.variant_validate(kernel, E, N, F, v) == 0
+        got = run(lc, kernel, v, D, uu, layout)
+        Ds, us = oracle.bf16_split3(D), oracle.bf16_split3(uu)
+        bound = accum_bound(np.abs(Ds[0]) + np.abs(Ds[1]) + np.abs(Ds[2]),
+                            np.abs(us[0]) + np.abs(us[1]) + np.abs(us[2]), layout, "bf16x3")
+        target = oracle.contract_bf16x3(D, uu, layout)
+        assert np.all(np.abs(got - target) <= bound), (E, N, F)
+        assert oracle.rel_fro_error(got, oracle.contract(D, uu, layout)) <= 1e-6, (E, N, F)
+
