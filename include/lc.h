@@ -482,7 +482,8 @@ lc_status lc_error_norm(const void *out_dev, int32_t out_dtype, const double *re
 
 /*
  * The candidate descriptors for a problem (the autotuner's search space), valid ones
- * only, in a fixed order.  Writes min(count, cap) entries; *count = the number of
+ * only, in a fixed order; descriptors whose plan (lc_variant_plan) has fewer than two
+ * warps per CTA are left out (they remain valid for lc_contract).  Writes min(count, cap) entries; *count = the number of
  * candidates.  Errors: LC_ERR_INVALID_ARGUMENT, LC_ERR_BUFFER_TOO_SMALL (cap < count).
  */
 lc_status lc_enumerate_variants(const lc_kernel *k, int64_t E, int32_t N, int32_t F, int32_t layout,

@@ -118,6 +118,13 @@ lc_status lc_enumerate_variants(const lc_kernel *k, int64_t E, int32_t N, int32_
     for (const lc_variant &v : cand) {
         if (lc_variant_validate(k, E, N, F, &v) != LC_OK)
             continue;
+        // leave out plans that shrink to one warp per CTA (the column block split until
+        // the tile's operators fit shared memory): one warp then holds a whole SM
+        lc_plan p;
+        memset(&p, 0, sizeof p);
+        p.struct_size = sizeof(lc_plan);
+        if (lc_variant_plan(k, E, N, F, &v, &p) != LC_OK || p.threads < 64)
+            continue;
         // keep one copy of descriptors that resolve to the same launch (e.g. G = F)
         bool dup = false;
         for (int q = 0; q < std::min(n, cap); ++q)

@@ -243,6 +243,23 @@ def test_variant_features_and_pick_arguments(lib):
     assert lib.lc_pick_variant(kernel.handle, 1000, 35, 3, 0, 3, 16, 16, 8, ctypes.byref(v), None, None) == 6
 
 
+def test_enumeration_leaves_out_one_warp_plans(lib):
+    """Large N with one operator (E=43715, N=145): a SIMT descriptor whose tile does not fit
+    shared memory resolves to many column blocks of one warp each; such plans stay valid but
+    are not candidates (one of them ran 12x slower than the best in the autotuner)."""
+    kernel = lc.Kernel("{ [e,i,j]: 0<=e<E and 0<=i,j<N }", "out[e,i] = sum(j, D[i,j]*u[e,j])")
+    E, N, F = 43715, 145, 1
+    cands = lc.enumerate_variants(kernel, E, N, F, "elem", "bf16")
+    assert cands
+    for v in cands:
+        assert lc.variant_plan(kernel, E, N, F, v)["threads"] >= 64
+    v = lc.Variant(engine="simt", tile_e=128, elems_per_thread=8, split_i=4, unroll=1, prefetch_smem=1, stages=2,
+                   ctas_per_sm=2)
+    assert lc.variant_validate(kernel, E, N, F, v) == 0
+    assert lc.variant_plan(kernel, E, N, F, v)["threads"] < 64
+    assert lc.variant_dict(v) not in [lc.variant_dict(c) for c in cands]
+
+
 GEO_DOM = "{ [d,f,e,i,j]: 0<=d<F and 0<=f<F and 0<=e<E and 0<=i,j<N }"
 
 

@@ -2,7 +2,7 @@
 
 A seeded set of shapes (N ~ U{4..165}, E = floor(2^U(14, 19)), F ~ U{1..4}, every
 precision path and layout) is autotuned exhaustively by the library; a network is trained
-on the first 200 shapes' timings by the library's own kernels; on the 40 held-out shapes
+on the first 400 shapes' timings by the library's own kernels; on the 40 held-out shapes
 the library's lc_pick_variant chooses a descriptor, and the pick, the autotuned best and
 the default descriptor (lc_variant_default: the fixed choice the method makes without a
 model) are re-timed together.  The network's geo-mean regret must be below the default's.
@@ -28,11 +28,11 @@ def lc():
 
 def test_learned_pick_beats_default_on_held_out_shapes(lc):
     from paper_1405_7470_gb300 import picker
-    seed, n_train, n_test = 1, 200, 40
+    seed, n_train, n_test = 1, 400, 40
     shapes = synth.picker_shapes(seed, n_train + n_test, e_lo=14.0, e_hi=19.0)
     recs = picker.collect(shapes, reps=3, seed=seed)
     X, y = picker.dataset(recs[:n_train])
-    params, hist = picker.train(X, y, epochs=600, seed=seed)
+    params, hist = picker.train(X, y, epochs=300, seed=seed)
     assert hist[-1][1] < hist[0][1]
     pool = picker.make_pool(shapes[n_train:])
     ev = picker.evaluate(params, recs[n_train:], pool=pool,
