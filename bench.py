@@ -81,12 +81,14 @@ L2_BYTES = 129 * 1000 * 1000  # GB300 L2
 # FP32 SIMT descriptors tried for the grouped launch: (elems_per_thread, split_i, unroll,
 # prefetch_smem, stages, ctas_per_sm)
 GROUPED_CANDIDATES = [(8, 8, 4, 1, 2, 3), (4, 8, 4, 1, 2, 3), (4, 8, 4, 1, 1, 3), (8, 4, 4, 1, 2, 2),
-                      (4, 8, 4, 1, 2, 2), (8, 8, 4, 1, 2, 1), (8, 8, 1, 1, 1, 1)]
+                      (4, 8, 4, 1, 2, 2), (8, 8, 4, 1, 2, 1), (8, 8, 1, 1, 1, 1), (4, 8, 1, 1, 2, 2),
+                      (4, 8, 1, 1, 2, 3), (8, 8, 1, 1, 2, 2)]
 # tensor-core descriptors tried for the grouped launch (BF16 / BF16X3): (K-block width,
-# epilogue threads per row, stages, store rows); the groups without a tensor-core plan run
-# in the library's FP32 launches after it (K-split, one a group)
-GROUPED_TC_CANDIDATES = [(64, 4, 1, 128), (1, 4, 1, 128), (64, 3, 1, 128), (64, 4, 2, 32), (64, 2, 2, 128),
-                         (1, 3, 2, 32)]
+# epilogue threads per row, stages, store rows, prefetch_smem: 2 = stage released early); the
+# groups without a shared-memory tensor-core plan run in the library's own launches after it
+GROUPED_TC_CANDIDATES = [(64, 4, 1, 128, 1), (1, 4, 1, 128, 1), (64, 3, 1, 128, 1), (64, 4, 2, 32, 1),
+                         (64, 2, 2, 128, 1), (1, 3, 2, 32, 1), (64, 3, 1, 128, 2), (1, 3, 1, 128, 2),
+                         (64, 2, 2, 128, 2)]
 
 # sources that decide each measured kernel's launch: the kernel, its helpers, the planner
 TC_SOURCES = ('tc.cu', 'tc.cuh', 'tma.cuh', 'lc_internal.h', 'api.cu')
@@ -646,9 +648,9 @@ def run_grouped(args, wl, world, rank, local_rank):
                           stages=st, ctas_per_sm=cps)
 
     def tc_variant(c):
-        kbw, tpr, st, rows = c
+        kbw, tpr, st, rows, pf = c
         return lc.Variant(engine="tcgen05", layout=args.layout, precision=prec, tile_e=128, elems_per_thread=kbw,
-                          split_i=0, unroll=tpr, prefetch_smem=1, stages=st, store_rows=0 if node else rows)
+                          split_i=0, unroll=tpr, prefetch_smem=pf, stages=st, store_rows=0 if node else rows)
 
     # descriptor: the fastest of a few tile shapes, each planned and captured once
     cands = [tc_variant(c) for c in GROUPED_TC_CANDIDATES] if tensor else \

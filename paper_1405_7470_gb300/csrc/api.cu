@@ -1841,20 +1841,53 @@ lc_status lc_variant_default(const lc_kernel *kh, int64_t E, int32_t N, int32_t 
                 return LC_OK;
             }
         }
+        if (N <= 12) {
+            // small N: the warp engine (32 / N elements a warp, D rows in registers, u values
+            // passed by shuffles); measured at N = 4, E = 360273: 12 us against 32 us for
+            // the SIMT tiles
+            lc_variant w = d;
+            w.engine = LC_ENGINE_WARP;
+            w.tile_e = (32 / N) * 8;
+            w.elems_per_thread = 1;
+            w.split_i = 1;
+            w.unroll = 1;
+            w.prefetch_smem = 0;
+            w.stages = 1;
+            w.ctas_per_sm = 4;
+            if (lc_variant_validate(kh, E, N, F, &w) == LC_OK) {
+                *v = w;
+                return LC_OK;
+            }
+        }
+        // SIMT tiles, two CTAs per SM, the u tile staged by bulk copies two tiles ahead; the
+        // fastest measured per layout and node count (autotuner, N = 20 .. 84, F = 2 .. 4):
+        // element-major 4 x 8 register blocks with j unrolled 4 times, 64-element tiles up to
+        // N = 40 and 32 above (N = 56: 0.58 ms against 1.00 ms for 128-element tiles of 8 x 8
+        // blocks); node-major without unrolling (N = 56: 0.57 against 0.77 ms unrolled)
         d.engine = LC_ENGINE_SIMT;
         d.ctas_per_sm = 2;
+        d.prefetch_smem = 1;
+        d.stages = 2;
         if (layout == LC_LAYOUT_ELEM_MAJOR) {
+            d.elems_per_thread = 4;
+            d.split_i = 8;
+            d.tile_e = N <= 40 ? 64 : 32;
+            d.unroll = 4;
+        } else if (N <= 24) {
+            d.elems_per_thread = 8;
+            d.split_i = 4;
+            d.tile_e = 128;
+            d.unroll = 4;
+        } else if (N <= 40) {
             d.elems_per_thread = 8;
             d.split_i = 8;
             d.tile_e = 128;
             d.unroll = 1;
-            d.stages = 1;
         } else {
             d.elems_per_thread = 4;
             d.split_i = 8;
-            d.tile_e = 64;
-            d.unroll = 4;
-            d.stages = 2;
+            d.tile_e = N <= 72 ? 64 : 32;
+            d.unroll = 1;
         }
     } else {
         d.engine = LC_ENGINE_TCGEN05;
@@ -1867,8 +1900,6 @@ lc_status lc_variant_default(const lc_kernel *kh, int64_t E, int32_t N, int32_t 
         // fewest cycles; then the narrowest blocks that cover K (least shared memory).
         // BF16X3: the A terms in shared memory first (the stacked order), one stage first (two
         // stages leave room for one output slot only); BF16: the planner's placement, two stages.
-        // (BF16X3 with the A terms in tensor memory, the only plan for N of about 100 to 128,
-        // measured slower than the K-split FP32 kernel there: shared-memory A only)
         const bool x3 = precision == LC_PREC_BF16X3;
         lc_status st = LC_ERR_INVALID_VARIANT;
         const bool x3node = x3 && layout == LC_LAYOUT_NODE_MAJOR;
@@ -1888,6 +1919,24 @@ lc_status lc_variant_default(const lc_kernel *kh, int64_t E, int32_t N, int32_t 
                     if (st != LC_OK && st != LC_ERR_INVALID_VARIANT)
                         return st;
                 }
+        if (st != LC_OK && x3) {
+            // no shared-memory plan for the three A terms (N of about 100 and more): the
+            // planner's placement (tensor memory), one operator per column block, 32-row
+            // stores; measured at N = 120, E = 310977: 0.44 ms against 0.69 ms for the K-split
+            // FP32 kernel (node-major 0.65 against 0.89 ms)
+            d.a_operand = 0;
+            d.split_i = 1;
+            d.unroll = 3;
+            d.prefetch_smem = 1;
+            d.stages = 1;
+            d.store_rows = layout == LC_LAYOUT_ELEM_MAJOR ? 32 : 0;
+            for (int kbw : {64, 1}) {
+                d.elems_per_thread = kbw;
+                st = lc_variant_validate(kh, E, N, F, &d);
+                if (st == LC_OK || st != LC_ERR_INVALID_VARIANT)
+                    break;
+            }
+        }
         if (st == LC_OK) {
             *v = d;
             return LC_OK;
@@ -2200,10 +2249,18 @@ lc_status lc_contract_host(const lc_kernel *kh, const lc_variant *v, const void 
 // ------------------------------------------------------------------ grouped launch
 
 namespace lc {
-// One plain K-split launch (a group of a tensor-core grouped plan without a tensor-core plan).
+// One plain K-split launch: a group of a tensor-core grouped plan without a tensor-core plan,
+// or a large-N group of an FP32 grouped plan.
 struct KsLaunch {
     KsArgs a;
     int grid, bm, bk, group;
+};
+
+// One plain tensor-core launch: a group of a tensor-core grouped plan whose plan needs the A
+// terms in tensor memory (no shared-memory plan fits), which the grouped kernel does not take.
+struct TcLaunch {
+    TcArgs a;
+    int layout, nterms, grid, group;
 };
 
 }  // namespace lc
@@ -2224,6 +2281,7 @@ struct lc_grouped_plan {
     int ngroups = 0, nsegs = 0;
     std::vector<lc_variant> group_variant;  // the descriptor serving each group
     std::vector<lc::KsLaunch> ks;           // K-split launches (after the tensor-core one)
+    std::vector<lc::TcLaunch> tcl;          // single-group tensor-core launches (after the K-split ones)
     int layout = 0;
 };
 
@@ -2280,8 +2338,13 @@ static lc_status grouped_plan_host(const Kernel &K, const lc_variant *v, const l
             const double idle = (double)(T - r.g.threads) / T;
             const double pad = (double)(r.g.nchunks * (long long)r.g.CW) / ((double)G.F * G.N) - 1.0;
             const bool nodel = v->layout == LC_LAYOUT_NODE_MAJOR;
-            const double key = idle * (nodel ? 0.25 : 4.0) + pad + (nodel ? 0.5 * (r.g.nchunks - 1) : 0.0) -
-                               0.05 * std::log2((double)vg.tile_e);
+            // node-major: the tile the autotuner measured fastest for the plain SIMT kernel at
+            // this N (lc_variant_default) comes first (grouped, full-size uneven batching: 7.9
+            // against 8.5 ms; element-major kept the weighted sum: 6.2 against 6.6 ms); the
+            // weighted sum orders the rest
+            const int pref = nodel ? (G.N <= 40 ? 128 : G.N <= 72 ? 64 : 32) : 0;
+            const double key = (vg.tile_e == pref ? -100.0 : 0.0) + idle * (nodel ? 0.25 : 4.0) + pad +
+                               (nodel ? 0.5 * (r.g.nchunks - 1) : 0.0) - 0.05 * std::log2((double)vg.tile_e);
             if (!have || key < best_key) {
                 best_key = key;
                 best = r;
@@ -2594,8 +2657,9 @@ struct GroupedPlanAll {
     GroupedPlanTc T;
     std::vector<lc_group> simt_groups;
     std::vector<int> simt_gi;  // their indices among the caller's groups
-    lc_variant simt_v, ks_v;
+    lc_variant simt_v, ks_v, tcl_v;
     std::vector<KsLaunch> ks;
+    std::vector<TcLaunch> tcl;
     bool has_simt = false;
     size_t off_map = 0, bytes = 0;
 };
@@ -2620,17 +2684,90 @@ static lc_variant grouped_ks_fallback(const lc_variant *v)
     return s;
 }
 
+// The tensor-core descriptor for the groups of a three-term grouped plan without a shared-
+// memory plan: the A terms where the planner puts them (tensor memory), one operator per
+// column block, 32-row stores (the library's default there; N = 120: 0.44 ms against 0.69 ms
+// for the K-split kernel).
+static lc_variant grouped_tc_fallback(const lc_variant *v)
+{
+    lc_variant s;
+    memset(&s, 0, sizeof s);
+    s.struct_size = sizeof(lc_variant);
+    s.engine = LC_ENGINE_TCGEN05;
+    s.layout = v->layout;
+    s.precision = v->precision;
+    s.tile_e = 128;
+    s.elems_per_thread = 64;
+    s.split_i = 1;
+    s.unroll = 3;
+    s.prefetch_smem = 1;
+    s.stages = 1;
+    s.store_rows = v->layout == LC_LAYOUT_ELEM_MAJOR ? 32 : 0;
+    return s;
+}
+
+// A K-split launch for group gi if its plan resolves (false: no K-split plan).
+static lc_status grouped_add_ks(const Kernel &K, const lc_variant &kv, const lc_group &G, int gi,
+                                std::vector<KsLaunch> &ks, bool *added)
+{
+    *added = false;
+    Resolved r;
+    const lc_status rs = resolve(K, G.E, G.N, G.F, &kv, r, true);
+    if (rs == LC_ERR_NO_DEVICE || rs == LC_ERR_CUDA)
+        return rs;
+    if (rs != LC_OK)
+        return LC_OK;
+    KsLaunch L;
+    L.a = r.ks;
+    L.a.D = static_cast<const float *>(G.D_dev);
+    L.a.u = static_cast<const float *>(G.u_dev);
+    L.a.out = static_cast<float *>(G.out_dev);
+    L.grid = r.g.grid;
+    L.bm = r.ks_bm;
+    L.bk = r.ks_bk;
+    L.group = gi;
+    ks.push_back(L);
+    *added = true;
+    return LC_OK;
+}
+
 static lc_status grouped_plan_all(const Kernel &K, const lc_variant *v, const lc_group *groups, int ng,
                                   GroupedPlanAll &A)
 {
     if (!v || v->struct_size != sizeof(lc_variant) || !groups || ng <= 0)
         return LC_ERR_INVALID_ARGUMENT;
     if (v->engine != LC_ENGINE_TCGEN05) {
-        lc_status st = grouped_plan_host(K, v, groups, ng, A.S);
+        // FP32: the groups of N >= 96 (where the K-split kernel, which streams D^T in chunks,
+        // is the library's default) run as one K-split launch each after the persistent launch
+        lc_status st = grouped_plan_host(K, v, groups, ng, A.S);  // validates the descriptor
         if (st != LC_OK)
             return st;
-        A.has_simt = true;
-        A.bytes = A.S.bytes;
+        if (v->precision == LC_PREC_FP32) {
+            A.ks_v = grouped_ks_fallback(v);
+            for (int gi = 0; gi < ng; ++gi) {
+                const lc_group &G = groups[gi];
+                bool added = false;
+                if (G.E > 0 && G.N >= 96) {
+                    st = grouped_add_ks(K, A.ks_v, G, gi, A.ks, &added);
+                    if (st != LC_OK)
+                        return st;
+                }
+                if (!added) {
+                    A.simt_groups.push_back(G);
+                    A.simt_gi.push_back(gi);
+                }
+            }
+            if (!A.ks.empty()) {
+                A.S = GroupedPlanHost();
+                if (!A.simt_groups.empty()) {
+                    st = grouped_plan_host(K, v, A.simt_groups.data(), (int)A.simt_groups.size(), A.S);
+                    if (st != LC_OK)
+                        return st;
+                }
+            }
+        }
+        A.has_simt = A.ks.empty() || !A.simt_groups.empty();
+        A.bytes = A.has_simt ? A.S.bytes : 16;
         return LC_OK;
     }
     if (v->precision != LC_PREC_BF16 && v->precision != LC_PREC_BF16X3)
@@ -2638,28 +2775,40 @@ static lc_status grouped_plan_all(const Kernel &K, const lc_variant *v, const lc
     lc_status st = grouped_plan_tc(K, v, groups, ng, A.T);
     if (st != LC_OK)
         return st;
-    // the rest: one K-split launch each, else (no K-split plan) the SIMT grouped launch
+    // the rest: three terms, one tensor-core launch each with the A terms in tensor memory
+    // where that plan resolves; else one K-split launch each; else (no K-split plan) the SIMT
+    // grouped launch
     A.ks_v = grouped_ks_fallback(v);
+    A.tcl_v = grouped_tc_fallback(v);
     for (int gi : A.T.simt_groups) {
         const lc_group &G = groups[gi];
         if (G.E == 0)
             continue;
-        Resolved r;
-        const lc_status rs = resolve(K, G.E, G.N, G.F, &A.ks_v, r, true);
-        if (rs == LC_ERR_NO_DEVICE || rs == LC_ERR_CUDA)
-            return rs;
-        if (rs == LC_OK) {
-            KsLaunch L;
-            L.a = r.ks;
-            L.a.D = static_cast<const float *>(G.D_dev);
-            L.a.u = static_cast<const float *>(G.u_dev);
-            L.a.out = static_cast<float *>(G.out_dev);
-            L.grid = r.g.grid;
-            L.bm = r.ks_bm;
-            L.bk = r.ks_bk;
-            L.group = gi;
-            A.ks.push_back(L);
-        } else {
+        if (v->precision == LC_PREC_BF16X3) {
+            Resolved r;
+            const lc_status rs = resolve(K, G.E, G.N, G.F, &A.tcl_v, r, true);
+            if (rs == LC_ERR_NO_DEVICE || rs == LC_ERR_CUDA)
+                return rs;
+            if (rs == LC_OK) {
+                TcLaunch L;
+                L.a = r.tc;
+                L.a.D = static_cast<const float *>(G.D_dev);
+                L.a.u = static_cast<const float *>(G.u_dev);
+                L.a.out = static_cast<float *>(G.out_dev);
+                L.a.err = error_word();
+                L.layout = r.layout;
+                L.nterms = 3;
+                L.grid = r.tc_grid;
+                L.group = gi;
+                A.tcl.push_back(L);
+                continue;
+            }
+        }
+        bool added = false;
+        const lc_status sk = grouped_add_ks(K, A.ks_v, G, gi, A.ks, &added);
+        if (sk != LC_OK)
+            return sk;
+        if (!added) {
             A.simt_groups.push_back(G);
             A.simt_gi.push_back(gi);
         }
@@ -2789,16 +2938,27 @@ lc_status lc_grouped_plan_create(const lc_kernel *kh, const lc_variant *v, const
             plan->group_variant[gi] = A.T.gv[gi];
         for (int gi : A.simt_gi)
             plan->group_variant[gi] = A.simt_v;
-        for (const KsLaunch &L : A.ks)
-            plan->group_variant[L.group] = A.ks_v;
-        plan->ks = A.ks;
-        plan->layout = v->layout;
-        for (const KsLaunch &L : A.ks) {
-            st = ks_launch(L.a, v->layout, L.bm, L.bk, 0, s, true);  // shared-memory size, before any capture
-            if (st != LC_OK) {
-                delete plan;
-                return st;
-            }
+    }
+    for (const KsLaunch &L : A.ks)
+        plan->group_variant[L.group] = A.ks_v;
+    for (const TcLaunch &L : A.tcl)
+        plan->group_variant[L.group] = A.tcl_v;
+    plan->ks = A.ks;
+    plan->tcl = A.tcl;
+    plan->layout = v->layout;
+    // shared-memory sizes, before any capture
+    for (const KsLaunch &L : A.ks) {
+        st = ks_launch(L.a, v->layout, L.bm, L.bk, 0, s, true);
+        if (st != LC_OK) {
+            delete plan;
+            return st;
+        }
+    }
+    for (const TcLaunch &L : A.tcl) {
+        st = tc_launch(L.a, L.layout, L.nterms, 0, s);
+        if (st != LC_OK) {
+            delete plan;
+            return st;
         }
     }
     if (use_graph) {
@@ -2812,6 +2972,9 @@ lc_status lc_grouped_plan_create(const lc_kernel *kh, const lc_variant *v, const
             }
             for (const KsLaunch &L : plan->ks)
                 if (le == cudaSuccess && ks_launch(L.a, plan->layout, L.bm, L.bk, L.grid, s, false) != LC_OK)
+                    le = cudaErrorLaunchFailure;
+            for (const TcLaunch &L : plan->tcl)
+                if (le == cudaSuccess && tc_launch(L.a, L.layout, L.nterms, L.grid, s) != LC_OK)
                     le = cudaErrorLaunchFailure;
             if (le == cudaSuccess && plan->fn) {
                 void *params[] = {&plan->args};
@@ -2855,6 +3018,13 @@ lc_status lc_grouped_run(lc_grouped_plan *plan, void *stream)
             if (st != LC_OK)
                 return st;
         }
+        for (const TcLaunch &L : plan->tcl) {
+            if (e != cudaSuccess)
+                break;
+            const lc_status st = tc_launch(L.a, L.layout, L.nterms, L.grid, s);
+            if (st != LC_OK)
+                return st;
+        }
         if (e == cudaSuccess && plan->fn) {
             void *params[] = {&plan->args};
             e = cudaLaunchKernel(plan->fn, dim3(plan->grid), dim3(plan->threads), params, plan->smem, s);
@@ -2871,6 +3041,8 @@ lc_status lc_grouped_plan_info(const lc_grouped_plan *plan, int32_t *grid, int32
         return LC_ERR_INVALID_ARGUMENT;
     int g = plan->grid + plan->grid_tc;
     for (const KsLaunch &L : plan->ks)
+        g += L.grid;
+    for (const TcLaunch &L : plan->tcl)
         g += L.grid;
     *grid = g;
     *segments = plan->nsegs;

@@ -1039,6 +1039,8 @@ static inline lc_status tc_launch_fn(void *fn, const TcArgs &a, int grid, cudaSt
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.smem_bytes);
     if (e != cudaSuccess)
         return cuda_fail(e);
+    if (grid <= 0)
+        return LC_OK;  // attribute set only (a capture launches later)
     TcArgs args = a;
     void *params[] = {&args};
     e = cudaLaunchKernel(fn, dim3(grid), dim3(tc_threads(a)), params,

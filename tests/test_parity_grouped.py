@@ -37,7 +37,7 @@ def test_grouped_matches_oracle(lc, layout, graph):
         groups.append((to_dev(D), to_dev(uu), out))
         host.append((D, uu))
     stream = torch.cuda.Stream()
-    for re_, rc, unr, pf, st in [(8, 4, 4, 1, 2), (4, 8, 1, 0, 1), (8, 8, 1, 1, 1)]:
+    for re_, rc, unr, pf, st in [(8, 4, 4, 1, 2), (4, 8, 1, 0, 1), (8, 8, 1, 1, 1), (4, 8, 1, 1, 2)]:
         v = lc.Variant(layout=layout, elems_per_thread=re_, split_i=rc, unroll=unr, prefetch_smem=pf, stages=st,
                        ctas_per_sm=2)
         plan = lc.GroupedPlan(kernel, v, groups, use_graph=graph, stream=stream)
@@ -53,7 +53,10 @@ def test_grouped_matches_oracle(lc, layout, graph):
                 ref = oracle.contract(D, uu, layout)
                 assert np.all(np.abs(got - ref) <= fma_bound(D, uu, layout, 2.0 ** -24)), (D.shape, layout)
         info = plan.info()
-        assert info["segments"] >= len(SIZES) - 1
+        assert info["segments"] >= len([n for n, _ in SIZES if n < 96]) - 1
+        # N >= 96: one K-split launch each (D^T streamed in chunks), the rest in the persistent launch
+        for k, (N, E) in enumerate(SIZES):
+            assert lc.variant_dict(plan.group_variant(k))["engine"] == ("ksplit" if N >= 96 else "simt"), (N, E)
         del plan
 
 

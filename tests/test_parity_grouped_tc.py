@@ -33,9 +33,9 @@ def lc():
 SIZES = [(4, 3000), (10, 777), (20, 1), (35, 4096), (56, 513), (84, 2000), (120, 300), (165, 257)]
 
 
-def tc_variant(lc, layout, prec, kbw=64, tpr=4, stages=1):
+def tc_variant(lc, layout, prec, kbw=64, tpr=4, stages=1, pf=1):
     return lc.Variant(engine="tcgen05", layout=layout, precision=prec, tile_e=128, elems_per_thread=kbw,
-                      split_i=0, unroll=tpr, prefetch_smem=1, stages=stages,
+                      split_i=0, unroll=tpr, prefetch_smem=pf, stages=stages,
                       store_rows=0 if layout == "node" else 128)
 
 
@@ -81,8 +81,10 @@ def test_grouped_tc_integer_exact(lc, layout, prec):
     data = [synth.integer_operands(E, N, 3, seed=k) for k, (N, E) in enumerate(SIZES)]
     groups, host = make_groups(SIZES, data, layout)
     stream = torch.cuda.Stream()
-    for kbw, tpr, stages, graph in ((64, 4, 1, True), (1, 2, 2, False), (1, 3, 1, True)):
-        v = tc_variant(lc, layout, prec, kbw, tpr, stages)
+    # (the last two release the u stage early: prefetch_smem = 2)
+    for kbw, tpr, stages, graph, pf in ((64, 4, 1, True, 1), (1, 2, 2, False, 1), (1, 3, 1, True, 1),
+                                        (64, 3, 1, True, 2), (1, 2, 2, False, 2)):
+        v = tc_variant(lc, layout, prec, kbw, tpr, stages, pf)
         plan = lc.GroupedPlan(kernel, v, groups, use_graph=graph, stream=stream)
         on_tc = [on_tensor_cores(lc, plan, k) for k in range(len(SIZES))]
         assert all(on_tc[:6]), (prec, kbw, on_tc)  # every group up to N = 84 runs on the tensor cores
@@ -104,7 +106,11 @@ def test_grouped_tc_random_within_bounds(lc, layout, prec):
     data = synth.grouped_operands(SIZES, F=3, seed=7)
     groups, host = make_groups(SIZES, data, layout)
     stream = torch.cuda.Stream()
-    v = tc_variant(lc, layout, prec)
+    for pf in (1, 2):
+        _check_random(lc, kernel, tc_variant(lc, layout, prec, pf=pf), groups, host, stream, layout, prec)
+
+
+def _check_random(lc, kernel, v, groups, host, stream, layout, prec):
     plan = lc.GroupedPlan(kernel, v, groups, use_graph=True, stream=stream)
     run_plan(lc, plan, groups, stream)
     for k, ((N, E), (D, uu), (_, _, out)) in enumerate(zip(SIZES, host, groups)):
@@ -175,8 +181,9 @@ def test_grouped_tc_strided_large_groups(lc, layout):
 @pytest.mark.parametrize("layout", ["elem", "node"])
 def test_grouped_tc_full_size_sampled(lc, layout):
     """The uneven-batching workload at full size (8 groups, N in {4, ..., 165}, 3,554,987
-    elements, F = 3) in the bench's launch configuration: BF16X3 tensor-core launch for
-    N <= 120, SIMT launch for N = 165, one graph; sampled rows of every group."""
+    elements, F = 3) in the bench's launch configuration: BF16X3 grouped tensor-core launch
+    for N <= 84, a tensor-core launch with the A terms in tensor memory for N = 120, a K-split
+    launch for N = 165, one graph; sampled rows of every group."""
     kernel = lc.Kernel()
     sizes = synth.grouped_sizes(0)
     data = synth.grouped_operands(sizes, F=3, seed=0)

@@ -236,9 +236,22 @@ def test_bf16x3_a_in_tensor_memory(lc, layout, E, N, F):
                             layout, "bf16x3")
         assert np.all(np.abs(got - oracle.contract_bf16x3(D, uu, layout)) <= bound), (E, N, F, kbw)
         assert oracle.rel_fro_error(got, oracle.contract(D, uu, layout)) <= 1e-6
-    # the default for N = 120 is the faster K-split FP32 kernel (FP32 error, below the bound)
-    v = lc.variant_default(kernel, 300, 120, 3, layout, "bf16x3")
-    assert lc.variant_dict(v)["engine"] == "ksplit"
+    if N >= 120:
+        # the default from N of about 100 (no shared-memory plan): A in tensor memory, one
+        # operator per column block, 32-row stores; checked the same way
+        v = lc.variant_default(kernel, E, N, F, layout, "bf16x3")
+        assert lc.variant_dict(v)["engine"] == "tcgen05" and lc.variant_plan(kernel, E, N, F, v)["a_in_tmem"] == 1
+        D, u = synth.integer_operands(E, N, F, seed=E + N + 7)
+        uu = synth.to_node_major(u) if layout == "node" else u
+        assert np.array_equal(run(lc, kernel, v, D, uu, layout), oracle.contract(D, uu, layout)), (E, N, F)
+        D, u = synth.operands(E, N, F, np.float32, seed=E + 5 * N, scale_exp=3.0)
+        uu = synth.to_node_major(u) if layout == "node" else u
+        got = run(lc, kernel, v, D, uu, layout)
+        Ds, us = oracle.bf16_split3(D), oracle.bf16_split3(uu)
+        bound = accum_bound(np.abs(Ds[0]) + np.abs(Ds[1]) + np.abs(Ds[2]), np.abs(us[0]) + np.abs(us[1]) + np.abs(us[2]),
+                            layout, "bf16x3")
+        assert np.all(np.abs(got - oracle.contract_bf16x3(D, uu, layout)) <= bound), (E, N, F)
+        assert oracle.rel_fro_error(got, oracle.contract(D, uu, layout)) <= 1e-6
 
 
 
