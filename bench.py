@@ -1055,9 +1055,11 @@ def run_lift(args, wl, world, rank, local_rank):
     out = torch.zeros((E, N), device="cuda")
     stream = torch.cuda.Stream()
     best = None
-    for ctas in ((4,) if args.variant == "default" else (1, 2, 3, 4, 6, 8)):
+    v0 = lc.variant_default(k, E, N, 1, "elem", "fp32")
+    for ctas, stages in (((v0.ctas_per_sm, v0.stages),) if args.variant == "default" else
+                         ((2, 1), (3, 1), (4, 1), (6, 1), (2, 2), (3, 2))):
         v = lc.variant_default(k, E, N, 1, "elem", "fp32")
-        v.ctas_per_sm = ctas
+        v.ctas_per_sm, v.stages = ctas, stages
         with torch.cuda.stream(stream):
             lc.lift(k, v, Ld, fd, vd, sd, ud, out, stream=stream)
             a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1103,7 +1105,7 @@ def run_lift(args, wl, world, rank, local_rank):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl["desc"], "E": E, "N": N, "M": M, "variant": lc.variant_dict(v),
-                       "variant_choice": "fastest CTAs/SM of 6", "bytes_per_step": nbytes,
+                       "variant_choice": "default descriptor" if args.variant == "default" else "fastest (CTAs/SM, staging buffers) of 6", "bytes_per_step": nbytes,
                        "l2": "inputs+outputs larger than L2 (no flush needed)"},
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": ach / peaks["hbm_gbs"], "traffic": ncu_traffic("lift", "elem", "fp32", "simt"),

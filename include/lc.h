@@ -333,12 +333,13 @@ lc_status lc_contract_geo(const lc_kernel *k, const lc_variant *v, const void *D
  *   s_dev      [E][Nf] float               u_dev, out_dev  [E][N] float, out not overlapping
  *   accumulate 1: out += the lifted fluxes; 0: out = them
  * Sizes: 1 <= N <= 128, Nf * Nfp <= 256, E * N < 2^31.  Descriptor: engine SIMT, FP32,
- * element-major; prefetch_smem 1 (add_prefetch) has the bulk-copy engine stage, two tiles
- * ahead, each 64-element tile's vmapP rows, face scales, u rows and up to 64 u rows on
- * either side (fewer where shared memory is short) in shared memory; exterior traces
- * inside that window are read from there, the others from global memory (u, vmapP and s
- * must then be 16-byte aligned, else every operand is read from global memory, as with
- * prefetch_smem 0); ctas_per_sm (0 = 4) and max_ctas size the persistent grid.  An index out
+ * element-major; prefetch_smem 1 (add_prefetch) has the bulk-copy engine stage, `stages`
+ * (1 or 2) tiles ahead in as many buffers, each 64-element tile's vmapP rows, face scales,
+ * u rows and up to 64 u rows on either side (fewer where shared memory is short) in shared
+ * memory; exterior traces inside that window are read from there, the others from global
+ * memory (u, vmapP and s must then be 16-byte aligned, else every operand is read from
+ * global memory, as with prefetch_smem 0); ctas_per_sm (0 = 4) and max_ctas size the
+ * persistent grid, which never exceeds the CTAs resident at once.  An index out
  * of range is not followed: its flux becomes NaN and lc_device_error reports LC_ERR_INDEX.
  * Errors: LC_ERR_INVALID_ARGUMENT, LC_ERR_INVALID_VARIANT, LC_ERR_MISALIGNED (4-byte),
  * LC_ERR_NO_DEVICE, LC_ERR_UNSUPPORTED (not a kernel of this form), LC_ERR_CUDA.

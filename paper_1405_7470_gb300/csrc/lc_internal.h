@@ -184,13 +184,14 @@ struct LiftArgs {
     int N, Nf, Nfp, M;
     int accumulate;
     int halo;              // >= 0: the tile's vmapP rows, scales, u rows and `halo` u rows on
-                           // either side are staged in shared memory (bulk copies, two tiles
+                           // either side are staged in shared memory (bulk copies, nbuf tiles
                            // ahead) and exterior traces inside that window read from there;
                            // -1: every operand read from global memory
+    int nbuf;              // staging buffers (1 or 2)
     unsigned int *err;     // device error word: bit 1 set on an index out of range
 };
 lc_status lift_launch(const LiftArgs &a, int grid, cudaStream_t s);
-size_t lift_smem_bytes(int N, int M, int Nf, int halo);
+size_t lift_smem_bytes(int N, int M, int Nf, int halo, int nbuf);
 int lift_threads(int N);
 
 // Elementwise kernels: check a descriptor against extents (one per iname) without launching;

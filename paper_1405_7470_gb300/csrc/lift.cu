@@ -8,9 +8,10 @@
 // the limit, so the tensor cores would buy nothing here).
 //
 // One CTA walks element tiles of TE elements (persistent, grid-stride):
-//   stage    (add_prefetch, descriptor prefetch_smem = 1) the bulk-copy engine fetches, two
-//            tiles ahead of the compute, the tile's vmapP rows, its face scales and a u
-//            window: the rows of the tile and of `halo` elements on either side, one
+//   stage    (add_prefetch, descriptor prefetch_smem = 1) the bulk-copy engine fetches, one
+//            or two tiles ahead of the compute (descriptor stages: staging buffers), the
+//            tile's vmapP rows, its face scales and a u window: the rows of the tile and of
+//            `halo` elements on either side, one
 //            contiguous run.  Exterior traces inside the window (on a structured mesh, all
 //            of them) are read from shared memory, the others from global memory;
 //            (prefetch_smem = 0: every operand is read from global memory)
@@ -39,11 +40,12 @@ static constexpr int kLiftG = 4;       // gathered items per thread in flight
 __host__ __device__ inline size_t lift_r4(size_t n) { return (n + 3) & ~(size_t)3; }
 
 // Shared memory: L^T [M][NP], the flux tile [M][TP], {node, face} per face node, two
-// mbarriers, then (staged) two buffers of {u window, vmapP tile, scale tile}, 16-byte aligned.
+// mbarriers, then (staged) nbuf buffers of {u window, vmapP tile, scale tile}, 16-byte
+// aligned.
 struct LiftSmem {
     size_t flux, fmf, bars, buf, buf_bytes, win, vm, sc, total;
 };
-__host__ __device__ inline LiftSmem lift_smem(int N, int M, int Nf, int halo)
+__host__ __device__ inline LiftSmem lift_smem(int N, int M, int Nf, int halo, int nbuf)
 {
     LiftSmem L;
     const size_t NP = (size_t)(N + kLiftRC - 1) / kLiftRC * kLiftRC, TP = kLiftTE + kLiftPad;
@@ -55,7 +57,7 @@ __host__ __device__ inline LiftSmem lift_smem(int N, int M, int Nf, int halo)
     L.vm = halo < 0 ? 0 : sizeof(float) * lift_r4((size_t)(kLiftTE + 2 * halo) * N);
     L.sc = L.vm + sizeof(int) * lift_r4((size_t)kLiftTE * M);
     L.buf_bytes = halo < 0 ? 0 : L.sc + sizeof(float) * lift_r4((size_t)kLiftTE * Nf);
-    L.total = L.buf + 2 * L.buf_bytes;
+    L.total = L.buf + (size_t)nbuf * L.buf_bytes;
     return L;
 }
 
@@ -69,7 +71,8 @@ __global__ void __launch_bounds__(512) lift_kernel(LiftArgs a)
     const int NP = CG * kLiftRC;                 // padded node count
     const int TP = kLiftTE + kLiftPad;           // flux row stride
     const int H = STAGED ? a.halo : 0;
-    const LiftSmem lay = lift_smem(N, M, Nf, STAGED ? H : -1);
+    const int NB = STAGED ? a.nbuf : 1;  // staging buffers (1 or 2)
+    const LiftSmem lay = lift_smem(N, M, Nf, STAGED ? H : -1, NB);
     float *LT = reinterpret_cast<float *>(smem_raw);  // [M][NP]
     float *flux = reinterpret_cast<float *>(smem_raw + lay.flux);  // [M][TP]
     int2 *fmf = reinterpret_cast<int2 *>(smem_raw + lay.fmf);      // [M] {node, face}
@@ -120,10 +123,11 @@ __global__ void __launch_bounds__(512) lift_kernel(LiftArgs a)
     }
     __syncthreads();
     if (STAGED && tid == 0) {
-        for (int b = 0; b < 2; ++b)
+        for (int b = 0; b < NB; ++b)
             if (blockIdx.x + (long long)b * gridDim.x < ntiles)
                 issue(blockIdx.x + (long long)b * gridDim.x, b);
     }
+    const int EN = (int)(E * N);  // E * N < 2^31 (checked by the host): flat u indices are ints
     // the gather walks idx = te * M + m = tid, tid + nthr, ...: one step adds dte to te and
     // dm (< M) to m, with a carry
     const int dte = nthr / M, dm = nthr - dte * M;
@@ -135,7 +139,8 @@ __global__ void __launch_bounds__(512) lift_kernel(LiftArgs a)
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
         const long long e0 = t * kLiftTE;
         const int TEv = (int)min((long long)kLiftTE, E - e0);
-        const int b = k & 1;
+        const int b = NB == 2 ? (k & 1) : 0;
+        const uint32_t ph = (uint32_t)((NB == 2 ? k >> 1 : k) & 1);
         long long lo = 0;
         int wn = 0, vn = 0, sn = 0;
         const float *win = nullptr, *scb = nullptr;
@@ -143,7 +148,7 @@ __global__ void __launch_bounds__(512) lift_kernel(LiftArgs a)
         if (STAGED) {
             runs(t, lo, wn, vn, sn);
             unsigned char *buf = smem_raw + lay.buf + (size_t)b * lay.buf_bytes;
-            const bool ok = mbar_wait(&bars[b], (uint32_t)((k >> 1) & 1));
+            const bool ok = mbar_wait(&bars[b], ph);
             if (!__syncthreads_and(ok)) {
                 if (tid == 0)
                     atomicOr(a.err, 1u);
@@ -164,7 +169,8 @@ __global__ void __launch_bounds__(512) lift_kernel(LiftArgs a)
             vm = v;
             scb = c;
         }
-        const long long wb = lo * N;  // flat u index of the window's first value
+        const int wb = (int)(lo * N);                 // flat u index of the window's first value
+        const int ib = (int)(e0 - lo) * N;            // window index of the tile's first row
         // gather the tile's fluxes, kLiftG items per thread in flight: all index loads first,
         // then all trace loads, then the fluxes
         int te_c = te_first, m_c = m_first;
@@ -187,12 +193,12 @@ __global__ void __launch_bounds__(512) lift_kernel(LiftArgs a)
 #pragma unroll
             for (int g = 0; g < kLiftG; ++g) {
                 const bool live = te[g] < TEv;
-                const bool in = live && q[g] >= 0 && (long long)q[g] < E * N;
+                const bool in = live && (unsigned)q[g] < (unsigned)EN;
                 const int2 nf = fmf[live ? m[g] : 0];
                 if (STAGED) {
-                    const long long qw = (long long)q[g] - wb;  // position in the window
-                    ux[g] = in ? ((qw >= 0 && qw < wn) ? win[qw] : a.u[q[g]]) : 0.f;
-                    ui[g] = live ? win[(e0 + te[g] - lo) * N + nf.x] : 0.f;  // the tile lies in the window
+                    const int qw = q[g] - wb;  // position in the window
+                    ux[g] = in ? ((unsigned)qw < (unsigned)wn ? win[qw] : a.u[q[g]]) : 0.f;
+                    ui[g] = live ? win[ib + te[g] * N + nf.x] : 0.f;  // the tile lies in the window
                     sc[g] = live ? scb[te[g] * Nf + nf.y] : 0.f;
                 } else {
                     ux[g] = in ? a.u[q[g]] : 0.f;
@@ -206,7 +212,7 @@ __global__ void __launch_bounds__(512) lift_kernel(LiftArgs a)
                     break;
                 float v = 0.f;
                 if (te[g] < TEv) {
-                    if (q[g] >= 0 && (long long)q[g] < E * N) {
+                    if ((unsigned)q[g] < (unsigned)EN) {
                         v = __fmul_rn(sc[g], __fsub_rn(ui[g], ux[g]));
                     } else {
                         v = __int_as_float(0x7fc00000);  // out-of-range index: NaN, recorded
@@ -219,8 +225,8 @@ __global__ void __launch_bounds__(512) lift_kernel(LiftArgs a)
         fence_async_smem();
         __syncthreads();
         if (STAGED && tid == 0) {
-            // buffer b is consumed: fetch the tile two steps ahead into it
-            const long long nt = t + 2LL * gridDim.x;
+            // buffer b is consumed: fetch the tile NB steps ahead into it
+            const long long nt = t + (long long)NB * gridDim.x;
             if (nt < ntiles)
                 issue(nt, b);
         }
@@ -264,7 +270,7 @@ __global__ void __launch_bounds__(512) lift_kernel(LiftArgs a)
     }
 }
 
-size_t lift_smem_bytes(int N, int M, int Nf, int halo) { return lift_smem(N, M, Nf, halo).total; }
+size_t lift_smem_bytes(int N, int M, int Nf, int halo, int nbuf) { return lift_smem(N, M, Nf, halo, nbuf).total; }
 
 int lift_threads(int N)
 {
@@ -275,11 +281,20 @@ int lift_threads(int N)
 
 lc_status lift_launch(const LiftArgs &a, int grid, cudaStream_t s)
 {
-    const size_t smem = lift_smem_bytes(a.N, a.M, a.Nf, a.halo);
+    const size_t smem = lift_smem_bytes(a.N, a.M, a.Nf, a.halo, a.nbuf);
     void *fn = a.halo >= 0 ? reinterpret_cast<void *>(&lift_kernel<true>) : reinterpret_cast<void *>(&lift_kernel<false>);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return cuda_fail(e);
+    // a persistent grid no larger than the CTAs that are resident at once (shared memory may
+    // allow fewer per SM than asked for; the rest would wait for a second wave)
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, lift_threads(a.N), smem);
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    const int sms = sm_count();
+    if (per_sm > 0 && sms > 0)
+        grid = std::min(grid, per_sm * sms);
     LiftArgs args = a;
     void *params[] = {&args};
     e = cudaLaunchKernel(fn, dim3(grid), dim3(lift_threads(a.N)), params, smem, s);
@@ -310,8 +325,9 @@ lc_status lc_lift(const lc_kernel *kh, const lc_variant *v, const float *L, cons
     // persistent grid; nothing else is used
     if (v->engine != LC_ENGINE_SIMT || v->precision != LC_PREC_FP32 || v->layout != LC_LAYOUT_ELEM_MAJOR ||
         v->ctas_per_sm < 0 || v->ctas_per_sm > 8 || v->max_ctas < 0 || v->prefetch_smem < 0 ||
-        v->prefetch_smem > 1)
+        v->prefetch_smem > 1 || v->stages < 1 || v->stages > 2)
         return LC_ERR_INVALID_VARIANT;
+    const int nbuf = v->stages;  // staging buffers
     for (const void *p : {(const void *)L, (const void *)fmask, (const void *)vmapP, (const void *)s,
                           (const void *)u, (const void *)out})
         if ((uintptr_t)p & 3u)
@@ -332,20 +348,22 @@ lc_status lc_lift(const lc_kernel *kh, const lc_variant *v, const float *L, cons
     if (current_cc(&major, &minor) != 0 || major != 10 || minor != 3)
         return LC_ERR_NO_DEVICE;
     // the window's halo: 64 elements (the largest face-neighbour offset of a structured
-    // strip of width 64), halved while the CTA's shared memory would exceed a quarter of the
-    // SM's (four CTAs per SM), none without prefetch_smem
+    // strip of width 64), halved while the CTA's shared memory would keep ctas_per_sm (at
+    // least 2) CTAs from sharing an SM; none without prefetch_smem
     // The staged path needs 16-byte aligned u, vmapP and s (bulk copies); others read every
     // operand from global memory.
     int halo = -1;
     if (v->prefetch_smem && ((((uintptr_t)u | (uintptr_t)vmapP | (uintptr_t)s) & 15u) == 0)) {
         // (a multiple of 4: the window's first row then starts on a 16-byte boundary)
         halo = 64;
-        while (halo > 0 && lift_smem_bytes(N, Nf * Nfp, Nf, halo) > smem_optin_limit() / 2)
+        const int want = std::max(2, v->ctas_per_sm ? v->ctas_per_sm : 4);
+        const size_t fit = smem_optin_limit() / want - 1024;  // (1 KB reserved per CTA)
+        while (halo > 0 && lift_smem_bytes(N, Nf * Nfp, Nf, halo, nbuf) > fit)
             halo = halo > 4 ? halo / 2 : 0;
-        if (lift_smem_bytes(N, Nf * Nfp, Nf, halo) > smem_optin_limit())
+        if (lift_smem_bytes(N, Nf * Nfp, Nf, halo, nbuf) > smem_optin_limit())
             halo = -1;
     }
-    if (lift_smem_bytes(N, Nf * Nfp, Nf, halo) > smem_optin_limit())
+    if (lift_smem_bytes(N, Nf * Nfp, Nf, halo, nbuf) > smem_optin_limit())
         return LC_ERR_INVALID_VARIANT;
     if (E == 0)
         return LC_OK;
@@ -366,6 +384,7 @@ lc_status lc_lift(const lc_kernel *kh, const lc_variant *v, const float *L, cons
     a.M = Nf * Nfp;
     a.accumulate = accumulate;
     a.halo = halo;
+    a.nbuf = nbuf;
     a.err = error_word();
     const long long ntiles = (E + 63) / 64;
     long long grid = std::min<long long>(ntiles, (long long)(v->ctas_per_sm ? v->ctas_per_sm : 4) * sms);
