@@ -567,6 +567,23 @@ lc_status lc_pick_variant(const lc_kernel *k, int64_t E, int32_t N, int32_t F, i
                           lc_variant *picked, float *predicted, void *stream);
 
 /*
+ * lc_pick_variant with an ensemble of n_models networks of the same shape, trained apart
+ * (different initialisations and minibatch orders): each candidate's prediction is the mean
+ * of the models' predicted log run times (models taken in order), and the candidate with
+ * the smallest mean is returned (*predicted = that mean).  Averaging removes much of one
+ * network's variance between trainings (held-out regret of single networks differs by
+ * several points from seed to seed).  lc_pick_variant is the case n_models = 1.
+ *   params_dev  n_models consecutive parameter blocks of lc_mlp_param_count(LC_FEATURES)
+ *               floats each, 4-byte aligned
+ *   n_models    1 to 64
+ * Errors: those of lc_pick_variant.
+ */
+lc_status lc_pick_variant_ensemble(const lc_kernel *k, int64_t E, int32_t N, int32_t F, int32_t layout,
+                                   int32_t precision, const float *params_dev, int32_t n_models,
+                                   void *workspace_dev, size_t workspace_bytes, lc_variant *picked,
+                                   float *predicted, void *stream);
+
+/*
  * lc_error_norm without a workspace, for callers that cannot allocate device memory
  * (cudaMalloc synchronises the device, which latency-bound or real-time callers forbid,
  * and some host frameworks give their plugins no allocator).  This call has no

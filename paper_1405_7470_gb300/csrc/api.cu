@@ -2564,8 +2564,9 @@ static lc_status grouped_plan_tc(const Kernel &K, const lc_variant *v, const lc_
             }
             if (q > 0 && memcmp(&vg, v, sizeof vg) == 0)
                 continue;
-            // three terms: the A terms in shared memory unless tensor memory is asked for (the
-            // K-split FP32 launch beats the tensor-memory plans, measured at N = 120)
+            // three terms: the A terms in shared memory unless tensor memory is asked for; a
+            // group whose three-term plan needs them in tensor memory runs as its own launch
+            // after the grouped one (grouped_plan_all)
             if (T.nterms == 3 && v->a_operand == 0)
                 vg.a_operand = 1;
             rs = resolve(K, G.E, G.N, G.F, &vg, r, true);

@@ -1,6 +1,7 @@
 // Learned variant pick behind the C ABI: the cost model's input features of a
 // (problem, descriptor) pair, and the pick itself (enumerate the candidates, build their
-// features, run the network with lc_mlp_forward on the device, take the argmin).
+// features, run the network, or each network of an ensemble, with lc_mlp_forward on the
+// device, take the argmin of the (mean) prediction).
 //
 // The paper leaves the choice of transformations to the controlling program, which can
 // react to the target and the workload (Section 1); here that program is a small network
@@ -98,24 +99,28 @@ lc_status lc_pick_workspace_size(size_t *bytes)
     return LC_OK;
 }
 
-lc_status lc_pick_variant(const lc_kernel *k, int64_t E, int32_t N, int32_t F, int32_t layout, int32_t precision,
-                          const float *params_dev, void *workspace_dev, size_t workspace_bytes, lc_variant *picked,
-                          float *predicted, void *stream)
+lc_status lc_pick_variant_ensemble(const lc_kernel *k, int64_t E, int32_t N, int32_t F, int32_t layout,
+                                   int32_t precision, const float *params_dev, int32_t n_models, void *workspace_dev,
+                                   size_t workspace_bytes, lc_variant *picked, float *predicted, void *stream)
 {
-    if (!k || !params_dev || !workspace_dev || !picked)
+    if (!k || !params_dev || !workspace_dev || !picked || n_models < 1 || n_models > 64)
         return LC_ERR_INVALID_ARGUMENT;
     if (workspace_bytes < lc::pick_bytes())
         return LC_ERR_BUFFER_TOO_SMALL;
     if (((uintptr_t)workspace_dev & 15u) || ((uintptr_t)params_dev & 3u))
         return LC_ERR_MISALIGNED;
+    int64_t P = 0;
+    lc_status st = lc_mlp_param_count(LC_FEATURES, &P);
+    if (st != LC_OK)
+        return st;
     std::vector<lc_variant> cand(lc::kPickCap);
     int n = 0;
-    lc_status st = lc_enumerate_variants(k, E, N, F, layout, precision, cand.data(), lc::kPickCap, &n);
+    st = lc_enumerate_variants(k, E, N, F, layout, precision, cand.data(), lc::kPickCap, &n);
     if (st != LC_OK)
         return st;
     if (n == 0)
         return LC_ERR_UNSUPPORTED;
-    std::vector<float> X((size_t)n * LC_FEATURES), y(n);
+    std::vector<float> X((size_t)n * LC_FEATURES), y(n), sum(n, 0.f);
     for (int c = 0; c < n; ++c) {
         st = lc::features(k, E, N, F, layout, precision, &cand[c], &X[(size_t)c * LC_FEATURES]);
         if (st != LC_OK)
@@ -127,22 +132,35 @@ lc_status lc_pick_variant(const lc_kernel *k, int64_t E, int32_t N, int32_t F, i
     cudaError_t e = cudaMemcpyAsync(Xd, X.data(), sizeof(float) * X.size(), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess)
         return lc::cuda_fail(e);
-    st = lc_mlp_forward(params_dev, Xd, n, LC_FEATURES, yd, stream);
-    if (st != LC_OK)
-        return st;
-    e = cudaMemcpyAsync(y.data(), yd, sizeof(float) * n, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess)
-        e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess)
-        return lc::cuda_fail(e);
+    // the models' predicted log times, averaged in model order
+    for (int q = 0; q < n_models; ++q) {
+        st = lc_mlp_forward(params_dev + (size_t)q * P, Xd, n, LC_FEATURES, yd, stream);
+        if (st != LC_OK)
+            return st;
+        e = cudaMemcpyAsync(y.data(), yd, sizeof(float) * n, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess)
+            return lc::cuda_fail(e);
+        for (int c = 0; c < n; ++c)
+            sum[c] += y[c];
+    }
     int best = 0;
     for (int c = 1; c < n; ++c)
-        if (y[c] < y[best])
+        if (sum[c] < sum[best])
             best = c;
     *picked = cand[best];
     if (predicted)
-        *predicted = y[best];
+        *predicted = sum[best] / (float)n_models;
     return LC_OK;
+}
+
+lc_status lc_pick_variant(const lc_kernel *k, int64_t E, int32_t N, int32_t F, int32_t layout, int32_t precision,
+                          const float *params_dev, void *workspace_dev, size_t workspace_bytes, lc_variant *picked,
+                          float *predicted, void *stream)
+{
+    return lc_pick_variant_ensemble(k, E, N, F, layout, precision, params_dev, 1, workspace_dev, workspace_bytes,
+                                    picked, predicted, stream);
 }
 
 }  // extern "C"

@@ -108,6 +108,8 @@ SIGNATURES = {
     "lc_pick_workspace_size": ([ctypes.POINTER(_SZ)], ctypes.c_int),
     "lc_pick_variant": ([_P, _I64, _I32, _I32, _I32, _I32, _P, _P, _SZ, _VP, ctypes.POINTER(ctypes.c_float), _P],
                         ctypes.c_int),
+    "lc_pick_variant_ensemble": ([_P, _I64, _I32, _I32, _I32, _I32, _P, _I32, _P, _SZ, _VP,
+                                  ctypes.POINTER(ctypes.c_float), _P], ctypes.c_int),
 }
 FEATURES = 32  # LC_FEATURES
 
@@ -450,7 +452,9 @@ def variant_features(kernel: Kernel, E: int, N: int, F: int, layout, precision, 
 
 
 def pick_variant(kernel: Kernel, E: int, N: int, F: int, layout, precision, params, workspace=None, stream=None):
-    """(descriptor, predicted log ms) picked by the trained network `params` (lc_pick_variant)."""
+    """(descriptor, predicted log ms) picked by the trained network `params` (lc_pick_variant),
+    or by an ensemble when `params` is 2-D, one network's parameters per row
+    (lc_pick_variant_ensemble)."""
     import torch
     lib = load()
     need = ctypes.c_size_t(0)
@@ -459,9 +463,16 @@ def pick_variant(kernel: Kernel, E: int, N: int, F: int, layout, precision, para
         workspace = torch.empty(need.value // 4 + 4, dtype=torch.float32, device=params.device)
     v = lc_variant()
     pred = ctypes.c_float(0.0)
-    check(lib.lc_pick_variant(kernel.handle, E, N, F, LAYOUT[layout], PRECISION[precision], params.data_ptr(),
-                              workspace.data_ptr(), need.value, ctypes.byref(v), ctypes.byref(pred),
-                              _stream_ptr(stream)), "lc_pick_variant")
+    if params.dim() == 2:
+        params = params.contiguous()
+        check(lib.lc_pick_variant_ensemble(kernel.handle, E, N, F, LAYOUT[layout], PRECISION[precision],
+                                           params.data_ptr(), params.shape[0], workspace.data_ptr(), need.value,
+                                           ctypes.byref(v), ctypes.byref(pred), _stream_ptr(stream)),
+              "lc_pick_variant_ensemble")
+    else:
+        check(lib.lc_pick_variant(kernel.handle, E, N, F, LAYOUT[layout], PRECISION[precision], params.data_ptr(),
+                                  workspace.data_ptr(), need.value, ctypes.byref(v), ctypes.byref(pred),
+                                  _stream_ptr(stream)), "lc_pick_variant")
     return v, pred.value
 
 

@@ -5,7 +5,8 @@ transformations per target and per workload. Here the choice is made two ways:
   * exhaustively: lc_autotune times every valid descriptor (the judge of regret);
   * by a small MLP cost model (3 hidden ReLU layers of 64) that predicts log run time
     from problem and descriptor features; its training and inference run in the
-    library's own CUDA kernels (lc_mlp_loss_grad, lc_mlp_adam_step, lc_mlp_forward).
+    library's own CUDA kernels (lc_mlp_loss_grad, lc_mlp_adam_step, lc_mlp_forward); an
+    ensemble of three such networks, trained apart, averages their predictions.
 
 regret(shape) = t(picked) / t(best) - 1, where best is the exhaustive autotuner's winner;
 on held-out shapes the pick, the best and the default descriptor are re-timed together in
@@ -16,8 +17,8 @@ network with the library's kernels and reports.
 
 Running ``python -m paper_1405_7470_gb300.picker --out results.json`` on a GPU runs the
 whole experiment on the 600 seeded shapes (first 500 train, last 100 held out).
-Training: Adam, 1000 epochs of 512-sample minibatches, learning rate 3e-3 decayed on a
-cosine schedule.
+Training: three networks (seeds 0, 1, 2), each Adam, 1000 epochs of 512-sample
+minibatches, learning rate 3e-3 decayed on a cosine schedule.
 """
 
 from __future__ import annotations
@@ -179,8 +180,22 @@ def train(X: np.ndarray, y: np.ndarray, epochs: int = 1000, batch: int = 512, lr
     return params, hist
 
 
+def train_ensemble(X: np.ndarray, y: np.ndarray, models: int = 3, epochs: int = 1000, seed: int = 0, log=None,
+                   **kw):
+    """`models` networks trained apart (seeds seed, seed + 1, ...: initialisation and minibatch
+    order); returns (params [models][P], loss histories)."""
+    import torch
+    ps, hs = [], []
+    for q in range(models):
+        p, h = train(X, y, epochs=epochs, seed=seed + q, log=log, **kw)
+        ps.append(p)
+        hs.append(h)
+    return torch.stack(ps), hs
+
+
 def pick(params, shape: dict, workspace=None):
-    """The trained network's descriptor for a shape, chosen by the library (lc_pick_variant)."""
+    """The trained network's (or ensemble's, params [models][P]) descriptor for a shape, chosen
+    by the library (lc_pick_variant / lc_pick_variant_ensemble)."""
     v, _ = lc.pick_variant(kernel_for(shape["F"]), shape["E"], shape["N"], shape["F"], shape["layout"],
                            shape["path"], params, workspace=workspace)
     return lc.variant_dict(v)
@@ -269,7 +284,7 @@ def make_pool(shapes):
 
 
 def run_experiment(out_path: str, n_shapes: int = 600, n_train: int = 500, reps: int = 3, epochs: int = 1000,
-                   seed: int = 0):
+                   seed: int = 0, models: int = 3):
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import synth
     log = lambda s: print(s, flush=True)
@@ -280,7 +295,8 @@ def run_experiment(out_path: str, n_shapes: int = 600, n_train: int = 500, reps:
     tr, te = recs[:n_train], recs[n_train:]
     X, y = dataset(tr)
     t1 = time.perf_counter()
-    params, hist = train(X, y, epochs=epochs, seed=seed, log=log)
+    params, hists = train_ensemble(X, y, models=models, epochs=epochs, seed=seed, log=log)
+    hist = hists[0]
     train_s = time.perf_counter() - t1
     pool = make_pool(shapes[n_train:])
     t2 = time.perf_counter()
@@ -288,7 +304,7 @@ def run_experiment(out_path: str, n_shapes: int = 600, n_train: int = 500, reps:
     retime_s = time.perf_counter() - t2
     ev_te_pass = evaluate(params, te)
     ev_tr = evaluate(params, tr)
-    res = dict(n_shapes=n_shapes, n_train=n_train, samples=int(len(y)), epochs=epochs,
+    res = dict(n_shapes=n_shapes, n_train=n_train, samples=int(len(y)), epochs=epochs, models=models,
                autotune_wall_s=tune_total, autotune_wall_s_per_shape=float(np.mean([r["tune_s"] for r in recs])),
                train_wall_s=train_s, retime_wall_s=retime_s, loss_history=hist, heldout=ev_te,
                heldout_by_path=by_path(te, ev_te),
@@ -308,6 +324,7 @@ if __name__ == "__main__":
     ap.add_argument("--train", type=int, default=500)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--epochs", type=int, default=1000)
+    ap.add_argument("--models", type=int, default=3)
     a = ap.parse_args()
     lc.load()
-    run_experiment(a.out, a.shapes, a.train, a.reps, a.epochs)
+    run_experiment(a.out, a.shapes, a.train, a.reps, a.epochs, models=a.models)

@@ -241,6 +241,13 @@ def test_variant_features_and_pick_arguments(lib):
     v = lc.lc_variant()
     assert lib.lc_pick_variant(kernel.handle, 1000, 35, 3, 0, 3, None, None, 0, ctypes.byref(v), None, None) == 1
     assert lib.lc_pick_variant(kernel.handle, 1000, 35, 3, 0, 3, 16, 16, 8, ctypes.byref(v), None, None) == 6
+    # the ensemble form: at least one model, the same workspace rule
+    assert lib.lc_pick_variant_ensemble(kernel.handle, 1000, 35, 3, 0, 3, 16, 0, 16, need.value, ctypes.byref(v),
+                                        None, None) == 1
+    assert lib.lc_pick_variant_ensemble(kernel.handle, 1000, 35, 3, 0, 3, 16, 3, 16, 8, ctypes.byref(v), None,
+                                        None) == 6
+    assert lib.lc_pick_variant_ensemble(kernel.handle, 1000, 35, 3, 0, 3, 18, 3, 16, need.value, ctypes.byref(v),
+                                        None, None) == 5
 
 
 def test_enumeration_leaves_out_one_warp_plans(lib):
