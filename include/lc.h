@@ -339,7 +339,8 @@ lc_status lc_contract_geo(const lc_kernel *k, const lc_variant *v, const void *D
  * memory; exterior traces inside that window are read from there, the others from global
  * memory (u, vmapP and s must then be 16-byte aligned, else every operand is read from
  * global memory, as with prefetch_smem 0); ctas_per_sm (0 = 4) and max_ctas size the
- * persistent grid, which never exceeds the CTAs resident at once.  An index out
+ * persistent grid, which never exceeds the CTAs resident at once; tile_e 64 or 128 elements
+ * per tile.  An index out
  * of range is not followed: its flux becomes NaN and lc_device_error reports LC_ERR_INDEX.
  * Errors: LC_ERR_INVALID_ARGUMENT, LC_ERR_INVALID_VARIANT, LC_ERR_MISALIGNED (4-byte),
  * LC_ERR_NO_DEVICE, LC_ERR_UNSUPPORTED (not a kernel of this form), LC_ERR_CUDA.

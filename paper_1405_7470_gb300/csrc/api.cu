@@ -1687,14 +1687,14 @@ lc_status lc_variant_validate(const lc_kernel *kh, int64_t E, int32_t N, int32_t
         return LC_ERR_INVALID_ARGUMENT;
     if (kh->k.kind == KIND_LIFT) {
         // E and N as for lc_lift; the descriptor: FP32 SIMT, element-major, grid fields,
-        // staging buffers (stages 1 or 2)
+        // staging buffers (stages 1 or 2), tile of 64 or 128 elements
         if (!v || v->struct_size != sizeof(lc_variant))
             return LC_ERR_INVALID_ARGUMENT;
         if (E < 0 || N < 1 || N > 128)
             return LC_ERR_INVALID_ARGUMENT;
         return (v->engine == LC_ENGINE_SIMT && v->precision == LC_PREC_FP32 && v->layout == LC_LAYOUT_ELEM_MAJOR &&
                 v->ctas_per_sm >= 0 && v->ctas_per_sm <= 8 && v->max_ctas >= 0 && v->prefetch_smem >= 0 &&
-                v->prefetch_smem <= 1 && v->stages >= 1 && v->stages <= 2)
+                v->prefetch_smem <= 1 && v->stages >= 1 && v->stages <= 2 && (v->tile_e == 64 || v->tile_e == 128))
                    ? LC_OK
                    : LC_ERR_INVALID_VARIANT;
     }

@@ -188,11 +188,12 @@ struct LiftArgs {
                            // ahead) and exterior traces inside that window read from there;
                            // -1: every operand read from global memory
     int nbuf;              // staging buffers (1 or 2)
+    int te;                // elements per tile (64 or 128)
     unsigned int *err;     // device error word: bit 1 set on an index out of range
 };
 lc_status lift_launch(const LiftArgs &a, int grid, cudaStream_t s);
-size_t lift_smem_bytes(int N, int M, int Nf, int halo, int nbuf);
-int lift_threads(int N);
+size_t lift_smem_bytes(int N, int M, int Nf, int halo, int nbuf, int te);
+int lift_threads(int N, int te);
 
 // Elementwise kernels: check a descriptor against extents (one per iname) without launching;
 // reports the grid and the number of tiles.

@@ -30,7 +30,7 @@
 
 namespace lc {
 
-static constexpr int kLiftTE = 64;     // elements per tile
+// elements per tile: 64 or 128 (descriptor tile_e), a template parameter of the kernel
 static constexpr int kLiftRE = 4;      // elements per thread
 static constexpr int kLiftRC = 4;      // nodes per thread
 static constexpr int kLiftPad = 4;     // padding of a flux row: 16-byte rows (one vector load of a thread's
@@ -45,23 +45,23 @@ __host__ __device__ inline size_t lift_r4(size_t n) { return (n + 3) & ~(size_t)
 struct LiftSmem {
     size_t flux, fmf, bars, buf, buf_bytes, win, vm, sc, total;
 };
-__host__ __device__ inline LiftSmem lift_smem(int N, int M, int Nf, int halo, int nbuf)
+__host__ __device__ inline LiftSmem lift_smem(int N, int M, int Nf, int halo, int nbuf, int TE)
 {
     LiftSmem L;
-    const size_t NP = (size_t)(N + kLiftRC - 1) / kLiftRC * kLiftRC, TP = kLiftTE + kLiftPad;
+    const size_t NP = (size_t)(N + kLiftRC - 1) / kLiftRC * kLiftRC, TP = TE + kLiftPad;
     L.flux = sizeof(float) * (size_t)M * NP;
     L.fmf = L.flux + sizeof(float) * (size_t)M * TP;
     L.bars = L.fmf + sizeof(int2) * (size_t)M;
     L.buf = (L.bars + 2 * sizeof(uint64_t) + 15) & ~(size_t)15;
     L.win = 0;
-    L.vm = halo < 0 ? 0 : sizeof(float) * lift_r4((size_t)(kLiftTE + 2 * halo) * N);
-    L.sc = L.vm + sizeof(int) * lift_r4((size_t)kLiftTE * M);
-    L.buf_bytes = halo < 0 ? 0 : L.sc + sizeof(float) * lift_r4((size_t)kLiftTE * Nf);
+    L.vm = halo < 0 ? 0 : sizeof(float) * lift_r4((size_t)(TE + 2 * halo) * N);
+    L.sc = L.vm + sizeof(int) * lift_r4((size_t)TE * M);
+    L.buf_bytes = halo < 0 ? 0 : L.sc + sizeof(float) * lift_r4((size_t)TE * Nf);
     L.total = L.buf + (size_t)nbuf * L.buf_bytes;
     return L;
 }
 
-template <bool STAGED>
+template <bool STAGED, int TE>
 __global__ void __launch_bounds__(512) lift_kernel(LiftArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -69,10 +69,10 @@ __global__ void __launch_bounds__(512) lift_kernel(LiftArgs a)
     const int N = a.N, M = a.M, Nfp = a.Nfp, Nf = a.Nf;
     const int CG = (N + kLiftRC - 1) / kLiftRC;  // column groups
     const int NP = CG * kLiftRC;                 // padded node count
-    const int TP = kLiftTE + kLiftPad;           // flux row stride
+    const int TP = TE + kLiftPad;                // flux row stride
     const int H = STAGED ? a.halo : 0;
     const int NB = STAGED ? a.nbuf : 1;  // staging buffers (1 or 2)
-    const LiftSmem lay = lift_smem(N, M, Nf, STAGED ? H : -1, NB);
+    const LiftSmem lay = lift_smem(N, M, Nf, STAGED ? H : -1, NB, TE);
     float *LT = reinterpret_cast<float *>(smem_raw);  // [M][NP]
     float *flux = reinterpret_cast<float *>(smem_raw + lay.flux);  // [M][TP]
     int2 *fmf = reinterpret_cast<int2 *>(smem_raw + lay.fmf);      // [M] {node, face}
@@ -90,13 +90,13 @@ __global__ void __launch_bounds__(512) lift_kernel(LiftArgs a)
         if (bad)
             atomicOr(a.err, 2u);
     }
-    const long long ntiles = (E + kLiftTE - 1) / kLiftTE;
+    const long long ntiles = (E + TE - 1) / TE;
     // bulk parts (16-byte multiples) of tile t's three runs; the rest is read by plain loads
     auto runs = [&](long long t, long long &lo, int &wn, int &vn, int &sn) {
-        const long long e0 = t * kLiftTE;
-        const int TEv = (int)min((long long)kLiftTE, E - e0);
+        const long long e0 = t * TE;
+        const int TEv = (int)min((long long)TE, E - e0);
         lo = max(0LL, e0 - H);
-        const long long hi = min(E, e0 + kLiftTE + H);
+        const long long hi = min(E, e0 + TE + H);
         wn = (int)((hi - lo) * N);
         vn = TEv * M;
         sn = TEv * Nf;
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(512) lift_kernel(LiftArgs a)
         unsigned char *buf = smem_raw + lay.buf + (size_t)b * lay.buf_bytes;
         const uint32_t wb = (uint32_t)(wn * 4) & ~15u, vb = (uint32_t)(vn * 4) & ~15u, sb = (uint32_t)(sn * 4) & ~15u;
         mbar_arrive_expect_tx(&bars[b], wb + vb + sb);
-        const long long e0 = t * kLiftTE;
+        const long long e0 = t * TE;
         if (wb)
             bulk_g2s(buf + lay.win, a.u + lo * N, wb, &bars[b]);
         if (vb)
@@ -134,11 +134,11 @@ __global__ void __launch_bounds__(512) lift_kernel(LiftArgs a)
     const int te_first = tid / M, m_first = tid - te_first * M;
     // register block of this thread: elements eg*RE.., nodes cg*RC..
     const int cg = tid % CG, eg = tid / CG;
-    const bool active = eg < kLiftTE / kLiftRE;
+    const bool active = eg < TE / kLiftRE;
     int k = 0;
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
-        const long long e0 = t * kLiftTE;
-        const int TEv = (int)min((long long)kLiftTE, E - e0);
+        const long long e0 = t * TE;
+        const int TEv = (int)min((long long)TE, E - e0);
         const int b = NB == 2 ? (k & 1) : 0;
         const uint32_t ph = (uint32_t)((NB == 2 ? k >> 1 : k) & 1);
         long long lo = 0;
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(512) lift_kernel(LiftArgs a)
         // gather the tile's fluxes, kLiftG items per thread in flight: all index loads first,
         // then all trace loads, then the fluxes
         int te_c = te_first, m_c = m_first;
-        while (te_c < kLiftTE) {
+        while (te_c < TE) {
             int te[kLiftG], m[kLiftG], q[kLiftG];
             float ui[kLiftG], ux[kLiftG], sc[kLiftG];
 #pragma unroll
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(512) lift_kernel(LiftArgs a)
             }
 #pragma unroll
             for (int g = 0; g < kLiftG; ++g) {
-                if (te[g] >= kLiftTE)
+                if (te[g] >= TE)
                     break;
                 float v = 0.f;
                 if (te[g] < TEv) {
@@ -270,26 +270,32 @@ __global__ void __launch_bounds__(512) lift_kernel(LiftArgs a)
     }
 }
 
-size_t lift_smem_bytes(int N, int M, int Nf, int halo, int nbuf) { return lift_smem(N, M, Nf, halo, nbuf).total; }
+size_t lift_smem_bytes(int N, int M, int Nf, int halo, int nbuf, int te)
+{
+    return lift_smem(N, M, Nf, halo, nbuf, te).total;
+}
 
-int lift_threads(int N)
+int lift_threads(int N, int te)
 {
     const int CG = (N + kLiftRC - 1) / kLiftRC;
-    const int t = CG * (kLiftTE / kLiftRE);
+    const int t = CG * (te / kLiftRE);
     return (t + 31) / 32 * 32;
 }
 
 lc_status lift_launch(const LiftArgs &a, int grid, cudaStream_t s)
 {
-    const size_t smem = lift_smem_bytes(a.N, a.M, a.Nf, a.halo, a.nbuf);
-    void *fn = a.halo >= 0 ? reinterpret_cast<void *>(&lift_kernel<true>) : reinterpret_cast<void *>(&lift_kernel<false>);
+    const size_t smem = lift_smem_bytes(a.N, a.M, a.Nf, a.halo, a.nbuf, a.te);
+    void *fn = a.te == 128 ? (a.halo >= 0 ? reinterpret_cast<void *>(&lift_kernel<true, 128>)
+                                          : reinterpret_cast<void *>(&lift_kernel<false, 128>))
+                           : (a.halo >= 0 ? reinterpret_cast<void *>(&lift_kernel<true, 64>)
+                                          : reinterpret_cast<void *>(&lift_kernel<false, 64>));
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return cuda_fail(e);
     // a persistent grid no larger than the CTAs that are resident at once (shared memory may
     // allow fewer per SM than asked for; the rest would wait for a second wave)
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, lift_threads(a.N), smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, lift_threads(a.N, a.te), smem);
     if (e != cudaSuccess)
         return cuda_fail(e);
     const int sms = sm_count();
@@ -297,7 +303,7 @@ lc_status lift_launch(const LiftArgs &a, int grid, cudaStream_t s)
         grid = std::min(grid, per_sm * sms);
     LiftArgs args = a;
     void *params[] = {&args};
-    e = cudaLaunchKernel(fn, dim3(grid), dim3(lift_threads(a.N)), params, smem, s);
+    e = cudaLaunchKernel(fn, dim3(grid), dim3(lift_threads(a.N, a.te)), params, smem, s);
     e = cudaGetLastError();
     return e == cudaSuccess ? LC_OK : cuda_fail(e);
 }
@@ -325,9 +331,10 @@ lc_status lc_lift(const lc_kernel *kh, const lc_variant *v, const float *L, cons
     // persistent grid; nothing else is used
     if (v->engine != LC_ENGINE_SIMT || v->precision != LC_PREC_FP32 || v->layout != LC_LAYOUT_ELEM_MAJOR ||
         v->ctas_per_sm < 0 || v->ctas_per_sm > 8 || v->max_ctas < 0 || v->prefetch_smem < 0 ||
-        v->prefetch_smem > 1 || v->stages < 1 || v->stages > 2)
+        v->prefetch_smem > 1 || v->stages < 1 || v->stages > 2 || (v->tile_e != 64 && v->tile_e != 128))
         return LC_ERR_INVALID_VARIANT;
     const int nbuf = v->stages;  // staging buffers
+    const int te = v->tile_e;    // elements per tile
     for (const void *p : {(const void *)L, (const void *)fmask, (const void *)vmapP, (const void *)s,
                           (const void *)u, (const void *)out})
         if ((uintptr_t)p & 3u)
@@ -358,12 +365,12 @@ lc_status lc_lift(const lc_kernel *kh, const lc_variant *v, const float *L, cons
         halo = 64;
         const int want = std::max(2, v->ctas_per_sm ? v->ctas_per_sm : 4);
         const size_t fit = smem_optin_limit() / want - 1024;  // (1 KB reserved per CTA)
-        while (halo > 0 && lift_smem_bytes(N, Nf * Nfp, Nf, halo, nbuf) > fit)
+        while (halo > 0 && lift_smem_bytes(N, Nf * Nfp, Nf, halo, nbuf, te) > fit)
             halo = halo > 4 ? halo / 2 : 0;
-        if (lift_smem_bytes(N, Nf * Nfp, Nf, halo, nbuf) > smem_optin_limit())
+        if (lift_smem_bytes(N, Nf * Nfp, Nf, halo, nbuf, te) > smem_optin_limit())
             halo = -1;
     }
-    if (lift_smem_bytes(N, Nf * Nfp, Nf, halo, nbuf) > smem_optin_limit())
+    if (lift_smem_bytes(N, Nf * Nfp, Nf, halo, nbuf, te) > smem_optin_limit())
         return LC_ERR_INVALID_VARIANT;
     if (E == 0)
         return LC_OK;
@@ -385,8 +392,9 @@ lc_status lc_lift(const lc_kernel *kh, const lc_variant *v, const float *L, cons
     a.accumulate = accumulate;
     a.halo = halo;
     a.nbuf = nbuf;
+    a.te = te;
     a.err = error_word();
-    const long long ntiles = (E + 63) / 64;
+    const long long ntiles = (E + te - 1) / te;
     long long grid = std::min<long long>(ntiles, (long long)(v->ctas_per_sm ? v->ctas_per_sm : 4) * sms);
     if (v->max_ctas > 0)
         grid = std::min<long long>(grid, v->max_ctas);

@@ -51,9 +51,9 @@ def test_rejects_before_launch(lib):
     assert f(kc.handle, ctypes.byref(v), 16, 16, 16, 16, 16, 16, 10, 35, 4, 15, 0, None) == 2  # other kind
     bad = lc.variant_default(kc, 100, 35, 3, "elem", "bf16x3")
     assert f(k.handle, ctypes.byref(bad), 16, 16, 16, 16, 16, 16, 10, 35, 4, 15, 0, None) == 3
-    for st in (0, 3):  # one or two staging buffers
+    for st, te in ((0, 64), (3, 64), (1, 32), (1, 256)):  # one or two staging buffers, 64 or 128 elements
         w = lc.variant_default(k, 100, 35, 1, "elem", "fp32")
-        w.stages = st
+        w.stages, w.tile_e = st, te
         assert lc.variant_validate(k, 100, 35, 1, w) == 3
         assert f(k.handle, ctypes.byref(w), 16, 16, 16, 16, 16, 16, 10, 35, 4, 15, 0, None) == 3
 
@@ -88,16 +88,17 @@ def test_integer_inputs_bit_exact(accumulate, prefetch):
         u = rng.integers(-8, 9, u.shape).astype(np.float32)
         out0 = rng.integers(-5, 6, u.shape).astype(np.float32)
         want = oracle.lift(L, fmask, vmapP, s, u, out=out0 if accumulate else None)
-        for ctas, stages in ((0, 1), (2, 1), (0, 2), (3, 2)):
+        for ctas, stages, te in ((0, 1, 64), (2, 1, 64), (0, 2, 64), (3, 2, 64), (0, 1, 128), (2, 2, 128)):
             v = lc.variant_default(k, E, u.shape[1], 1, "elem", "fp32")
             v.max_ctas = ctas
             v.prefetch_smem = prefetch
             v.stages = stages
+            v.tile_e = te
             Ld, fd, vd, sd, ud, od = _dev(L, fmask, vmapP, s, u, out0 if accumulate else np.zeros_like(u))
             lc.lift(k, v, Ld, fd, vd, sd, ud, od, accumulate=accumulate)
             torch.cuda.synchronize()
             assert lc.device_error() == 0
-            assert np.array_equal(od.cpu().numpy().astype(np.float64), want), (E, order, ctas, stages)
+            assert np.array_equal(od.cpu().numpy().astype(np.float64), want), (E, order, ctas, stages, te)
 
 
 @pytest.mark.gpu
