@@ -186,7 +186,8 @@ lc_status lc_variant_validate(const lc_kernel *k, int64_t E, int32_t N, int32_t 
  * device current on the calling thread; without one, a 148-SM, 227 KB part is assumed).
  * Nothing is launched.  The caller sets p->struct_size = sizeof(lc_plan).
  * Errors: those of lc_variant_validate; LC_ERR_INVALID_ARGUMENT for a null or
- * mis-sized p.
+ * mis-sized p; LC_ERR_UNSUPPORTED for a surface-lift kernel (its plan depends on the
+ * face counts, which this call does not take).
  */
 typedef struct lc_plan {
     uint32_t struct_size;    /* sizeof(lc_plan) */

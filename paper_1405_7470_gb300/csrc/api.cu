@@ -1714,6 +1714,8 @@ lc_status lc_variant_plan(const lc_kernel *kh, int64_t E, int32_t N, int32_t F, 
 {
     if (!kh || !p || p->struct_size != sizeof(lc_plan))
         return LC_ERR_INVALID_ARGUMENT;
+    if (kh->k.kind == KIND_LIFT)
+        return LC_ERR_UNSUPPORTED;  // the lift's plan needs Nf and Nfp (lc_lift)
     if (kh->k.kind == KIND_ELEMENTWISE) {
         const int64_t ext[2] = {E, N};
         int grid = 0;

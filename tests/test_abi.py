@@ -151,6 +151,26 @@ def test_default_variant_fits(lib):
             assert lc.variant_validate(k, E, N, F, v) == 0
 
 
+def test_default_engine_per_size(lib):
+    """The defaults the autotuner's measurements chose: FP32 on the warp engine up to N = 12,
+    SIMT tiles below N = 96 (element-major 4 x 8 blocks, unrolled; node-major not unrolled
+    from N = 25), K-split from N = 96; BF16X3 on the tensor cores with the A terms in shared
+    memory, then (about N = 100 to 128) in tensor memory, then the K-split FP32 kernel."""
+    k = lc.Kernel()
+    eng = lambda E, N, F, layout, prec: lc.variant_dict(lc.variant_default(k, E, N, F, layout, prec))
+    for layout in ("elem", "node"):
+        assert eng(360273, 4, 3, layout, "fp32")["engine"] == "warp"
+        d = eng(1 << 20, 56, 3, layout, "fp32")
+        assert d["engine"] == "simt" and d["elems_per_thread"] == 4 and d["split_i"] == 8
+        assert d["unroll"] == (4 if layout == "elem" else 1) and d["stages"] == 2
+        assert eng(1 << 20, 120, 3, layout, "fp32")["engine"] == "ksplit"
+        v = lc.variant_default(k, 1 << 21, 35, 3, layout, "bf16x3")
+        assert lc.variant_dict(v)["engine"] == "tcgen05" and lc.variant_plan(k, 1 << 21, 35, 3, v)["a_in_tmem"] == 0
+        v = lc.variant_default(k, 310977, 120, 3, layout, "bf16x3")
+        assert lc.variant_dict(v)["engine"] == "tcgen05" and lc.variant_plan(k, 310977, 120, 3, v)["a_in_tmem"] == 1
+        assert eng(564445, 165, 3, layout, "bf16x3")["engine"] == "ksplit"
+
+
 def test_variant_plan_reports_the_resolved_launch(lib):
     """lc_variant_plan: the tensor plan of the default BF16X3 descriptor, a SIMT plan, and
     the argument checks (host only; without a GPU a 148-SM part is assumed)."""

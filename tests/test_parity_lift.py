@@ -51,6 +51,9 @@ def test_rejects_before_launch(lib):
     assert f(kc.handle, ctypes.byref(v), 16, 16, 16, 16, 16, 16, 10, 35, 4, 15, 0, None) == 2  # other kind
     bad = lc.variant_default(kc, 100, 35, 3, "elem", "bf16x3")
     assert f(k.handle, ctypes.byref(bad), 16, 16, 16, 16, 16, 16, 10, 35, 4, 15, 0, None) == 3
+    # no launch plan without the face counts
+    with pytest.raises(lc.LcError):
+        lc.variant_plan(k, 100, 35, 1, v)
     for st, te in ((0, 64), (3, 64), (1, 32), (1, 256)):  # one or two staging buffers, 64 or 128 elements
         w = lc.variant_default(k, 100, 35, 1, "elem", "fp32")
         w.stages, w.tile_e = st, te
