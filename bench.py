@@ -100,23 +100,23 @@ SAXPY_SOURCES = ('frontend.cu', 'lc_internal.h', 'api.cu')
 # full-size launch, keyed by (workload, layout, precision, engine); valid only while the kernel's
 # sources hash to `src`.  `variant` records the descriptor the capture ran.
 NCU_TRAFFIC = {
-    # E = 2^21: 293.70 MB read + 818.44 MB written (the rest of the output still in L2 at the end)
+    # E = 2^21: 293.77 MB read + 818.33 MB written (the rest of the output still in L2 at the end)
     ("fp32_three", "elem", "bf16x3", "tcgen05"): {
-        "bytes": 293_698_816 + 818_444_800, "files": TC_SOURCES, "src": "1170e40f76261017",
+        "bytes": 293_765_120 + 818_326_016, "files": TC_SOURCES, "src": "a49024fddaadeb7f",
         "variant": {"tile_e": 128, "elems_per_thread": 64, "split_i": 0, "unroll": 3, "prefetch_smem": 2,
                     "stages": 1, "store_rows": 128}},
-    # volume derivative, E = 2^21: 369.20 MB read + 818.72 MB written
+    # volume derivative, E = 2^21: 369.20 MB read + 818.94 MB written
     ("geo", "elem", "bf16x3", "tcgen05"): {
-        "bytes": 369_195_264 + 818_722_816, "files": GEO_SOURCES, "src": "ce0c77b7b90d1d40",
+        "bytes": 369_195_264 + 818_944_768, "files": GEO_SOURCES, "src": "e398372ec11de935",
         "variant": {"tile_e": 128, "elems_per_thread": 64, "split_i": 0, "unroll": 3, "prefetch_smem": 2,
                     "stages": 1, "a_operand": 1}},
-    # surface lift, E = 2^21: 831.01 MB read + 267.10 MB written
+    # surface lift, E = 2^21: 830.68 MB read + 267.15 MB written
     ("lift", "elem", "fp32", "simt"): {
-        "bytes": 831_009_280 + 267_098_624, "files": LIFT_SOURCES, "src": "bac21423264599b2",
+        "bytes": 830_676_736 + 267_149_568, "files": LIFT_SOURCES, "src": "bda8665b005ba89c",
         "variant": {"tile_e": 64, "prefetch_smem": 1, "stages": 1, "ctas_per_sm": 3}},
-    # saxpy, n = 2^28: 2147.74 MB read + 1036.45 MB written
+    # saxpy, n = 2^28: 2147.55 MB read + 1035.85 MB written
     ("saxpy", "elem", "fp32", "simt"): {
-        "bytes": 2_147_741_952 + 1_036_450_304, "files": SAXPY_SOURCES, "src": "8291ad7711ee1c47",
+        "bytes": 2_147_546_880 + 1_035_845_376, "files": SAXPY_SOURCES, "src": "4db89ff371aa9757",
         "variant": {"elems_per_thread": 4, "unroll": 4, "ctas_per_sm": 4}},
 }
 
