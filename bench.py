@@ -102,21 +102,21 @@ SAXPY_SOURCES = ('frontend.cu', 'lc_internal.h', 'api.cu')
 NCU_TRAFFIC = {
     # E = 2^21: 293.77 MB read + 818.33 MB written (the rest of the output still in L2 at the end)
     ("fp32_three", "elem", "bf16x3", "tcgen05"): {
-        "bytes": 293_765_120 + 818_326_016, "files": TC_SOURCES, "src": "a49024fddaadeb7f",
+        "bytes": 293_765_120 + 818_326_016, "files": TC_SOURCES, "src": "34f1edfce109485b",
         "variant": {"tile_e": 128, "elems_per_thread": 64, "split_i": 0, "unroll": 3, "prefetch_smem": 2,
                     "stages": 1, "store_rows": 128}},
     # volume derivative, E = 2^21: 369.20 MB read + 818.94 MB written
     ("geo", "elem", "bf16x3", "tcgen05"): {
-        "bytes": 369_195_264 + 818_944_768, "files": GEO_SOURCES, "src": "e398372ec11de935",
+        "bytes": 369_195_264 + 818_944_768, "files": GEO_SOURCES, "src": "dd8f4fd0ce0d8bf2",
         "variant": {"tile_e": 128, "elems_per_thread": 64, "split_i": 0, "unroll": 3, "prefetch_smem": 2,
                     "stages": 1, "a_operand": 1}},
     # surface lift, E = 2^21: 830.68 MB read + 267.15 MB written
     ("lift", "elem", "fp32", "simt"): {
-        "bytes": 830_676_736 + 267_149_568, "files": LIFT_SOURCES, "src": "bda8665b005ba89c",
+        "bytes": 830_676_736 + 267_149_568, "files": LIFT_SOURCES, "src": "63edc94dc8539bb3",
         "variant": {"tile_e": 64, "prefetch_smem": 1, "stages": 1, "ctas_per_sm": 3}},
     # saxpy, n = 2^28: 2147.55 MB read + 1035.85 MB written
     ("saxpy", "elem", "fp32", "simt"): {
-        "bytes": 2_147_546_880 + 1_035_845_376, "files": SAXPY_SOURCES, "src": "4db89ff371aa9757",
+        "bytes": 2_147_546_880 + 1_035_845_376, "files": SAXPY_SOURCES, "src": "3af129c596256b81",
         "variant": {"elems_per_thread": 4, "unroll": 4, "ctas_per_sm": 4}},
 }
 
@@ -129,13 +129,39 @@ def ncu_traffic(workload: str, layout: str, precision: str, engine: str):
     return None
 
 
+def strip_comments(src: str) -> str:
+    """C/C++ source without its comments and with runs of whitespace collapsed (string and
+    character literals kept as written): the text a change of code, not of a comment, alters."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def csrc_hash(files=None) -> str:
-    """Hash of the named library sources (all of csrc/ when None)."""
+    """Hash of the named library sources (all of csrc/ when None), comments and layout
+    ignored."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1405_7470_gb300", "csrc")
     for f in sorted(files or os.listdir(d)):
-        with open(os.path.join(d, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+        with open(os.path.join(d, f), encoding="utf-8") as fh:
+            h.update(f.encode() + strip_comments(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

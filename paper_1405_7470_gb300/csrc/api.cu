@@ -2670,9 +2670,10 @@ struct GroupedPlanAll {
     size_t off_map = 0, bytes = 0;
 };
 
-// The K-split descriptor for the groups of a tensor-core grouped plan without a tensor-core
-// plan (tiles of 128 elements, j chunks of 8, one u buffer: the fastest measured for N = 120
-// and 165).
+// The K-split descriptor for the groups of a grouped plan that run as their own K-split
+// launch: tensor-core plans' groups without any tensor-core plan (N above 128 for three
+// terms), FP32 plans' groups of N >= 96 (tiles of 128 elements, j chunks of 8, one u buffer:
+// the fastest measured for N = 120 and 165).
 static lc_variant grouped_ks_fallback(const lc_variant *v)
 {
     lc_variant s;
